@@ -1,0 +1,109 @@
+"""Planted mistakes in the C oracle must fail its pins (CPU only).
+
+Each case rewrites one line of ``oracle/vloc_oracle.c`` in a temporary copy
+(a dropped term, a wrong sign, a wrong index, a transposed operand, a lost
+normalisation), builds it, and checks that at least one independent pin --
+brute-force plane-wave sums (Eq. 2), the hand-worked 1x1x4 case, the
+few-mode closed form or the finite-difference gradient -- rejects it.
+"""
+import ctypes
+import json
+import os
+import subprocess
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_1601_07378_gb300 import synth
+
+SRC = os.path.join(os.path.dirname(O.__file__), "vloc_oracle.c")
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+MUTATIONS = {
+    "forward_sign": ("dft_axis(w, n, 1, -1);", "dft_axis(w, n, 1, +1);"),
+    "no_normalisation": ("o[2 * p] = w[2 * idx[p]] / (double)N;", "o[2 * p] = w[2 * idx[p]];"),
+    "transposed_index": ("int64_t j = (pmod(h, n1) * n2 + pmod(k, n2)) * n3 + pmod(l, n3);",
+                         "int64_t j = (pmod(k, n2) * n1 + pmod(h, n1)) * n3 + pmod(l, n3);"),
+    "dropped_plane_wave": ("for (int64_t p = 0; p < npw; ++p) {\n        psi[2 * idx[p]]",
+                           "for (int64_t p = 1; p < npw; ++p) {\n        psi[2 * idx[p]]"),
+    "wrong_twiddle_index": ("int t = (int)(((int64_t)m * k) % len);", "int t = (int)(((int64_t)m + k) % len);"),
+    "imag_part_of_V_product": ("w[2 * j + 1] *= V[j];", "w[2 * j + 1] *= 1.0;"),
+    "conjugated_input": ("psi[2 * idx[p] + 1] = c[2 * p + 1];", "psi[2 * idx[p] + 1] = -c[2 * p + 1];"),
+    "grad_dropped_term": ("(gr[2 * j] * psi[2 * j] + gr[2 * j + 1] * psi[2 * j + 1])",
+                          "(gr[2 * j] * psi[2 * j])"),
+}
+
+
+def _build_mutant(tmp_path, name):
+    src = open(SRC).read()
+    old, new = MUTATIONS[name]
+    assert src.count(old) == 1, name
+    path = tmp_path / f"{name}.c"
+    path.write_text(src.replace(old, new))
+    so = tmp_path / f"lib{name}.so"
+    subprocess.check_call(["gcc", "-O2", "-std=c11", "-D_GNU_SOURCE", "-fopenmp", "-fPIC", "-shared",
+                           "-o", str(so), str(path), "-lm"])
+    return ctypes.CDLL(str(so))
+
+
+def _pins_fail(lib):
+    """True when at least one pin rejects the oracle loaded from ``lib``."""
+    saved = O._lib
+    O._lib = None
+    try:
+        # reuse the wrapper's argtypes by loading through it, then swap the handle
+        real = O._load()
+        for fn in ("oracle_index_map", "oracle_to_real", "oracle_apply", "oracle_grad_V", "oracle_axis_dft"):
+            getattr(lib, fn).argtypes = getattr(real, fn).argtypes
+        O._lib = lib
+        failures = 0
+        # brute force, shuffled list on a non-square grid
+        n = (4, 6, 5)
+        g = synth.sphere_glist(*n, 2.2, order="shuffled", seed=1)
+        c = synth.coefficients(g, 2, seed=5)
+        V, modes = synth.potential(*n, "smooth", seed=7)
+        try:
+            failures += np.linalg.norm(O.apply(n, g, c, V) - O.bf_apply(n, g, c, V)) > 1e-10
+        except O.OracleError:
+            failures += 1
+        # hand-worked case
+        d = json.load(open(os.path.join(GOLDEN, "hand_1x1x4.json")))
+        try:
+            out = O.apply(tuple(d["grid"]), np.array(d["glist"], dtype=np.int32),
+                          np.array(d["coeffs_re"]) + 1j * np.array(d["coeffs_im"]), np.array(d["V"]))
+            failures += np.abs(out.ravel() - (np.array(d["out_re"]) + 1j * np.array(d["out_im"]))).max() > 1e-12
+        except O.OracleError:
+            failures += 1
+        # FD gradient in V
+        n = (6, 6, 6)
+        g = synth.sphere_glist(*n, 2)
+        c = synth.coefficients(g, 1, seed=2)
+        V, _ = synth.potential(*n, "smooth", seed=3)
+        gout = synth.coefficients(g, 1, seed=4)
+        try:
+            dV = O.grad_V(n, g, c, gout)
+            dirn = np.random.default_rng(0).standard_normal(n)
+            L = lambda VV: float(np.real(np.vdot(gout, O.np_apply(n, g, c, VV))))
+            fd = (L(V + 1e-6 * dirn) - L(V - 1e-6 * dirn)) / 2e-6
+            failures += abs(fd - float((dV * dirn).sum())) > 1e-6 * max(1.0, abs(fd))
+        except O.OracleError:
+            failures += 1
+        return failures > 0
+    finally:
+        O._lib = saved
+
+
+@pytest.mark.parametrize("name", sorted(MUTATIONS))
+def test_planted_mistake_is_caught(tmp_path, name):
+    assert _pins_fail(_build_mutant(tmp_path, name)), f"mutation {name} survived every pin"
+
+
+def test_unmutated_oracle_passes(tmp_path):
+    src = open(SRC).read()
+    path = tmp_path / "clean.c"
+    path.write_text(src)
+    so = tmp_path / "libclean.so"
+    subprocess.check_call(["gcc", "-O2", "-std=c11", "-D_GNU_SOURCE", "-fopenmp", "-fPIC", "-shared",
+                           "-o", str(so), str(path), "-lm"])
+    assert not _pins_fail(ctypes.CDLL(str(so)))
