@@ -1,0 +1,415 @@
+"""Benchmark of the V_loc|psi> action on GB300.
+
+Headline: bands/s of the FP32 forward apply on the 96^3 grid, cut-off sphere
+R = 24 (57777 plane waves), 1024 bands per step, inputs resident in HBM
+(473 MB in + 473 MB out per step, larger than L2).  The same JSON line also
+carries the FP64 path, the adjoint, the 96x96x120 grid, the end-to-end
+host-buffer number, the per-kernel roofline, the CPU oracle baseline and a
+cuFFT comparison (torch.fft, comparison only).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun each rank runs its own 1024 bands (weak scaling, no
+collective on the data path); rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "V_loc|ψ⟩ bands/s at 96^3 (FP32 vs FP64), fraction of HBM roofline"
+GRID, R, NBANDS, SEED = (96, 96, 96), 24, 1024, 2
+GRID2 = (96, 96, 120)
+FALLBACK_HBM_GBS = 6800.0
+FP64_NOMINAL_GFLOPS = 1250.0   # 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz ~ 1.26 TF/s
+KERNEL_SOURCES = ["paper_1601_07378_gb300/csrc/kernels_impl.cuh", "paper_1601_07378_gb300/csrc/fft_core.cuh"]
+
+
+def env_int(name, default):
+    try:
+        return int(os.environ.get(name, default))
+    except ValueError:
+        return default
+
+
+def host_cores() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+# ------------------------------------------------------------------ counts
+def path_counts(info, n):
+    """Algorithmic bytes per band per kernel and 5 n log2 n flops per band."""
+    n1, n2, n3 = n
+    S, NP, npw = info["nsticks"], info["nplanes"], info["npw"]
+    e = 8 if info["precision"] == 1 else 16
+    cyl, slab = S * n3, NP * n2 * n3
+    per_band = {
+        "k1_scatter_zpass": (npw + cyl) * e,
+        "k2_ypass_inv": (cyl + slab) * e,
+        "k3_xpass_v": 2 * slab * e,
+        "k2_ypass_fwd": (slab + cyl) * e,
+        "k4_zpass_gather": (cyl + npw) * e,
+    }
+    f = lambda m: 5.0 * m * math.log2(m)
+    flops = 2 * (S * f(n3) + NP * n3 * f(n2) + n2 * n3 * f(n1)) + 2 * n1 * n2 * n3
+    B5 = 2 * npw * e + 4 * cyl * e + 4 * slab * e
+    B3 = 2 * npw * e + 4 * slab * e
+    return per_band, flops, B5, B3
+
+
+def kernel_src_sha() -> str:
+    h = hashlib.sha256()
+    for p in KERNEL_SOURCES:
+        h.update(open(os.path.join(ROOT, p), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def load_traffic(kernel: str, prec: str):
+    """DRAM bytes per band of `kernel` from the committed ncu summary, if it
+    was taken on the current kernel source."""
+    p = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    try:
+        d = json.load(open(p))
+    except (OSError, ValueError):
+        return None
+    ent = d.get(f"{kernel}:{prec}")
+    if not ent or ent.get("source_sha") != kernel_src_sha():
+        return None
+    return ent["dram_bytes"] / ent["bands_per_launch"]
+
+
+def peaks():
+    try:
+        d = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+        return float(d["hbm_gbs"]), "measured"
+    except (OSError, ValueError, KeyError):
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+# ------------------------------------------------------------------ clocks
+REASONS = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+
+
+class ClockSampler:
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines: list[str] = []
+        self.t = None
+
+    def start(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "50"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.t = threading.Thread(target=self._read, daemon=True)
+        self.t.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm, smax, active = [], [], set()
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for name, v in zip(REASONS, f[5:9]):
+                if v.lower().startswith("active"):
+                    active.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        sm.sort()
+        return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": max(smax), "reasons": sorted(active), "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ timing
+def time_steps(fn, steps, warmup, stream, dist_on):
+    import torch
+    import torch.distributed as dist
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    if dist_on:
+        dist.barrier()
+    torch.cuda.synchronize()
+    start = torch.cuda.Event(enable_timing=True)
+    stop = torch.cuda.Event(enable_timing=True)
+    start.record(stream)
+    for _ in range(steps):
+        fn()
+    stop.record(stream)
+    torch.cuda.synchronize()
+    if dist_on:
+        dist.barrier()
+    ms = start.elapsed_time(stop)
+    if dist_on:
+        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    return ms
+
+
+def cpu_oracle_rate(n, g, c, V, nbands_sample):
+    from oracle import oracle as O
+    import numpy as np
+    cores = host_cores()
+    sub = np.ascontiguousarray(c[:nbands_sample].astype(np.complex128))
+    t0 = time.perf_counter()
+    O.apply(n, g, sub, V.astype(np.float64), nthreads=cores)
+    dt = time.perf_counter() - t0
+    return nbands_sample / dt, cores, dt
+
+
+# ------------------------------------------------------------------ arms
+def run_reference(args, rank):
+    """The reference arm: the FP64 CPU oracle, as it stands, on the host cores."""
+    if rank != 0:
+        return
+    import numpy as np
+    from oracle import oracle as O
+    from paper_1601_07378_gb300 import synth
+    O.build()
+    cores = host_cores()
+    g = synth.sphere_glist(*GRID, R)
+    per = max(1, cores)
+    c = synth.coefficients(g, per, seed=SEED, dtype=np.complex64)
+    V = synth.potential(*GRID, "smooth", SEED + 1000)[0].astype(np.float32)
+    for _ in range(args.warmup):
+        cpu_oracle_rate(GRID, g, c, V, per)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        cpu_oracle_rate(GRID, g, c, V, per)
+    dt = time.perf_counter() - t0
+    value = args.steps * per / dt
+    sample = f"{per} bands of the 96^3 R=24 workload per step (FP64 oracle on FP32-rounded inputs)"
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "bands/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "96^3 grid, sphere R=24 (57777 PWs), CPU oracle sample", "bands_per_step": per},
+        "cpu_baseline": {"value": value, "unit": "bands/s", "cores": cores, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": "bands/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args, rank, world, local_rank):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    dist_on = world > 1
+    torch.cuda.set_device(local_rank)
+    if dist_on:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    from paper_1601_07378_gb300.build import build
+    if local_rank == 0:
+        build()
+    if dist_on:
+        dist.barrier()
+    from paper_1601_07378_gb300 import synth, vloc
+
+    stream = torch.cuda.current_stream()
+    g = synth.sphere_glist(*GRID, R)
+    c64 = synth.coefficients(g, NBANDS, seed=SEED + rank, dtype=np.complex64)
+    V96 = synth.potential(*GRID, "smooth", SEED + 1000)[0]
+    V120 = synth.potential(*GRID2, "smooth", SEED + 1000)[0]
+    c_d = torch.from_numpy(c64).cuda()
+    out_d = torch.empty_like(c_d)
+    V_d = torch.from_numpy(V96.astype(np.float32)).cuda()
+    plan = vloc.VlocPlan(GRID, g, torch.complex64)
+    info = plan.info()
+    per_band, flops, B5, B3 = path_counts(info, GRID)
+
+    # ---- headline: FP32 forward, 1024 bands per step
+    sampler = ClockSampler(local_rank)
+    sampler.start()
+    l0 = plan.launch_count()
+    ms = time_steps(lambda: plan.apply(c_d, V_d, out=out_d), args.steps, args.warmup, stream, dist_on)
+    launches = (plan.launch_count() - l0) // (args.steps + args.warmup) * args.steps
+    clocks = sampler.stop()
+    ms_step = ms / args.steps
+    value = world * NBANDS / (ms_step / 1e3)
+
+    # ---- per-kernel device time (profiled pass over the same steps)
+    plan.profile(True)
+    for _ in range(args.steps):
+        plan.apply(c_d, V_d, out=out_d)
+    prof = plan.get_profile()
+    plan.profile(False)
+    tot = sum(t for _, t in prof.values())
+    dom = max(prof, key=lambda k: prof[k][1])
+    nl, tms = prof[dom]
+    bands_per_launch = NBANDS * args.steps / nl
+    bytes_launch = per_band[dom] * bands_per_launch + (GRID[0] * GRID[1] * GRID[2] * 4 if dom == "k3_xpass_v" else 0)
+    achieved = bytes_launch / (tms / nl / 1e3) / 1e9
+    peak, peak_kind = peaks()
+    tr = load_traffic(dom, "f32")
+    roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "peak_source": peak_kind,
+                "traffic": tr * bands_per_launch if tr is not None else None,
+                "alg_bytes_per_launch": bytes_launch, "bands_per_launch": bands_per_launch,
+                "kernel_share": {k: round(v[1] / tot, 4) for k, v in prof.items()}}
+    path = {"B5_bytes_per_band": B5, "B3_bytes_per_band": B3,
+            "frac_of_B5_roofline": value / world / (peak * 1e9 / B5),
+            "frac_of_B3_roofline": value / world / (peak * 1e9 / B3),
+            "flops_per_band": flops, "gflops": value / world * flops / 1e9}
+
+    # ---- adjoint FP32
+    ms_adj = time_steps(lambda: plan.apply(c_d, V_d, out=out_d, adjoint=True), args.steps, 2, stream, dist_on)
+    adj = world * NBANDS / (ms_adj / args.steps / 1e3)
+
+    # ---- 96x96x120 grid (same sphere and coefficients)
+    plan2 = vloc.VlocPlan(GRID2, g, torch.complex64)
+    V2_d = torch.from_numpy(V120.astype(np.float32)).cuda()
+    ms2 = time_steps(lambda: plan2.apply(c_d, V2_d, out=out_d), args.steps, 2, stream, dist_on)
+    c2_value = world * NBANDS / (ms2 / args.steps / 1e3)
+    del plan2, V2_d
+
+    # ---- FP64 path
+    plan64 = vloc.VlocPlan(GRID, g, torch.complex128)
+    c128_d = c_d.to(torch.complex128)
+    o128_d = torch.empty_like(c128_d)
+    V64_d = V_d.to(torch.float64)
+    k64 = max(2, args.steps // 5)
+    ms64 = time_steps(lambda: plan64.apply(c128_d, V64_d, out=o128_d), k64, 1, stream, dist_on)
+    f64_value = world * NBANDS / (ms64 / k64 / 1e3)
+    plan64.profile(True)
+    plan64.apply(c128_d, V64_d, out=o128_d)
+    prof64 = plan64.get_profile()
+    plan64.profile(False)
+    dom64 = max(prof64, key=lambda k: prof64[k][1])
+    f64 = {"value": f64_value, "unit": "bands/s", "ms_per_step": ms64 / k64, "steps": k64,
+           "speedup_fp32_over_fp64": value / f64_value,
+           "roofline": {"bound": "alu", "unit": "GFLOP/s", "achieved": f64_value / world * flops / 1e9,
+                        "peak": FP64_NOMINAL_GFLOPS, "frac": f64_value / world * flops / 1e9 / FP64_NOMINAL_GFLOPS,
+                        "peak_source": "nominal FP64 rate (152 SMs x 2 DFMA/clk at 2.07 GHz)",
+                        "dominant_kernel": dom64,
+                        "kernel_share": {k: round(v[1] / sum(t for _, t in prof64.values()), 4) for k, v in prof64.items()}},
+           "hbm_frac_of_B5": f64_value / world / (peak * 1e9 / (2 * B5))}
+    del plan64, c128_d, o128_d, V64_d
+
+    # ---- end to end through the host-buffer entry point (pinned host memory)
+    c_h = torch.from_numpy(c64).pin_memory()
+    V_h = torch.from_numpy(V96.astype(np.float32)).pin_memory()
+    o_h = torch.empty_like(c_h).pin_memory()
+    for _ in range(2):
+        plan.apply_host(c_h, V_h, o_h)
+    ke = max(3, args.steps // 5)
+    if dist_on:
+        dist.barrier()
+    t0 = time.perf_counter()
+    for _ in range(ke):
+        plan.apply_host(c_h, V_h, o_h)
+    dt = time.perf_counter() - t0
+    if dist_on:
+        t = torch.tensor([dt], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dt = float(t.item())
+    e2e = {"value": world * NBANDS * ke / dt, "unit": "bands/s", "steps": ke,
+           "h2d_bytes_per_step": c_h.numel() * 8 + V_h.numel() * 4, "d2h_bytes_per_step": o_h.numel() * 8}
+
+    # ---- cuFFT comparison (torch.fft on the full grid; comparison only)
+    cufft = None
+    if not args.no_cufft:
+        idx = torch.from_numpy(plan.index_map()).cuda()
+        N = GRID[0] * GRID[1] * GRID[2]
+        chunk = 64
+
+        def cufft_apply():
+            for b0 in range(0, NBANDS, chunk):
+                Z = torch.zeros((chunk, N), dtype=torch.complex64, device="cuda")
+                Z[:, idx] = c_d[b0:b0 + chunk]
+                psi = torch.fft.ifftn(Z.view(chunk, *GRID), dim=(1, 2, 3), norm="forward")
+                u = torch.fft.fftn(psi * V_d, dim=(1, 2, 3), norm="forward")
+                out_d[b0:b0 + chunk] = u.reshape(chunk, N)[:, idx]
+        kc = max(2, args.steps // 5)
+        msc = time_steps(cufft_apply, kc, 1, stream, dist_on)
+        cufft = {"value": world * NBANDS / (msc / kc / 1e3), "unit": "bands/s",
+                 "what": "torch.fft full-grid ifftn/fftn + index scatter/gather, 64-band chunks"}
+
+    # ---- CPU oracle baseline (rank 0, N = 1 only)
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        cores = host_cores()
+        sample = 2 * cores
+        rate, used, dt = cpu_oracle_rate(GRID, g, c64, V96.astype(np.float32), sample)
+        cpu = {"value": rate, "unit": "bands/s", "cores": used, "kind": "oracle",
+               "sample": f"{sample} of the 1024 bands (FP64 C oracle, OpenMP over bands), {dt:.1f} s wall"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "bands/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "96^3 grid, sphere h^2+k^2+l^2<=24^2 (57777 PWs), 1024 bands/GPU, FP32 forward apply",
+                       "grid": list(GRID), "npw": info["npw"], "bands_per_gpu": NBANDS, "chunk_bands": info["chunk_bands"],
+                       "l2": "inputs larger than L2 (473 MB in + 473 MB out per step)", "parallelism": f"bands x{world}"},
+            "roofline": roofline, "path": path,
+            "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clocks,
+            "fp64": f64, "adjoint": {"value": adj, "unit": "bands/s"},
+            "grid_96x96x120": {"value": c2_value, "unit": "bands/s"},
+            "cufft_comparison": cufft,
+        }
+        print(json.dumps(line), flush=True)
+    if dist_on:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--no-cufft", action="store_true", help="skip the torch.fft comparison")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "ours":
+        args.warmup = 3
+    rank = env_int("RANK", 0)
+    world = env_int("WORLD_SIZE", 1)
+    local_rank = env_int("LOCAL_RANK", 0)
+    if args.impl == "reference":
+        run_reference(args, rank)
+        return
+    run_ours(args, rank, world, local_rank)
+
+
+if __name__ == "__main__":
+    main()

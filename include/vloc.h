@@ -1,0 +1,221 @@
+/*
+ * vloc.h -- C ABI of the GB300 (sm_103a) local-potential action library.
+ *
+ * The library applies the local potential of a plane-wave Kohn-Sham
+ * Hamiltonian to a block of wave functions (Gao, Mo, Fang & Wang,
+ * arXiv:1601.07378, Sec. 2, Eqs. 2-3 and the two-FFT recipe after them):
+ * each band's coefficients on the cut-off sphere are scattered onto the
+ * n1 x n2 x n3 grid, transformed to real space by a compact 3-D FFT
+ * (Sec. 4.3, Fig. 5: z-pass on the occupied sticks, y-pass on the planes
+ * that meet them, x-pass on the whole grid), multiplied by the real V(r),
+ * transformed back and gathered onto the sphere:
+ *
+ *     out = A c,   A = (1/N) S^T F- diag(V) F+ S,   N = n1 n2 n3,
+ *
+ * with S the scatter G -> grid point (h mod n1, k mod n2, l mod n3),
+ * F+ the unnormalised transform with kernel exp(+2 pi i m.j / n) and
+ * F- = F+^H.  (Eq. 2 as printed uses exp(-iG.r); that is the same operator
+ * applied to the negated G-list.)
+ *
+ * Conventions for every entry point below:
+ *  - Layouts.  Coefficients and outputs are band-major [nbands][npw], in the
+ *    caller's G-list order, complex interleaved (re, im).  V and grad_V are
+ *    real [n1][n2][n3] with i3 fastest.  Complex64 + float32 for a VLOC_F32
+ *    plan, complex128 + float64 for a VLOC_F64 plan.
+ *  - Pointers passed to the hot-path calls are device pointers aligned to
+ *    their element size (8 B for complex64, 16 B for complex128, 4 or 8 B
+ *    for the real V) unless stated otherwise.  out == coeffs (exact alias) is
+ *    allowed; any other overlap between an input and an output is an error.
+ *  - Ownership.  The caller owns every buffer it passes.  A plan owns its
+ *    index tables, twiddles and workspace; no device memory is allocated by
+ *    vloc_apply, vloc_apply_adjoint, vloc_backward or vloc_apply_batched.
+ *  - Streams.  Work is enqueued on the caller's stream (a cudaStream_t passed
+ *    as void*, NULL = legacy default stream) and the call returns without
+ *    synchronising, except where stated.  A plan must not be used by two
+ *    streams at the same time.
+ *  - Errors.  Every int-returning call returns VLOC_OK (0) or a negative
+ *    VLOC_ERR_* code; no exception crosses this boundary.  On error nothing
+ *    has been enqueued unless the code is VLOC_ERR_CUDA.
+ */
+#ifndef VLOC_H
+#define VLOC_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- return codes -------------------------------------------------------- */
+#define VLOC_OK            0
+#define VLOC_ERR_ARG      (-1)  /* null/misaligned pointer, bad count, overlap      */
+#define VLOC_ERR_SIZE     (-2)  /* grid not 2/3/5-smooth, n < 2 or n > 256, too big  */
+#define VLOC_ERR_GLIST    (-3)  /* duplicate G, index outside [-n/2, (n+1)/2 - 1]   */
+#define VLOC_ERR_ALLOC    (-4)  /* device or host allocation failed                 */
+#define VLOC_ERR_CUDA     (-5)  /* a CUDA runtime call failed                        */
+#define VLOC_ERR_TIMEOUT  (-6)  /* a bounded device-side wait gave up                */
+#define VLOC_ERR_STATE    (-7)  /* plan flags do not allow this call                 */
+
+/* ---- plan flags ---------------------------------------------------------- */
+#define VLOC_F32                0x001  /* complex64 data, FP32 arithmetic           */
+#define VLOC_F64                0x002  /* complex128 data, FP64 arithmetic          */
+#define VLOC_PARTITION_GREEDY   0x000  /* Sec. 3.2 sorted round-robin (default)     */
+#define VLOC_PARTITION_BASIC    0x010  /* Sec. 4.1 cyclic row/column groups         */
+#define VLOC_PARTITION_IMPROVED 0x020  /* Sec. 4.2 plane-sorted row/column groups   */
+#define VLOC_GRAPH              0x100  /* replay apply chains as CUDA graphs        */
+#define VLOC_HOST_ONLY          0x200  /* build host tables only (no device memory, */
+                                       /* no CUDA call); for introspection: the     */
+                                       /* device calls then return VLOC_ERR_STATE   */
+
+typedef struct vloc_plan_s* vloc_plan;
+
+/* Plan information filled by vloc_get_info. */
+typedef struct vloc_info {
+    int32_t n1, n2, n3;          /* grid                                          */
+    int32_t precision;           /* VLOC_F32 or VLOC_F64                          */
+    int64_t npw;                 /* plane waves per band                          */
+    int32_t nsticks;             /* occupied (h, k) z-sticks (the cylinder)       */
+    int32_t nplanes;             /* occupied x-planes h (the cuboid)              */
+    int32_t nparts;              /* stick parts (one z-pass CTA each)             */
+    int32_t lines_per_tile;      /* FFT lines per CTA                             */
+    int64_t chunk_bands;         /* bands per workspace chunk                     */
+    int64_t workspace_bytes;     /* device workspace owned by the plan            */
+    int32_t radix[3][4];         /* per-axis radix schedule (0 = unused)          */
+    int32_t nstages[3];
+} vloc_info;
+
+/*
+ * vloc_plan_create -- build a plan for one grid and one G-list.
+ * Sec. 2 Eqs. 2-3 (which plane waves exist), Sec. 3.2 / Fig. 2 (stick
+ * workloads and the greedy sorted round-robin partition, here dealing
+ * z-sticks to z-pass thread blocks), Sec. 4.3 / Fig. 5 (cylinder and cuboid
+ * supports).
+ *   out        : receives the plan handle (host pointer, not null).
+ *   n1, n2, n3 : grid, each 2..256 and 2/3/5-smooth.
+ *   g_hkl      : HOST pointer, npw x 3 int32 Miller indices (h, k, l), each
+ *                in [-(n/2), (n+1)/2 - 1]; no duplicates.  Copied; the caller
+ *                may free it after the call.
+ *   npw        : number of plane waves, >= 1.
+ *   flags      : exactly one of VLOC_F32 / VLOC_F64, optionally one
+ *                partition flag, VLOC_GRAPH and VLOC_HOST_ONLY.
+ *   max_bands_per_chunk : bands per workspace chunk (<= 0: automatic, sized
+ *                to keep the chunk's intermediates in L2).
+ *   stream     : stream used for the one-time table uploads (synchronised
+ *                before return).
+ * Errors: VLOC_ERR_ARG, VLOC_ERR_SIZE, VLOC_ERR_GLIST, VLOC_ERR_ALLOC,
+ * VLOC_ERR_CUDA.  Must be called with the target device current.
+ */
+int vloc_plan_create(vloc_plan* out, int n1, int n2, int n3, const int32_t* g_hkl, int64_t npw,
+                     int flags, int64_t max_bands_per_chunk, void* stream);
+
+/* vloc_plan_destroy -- free the plan's device and host memory (synchronises
+ * the device first).  NULL is accepted.  Returns VLOC_OK or VLOC_ERR_CUDA. */
+int vloc_plan_destroy(vloc_plan plan);
+
+/*
+ * vloc_apply -- out = A c for nbands bands (Sec. 2: G->r FFT, multiply by
+ * V_loc(r), r->G FFT; compact passes of Sec. 4.3).
+ *   coeffs : device [nbands][npw] complex.   V : device [n1][n2][n3] real.
+ *   out    : device [nbands][npw] complex (may equal coeffs).
+ *   nbands : >= 0 (0 is a no-op).
+ * Errors: VLOC_ERR_ARG (null/misaligned pointer, nbands < 0, partial
+ * overlap), VLOC_ERR_CUDA.
+ */
+int vloc_apply(vloc_plan plan, const void* coeffs, const void* V, int64_t nbands, void* out,
+               void* stream);
+
+/* vloc_apply_adjoint -- out = A^H c.  With real V the operator is Hermitian
+ * (A^H = A), so this is the same action; it is a separate entry so that the
+ * operator contract used by the backward pass is explicit.  Arguments and
+ * errors as vloc_apply. */
+int vloc_apply_adjoint(vloc_plan plan, const void* coeffs, const void* V, int64_t nbands,
+                       void* out, void* stream);
+
+/*
+ * vloc_backward -- gradients of a real loss L through out = A c.
+ * grad_out holds dL/dRe(out) + i dL/dIm(out) (PyTorch's convention).
+ *   grad_coeffs (nullable) = A^H grad_out = A grad_out.
+ *   grad_V      (nullable, overwritten, real [n1][n2][n3]) =
+ *       (1/N) sum_n Re( conj(F+ S grad_out_n) * F+ S c_n ),
+ *   with psi_n = F+ S c_n recomputed band by band (no grid is stored); the
+ *   band sum is accumulated in FP64 in a fixed order (deterministic).
+ * Errors as vloc_apply.
+ */
+int vloc_backward(vloc_plan plan, const void* coeffs, const void* grad_out, const void* V,
+                  int64_t nbands, void* grad_coeffs, void* grad_V, void* stream);
+
+/*
+ * vloc_apply_batched -- ninst independent applies (plans of different grids
+ * and spheres) enqueued back to back on one stream; with VLOC_GRAPH plans the
+ * whole batch is one graph launch.  Arrays have ninst entries each; plans
+ * must share a precision.  Errors as vloc_apply, per instance.
+ */
+int vloc_apply_batched(int ninst, const vloc_plan* plans, const void* const* coeffs,
+                       const void* const* V, const int64_t* nbands, void* const* out,
+                       void* stream);
+
+/*
+ * vloc_apply_host -- vloc_apply with HOST buffers: copies the coefficients
+ * and V to the device in chunks, applies, and copies the result back,
+ * overlapping copies with compute on the plan's copy stream.  Pinned host
+ * memory gives asynchronous copies.  Synchronises `stream` before return.
+ * The first call allocates the plan's staging buffers (once).
+ * Errors: VLOC_ERR_ARG, VLOC_ERR_ALLOC, VLOC_ERR_CUDA.
+ */
+int vloc_apply_host(vloc_plan plan, const void* coeffs_host, const void* V_host, int64_t nbands,
+                    void* out_host, void* stream);
+
+/* vloc_get_index_map -- grid_index[p] = ((h mod n1) n2 + (k mod n2)) n3 +
+ * (l mod n3) for every G of the plan's list (host array of npw int64).
+ * Eqs. 2-3. */
+int vloc_get_index_map(vloc_plan plan, int64_t* grid_index);
+
+/* vloc_get_partition -- stick_part[s] = part (z-pass thread block) of the
+ * s-th occupied stick, sticks in ascending (h mod n1) n2 + (k mod n2) order
+ * (host array of nsticks int32); *nparts_out receives the number of parts.
+ * Sec. 3.2 / Fig. 2 (or Sec. 4.1 / 4.2 with the partition flags). */
+int vloc_get_partition(vloc_plan plan, int32_t* stick_part, int32_t* nparts_out);
+
+/* vloc_get_info -- fill *info (host pointer). */
+int vloc_get_info(vloc_plan plan, vloc_info* info);
+
+/* ---- tracing --------------------------------------------------------------
+ * Per-kernel timing with CUDA events recorded on the launching stream around
+ * every kernel of a plan's calls, for the roofline and profile reports.
+ * Kernel slots: 0 scatter + inverse z-pass, 1 inverse y-pass, 2 x-pass with
+ * V(r), 3 forward y-pass, 4 forward z-pass + gather, 5 dL/dV x-pass,
+ * 6 auxiliary (zero / convert). */
+#define VLOC_NKERNELS 8
+typedef struct vloc_kernel_stat {
+    int64_t launches;
+    double total_ms;
+} vloc_kernel_stat;
+
+/* vloc_profile -- enable (1) or disable (0) per-launch event timing and clear
+ * the recorded launches.  Timing costs two event records per launch. */
+int vloc_profile(vloc_plan plan, int enable);
+
+/* vloc_get_profile -- synchronise on the recorded events, fill
+ * stats[VLOC_NKERNELS] (host array) with launches and summed device time per
+ * kernel slot since the last vloc_profile / vloc_get_profile, then clear. */
+int vloc_get_profile(vloc_plan plan, vloc_kernel_stat* stats);
+
+/* vloc_get_launch_count -- kernels launched by this plan since creation
+ * (always counted, profiling or not). */
+int vloc_get_launch_count(vloc_plan plan, int64_t* count);
+
+/* vloc_strerror -- static string for a return code (never NULL). */
+const char* vloc_strerror(int code);
+
+/* vloc_version -- library version, major*10000 + minor*100 + patch. */
+int vloc_version(void);
+
+/* vloc_last_cuda_error -- text of the last CUDA error seen by this thread in
+ * a call that returned VLOC_ERR_CUDA or VLOC_ERR_ALLOC ("" if none). */
+const char* vloc_last_cuda_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* VLOC_H */

@@ -1,0 +1,309 @@
+// fft_core.cuh -- batched, line-parallel mixed-radix 1-D FFT building blocks
+// for the compact 3-D FFT of the V_loc action (Sec. 4.3, Fig. 5: three sets
+// of 1-D FFTs, each run only on the lines that can hold nonzero data).
+//
+// Design (GB300 / sm_103a, CUDA cores -- the transforms are not a dense
+// contraction, so there is no tensor-core form of them worth its accuracy):
+//  * A CTA owns a tile of up to 32 independent lines; lane l of every warp
+//    works on line l, so every shared-memory access is 32 consecutive
+//    elements (bank-conflict free) and every global access of a line tile
+//    whose lines are contiguous in memory is fully coalesced.
+//  * A length-n transform is a Stockham autosort sequence of radix-R stages
+//    (R in {2,3,4,5,6,8,9,10,12,15,16}, at most 4 stages for any 2/3/5-smooth
+//    n <= 256).  A stage reads R elements spaced n/R apart, applies the
+//    inter-stage twiddles, runs an R-point DFT fully in registers and writes R
+//    elements spaced Ns apart (Ns = product of the earlier radices).  The
+//    first stage may read straight from global memory and the last may write
+//    straight to it, so a two-stage transform touches shared memory once.
+//  * The small DFTs are unrolled at compile time; their internal twiddles are
+//    compile-time constants (Taylor series below).  Inter-stage twiddles come
+//    from a per-axis table exp(+2 pi i j / n), made once per plan in FP64.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <type_traits>
+#include <utility>
+
+namespace vloc {
+
+// ------------------------------------------------------------------ complex
+template <typename T> struct Cplx;
+template <> struct Cplx<float> { using type = float2; };
+template <> struct Cplx<double> { using type = double2; };
+template <typename T> using c2 = typename Cplx<T>::type;
+
+template <typename V> __device__ __forceinline__ V cmk(decltype(V{}.x) re, decltype(V{}.x) im) {
+    V r; r.x = re; r.y = im; return r;
+}
+template <typename V> __device__ __forceinline__ V cadd(V a, V b) { return cmk<V>(a.x + b.x, a.y + b.y); }
+template <typename V> __device__ __forceinline__ V csub(V a, V b) { return cmk<V>(a.x - b.x, a.y - b.y); }
+template <typename V> __device__ __forceinline__ V cmul(V a, V b) {
+    return cmk<V>(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+template <typename V> __device__ __forceinline__ V cmulc(V a, V b) {  // a * conj(b)
+    return cmk<V>(a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y);
+}
+template <typename V> __device__ __forceinline__ V cscale(V a, decltype(V{}.x) s) { return cmk<V>(a.x * s, a.y * s); }
+// multiply by S*i (S = +1 or -1)
+template <int S, typename V> __device__ __forceinline__ V mul_si(V a) {
+    return S > 0 ? cmk<V>(-a.y, a.x) : cmk<V>(a.y, -a.x);
+}
+template <typename V> __device__ __forceinline__ V czero() { return cmk<V>(0, 0); }
+
+// ------------------------------------------------- compile-time cos / sin
+// exp(2 pi i m / R) from Taylor series on the first octant (|x| <= pi/4,
+// truncation below 1e-21), with exact integer quadrant reduction.
+namespace ct {
+constexpr double kHalfPi = 1.57079632679489661923132169163975144;
+constexpr double sin_oct(double x) {
+    double x2 = x * x;
+    double s = 1.0 - x2 / (18.0 * 19.0);
+    s = 1.0 - x2 / (16.0 * 17.0) * s;
+    s = 1.0 - x2 / (14.0 * 15.0) * s;
+    s = 1.0 - x2 / (12.0 * 13.0) * s;
+    s = 1.0 - x2 / (10.0 * 11.0) * s;
+    s = 1.0 - x2 / (8.0 * 9.0) * s;
+    s = 1.0 - x2 / (6.0 * 7.0) * s;
+    s = 1.0 - x2 / (4.0 * 5.0) * s;
+    s = 1.0 - x2 / (2.0 * 3.0) * s;
+    return x * s;
+}
+constexpr double cos_oct(double x) {
+    double x2 = x * x;
+    double c = 1.0 - x2 / (19.0 * 20.0);
+    c = 1.0 - x2 / (17.0 * 18.0) * c;
+    c = 1.0 - x2 / (15.0 * 16.0) * c;
+    c = 1.0 - x2 / (13.0 * 14.0) * c;
+    c = 1.0 - x2 / (11.0 * 12.0) * c;
+    c = 1.0 - x2 / (9.0 * 10.0) * c;
+    c = 1.0 - x2 / (7.0 * 8.0) * c;
+    c = 1.0 - x2 / (5.0 * 6.0) * c;
+    c = 1.0 - x2 / (3.0 * 4.0) * c;
+    return 1.0 - x2 / (1.0 * 2.0) * c;
+}
+// cos(2 pi m / R) and sin(2 pi m / R)
+constexpr double cos_turn(int m, int R) {
+    int t = ((m % R) + R) % R;
+    int q = (4 * t) / R, r = 4 * t - q * R;  // angle = (q + r/R) * pi/2, 0 <= r < R
+    double c0 = 2 * r <= R ? cos_oct(kHalfPi * r / R) : sin_oct(kHalfPi * (R - r) / R);
+    double s0 = 2 * r <= R ? sin_oct(kHalfPi * r / R) : cos_oct(kHalfPi * (R - r) / R);
+    return q == 0 ? c0 : q == 1 ? -s0 : q == 2 ? -c0 : s0;
+}
+constexpr double sin_turn(int m, int R) {
+    int t = ((m % R) + R) % R;
+    int q = (4 * t) / R, r = 4 * t - q * R;
+    double c0 = 2 * r <= R ? cos_oct(kHalfPi * r / R) : sin_oct(kHalfPi * (R - r) / R);
+    double s0 = 2 * r <= R ? sin_oct(kHalfPi * r / R) : cos_oct(kHalfPi * (R - r) / R);
+    return q == 0 ? s0 : q == 1 ? c0 : q == 2 ? -s0 : -c0;
+}
+}  // namespace ct
+
+// compile-time unrolled loop: f(std::integral_constant<int, i>) for i < N
+template <int... Is, class F>
+__device__ __forceinline__ void sfor_impl(std::integer_sequence<int, Is...>, F&& f) {
+    (f(std::integral_constant<int, Is>{}), ...);
+}
+template <int N, class F> __device__ __forceinline__ void sfor(F&& f) {
+    sfor_impl(std::make_integer_sequence<int, N>{}, f);
+}
+
+// x * exp(S 2 pi i M / R), M and R compile-time; trivial angles cost no multiply.
+template <int R, int S, int M, typename V> __device__ __forceinline__ V tw_const(V x) {
+    constexpr int m = ((M % R) + R) % R;
+    if constexpr (m == 0) {
+        return x;
+    } else if constexpr (2 * m == R) {
+        return cmk<V>(-x.x, -x.y);
+    } else if constexpr (4 * m == R) {
+        return mul_si<S>(x);
+    } else if constexpr (4 * m == 3 * R) {
+        return mul_si<-S>(x);
+    } else {
+        using T = decltype(V{}.x);
+        constexpr T c = (T)ct::cos_turn(m, R);
+        constexpr T s = (T)(S * ct::sin_turn(m, R));
+        return cmk<V>(x.x * c - x.y * s, x.x * s + x.y * c);
+    }
+}
+
+// ------------------------------------------------------------ small DFTs
+// X[k] = sum_n x[n] exp(S 2 pi i n k / R), in place on registers.
+template <int R, int S> struct Dft;
+
+template <int S> struct Dft<1, S> {
+    template <typename V> __device__ __forceinline__ static void run(V*) {}
+};
+template <int S> struct Dft<2, S> {
+    template <typename V> __device__ __forceinline__ static void run(V* v) {
+        V a = v[0], b = v[1];
+        v[0] = cadd(a, b);
+        v[1] = csub(a, b);
+    }
+};
+template <int S> struct Dft<3, S> {
+    template <typename V> __device__ __forceinline__ static void run(V* v) {
+        using T = decltype(V{}.x);
+        constexpr T h = (T)0.866025403784438646763723170752936183;  // sqrt(3)/2
+        V t = cadd(v[1], v[2]);
+        V d = csub(v[1], v[2]);
+        V m = cmk<V>(v[0].x - (T)0.5 * t.x, v[0].y - (T)0.5 * t.y);
+        V r = mul_si<S>(cscale(d, h));
+        v[0] = cadd(v[0], t);
+        v[1] = cadd(m, r);
+        v[2] = csub(m, r);
+    }
+};
+template <int S> struct Dft<4, S> {
+    template <typename V> __device__ __forceinline__ static void run(V* v) {
+        V t0 = cadd(v[0], v[2]), t1 = csub(v[0], v[2]);
+        V t2 = cadd(v[1], v[3]), t3 = mul_si<S>(csub(v[1], v[3]));
+        v[0] = cadd(t0, t2);
+        v[2] = csub(t0, t2);
+        v[1] = cadd(t1, t3);
+        v[3] = csub(t1, t3);
+    }
+};
+template <int S> struct Dft<5, S> {
+    template <typename V> __device__ __forceinline__ static void run(V* v) {
+        using T = decltype(V{}.x);
+        constexpr T c1 = (T)ct::cos_turn(1, 5), c2 = (T)ct::cos_turn(2, 5);
+        constexpr T s1 = (T)ct::sin_turn(1, 5), s2 = (T)ct::sin_turn(2, 5);
+        V a1 = cadd(v[1], v[4]), b1 = csub(v[1], v[4]);
+        V a2 = cadd(v[2], v[3]), b2 = csub(v[2], v[3]);
+        V x0 = v[0];
+        V p1 = cmk<V>(x0.x + c1 * a1.x + c2 * a2.x, x0.y + c1 * a1.y + c2 * a2.y);
+        V p2 = cmk<V>(x0.x + c2 * a1.x + c1 * a2.x, x0.y + c2 * a1.y + c1 * a2.y);
+        V q1 = mul_si<S>(cmk<V>(s1 * b1.x + s2 * b2.x, s1 * b1.y + s2 * b2.y));
+        V q2 = mul_si<S>(cmk<V>(s2 * b1.x - s1 * b2.x, s2 * b1.y - s1 * b2.y));
+        v[0] = cmk<V>(x0.x + a1.x + a2.x, x0.y + a1.y + a2.y);
+        v[1] = cadd(p1, q1);
+        v[4] = csub(p1, q1);
+        v[2] = cadd(p2, q2);
+        v[3] = csub(p2, q2);
+    }
+};
+// composite R = A * B: n = B n1 + n2, k = k1 + A k2.
+template <int A, int B, int S> struct DftAB {
+    template <typename V> __device__ __forceinline__ static void run(V* v) {
+        constexpr int R = A * B;
+        V y[R];
+        sfor<B>([&](auto n2) {
+            V t[A];
+            sfor<A>([&](auto n1) { t[n1] = v[B * n1 + n2]; });
+            Dft<A, S>::run(t);
+            sfor<A>([&](auto k1) { y[n2 * A + k1] = tw_const<R, S, n2 * k1>(t[k1]); });
+        });
+        sfor<A>([&](auto k1) {
+            V t[B];
+            sfor<B>([&](auto n2) { t[n2] = y[n2 * A + k1]; });
+            Dft<B, S>::run(t);
+            sfor<B>([&](auto k2) { v[k1 + A * k2] = t[k2]; });
+        });
+    }
+};
+template <int S> struct Dft<6, S> : DftAB<2, 3, S> {};
+template <int S> struct Dft<8, S> : DftAB<4, 2, S> {};
+template <int S> struct Dft<9, S> : DftAB<3, 3, S> {};
+template <int S> struct Dft<10, S> : DftAB<2, 5, S> {};
+template <int S> struct Dft<12, S> : DftAB<4, 3, S> {};
+template <int S> struct Dft<15, S> : DftAB<3, 5, S> {};
+template <int S> struct Dft<16, S> : DftAB<4, 4, S> {};
+
+// ------------------------------------------------------------ per-axis plan
+constexpr int kMaxStages = 4;
+constexpr int kLines = 32;          // lines per tile (one per lane)
+constexpr int kLd = kLines + 1;     // shared-memory row pitch (elements)
+constexpr int kThreads = 128;       // threads per CTA
+constexpr int kWarps = kThreads / 32;
+
+struct AxisPlan {
+    int n;
+    int nst;
+    int radix[kMaxStages];
+};
+
+// shared-memory line buffer [n][kLd]
+template <typename V> struct Smem {
+    V* p;
+    __device__ __forceinline__ V operator()(int e, int l) const { return p[e * kLd + l]; }
+    __device__ __forceinline__ void operator()(int e, int l, V v) const { p[e * kLd + l] = v; }
+};
+
+// One Stockham stage of radix R over `lines` lines held across lanes.
+template <int R, int S, typename V, class Src, class Dst>
+__device__ __forceinline__ void fft_stage(int n, int Ns, const V* __restrict__ tw, const Src& src,
+                                         const Dst& dst, int lines) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nI = n / R;
+    const int twstep = n / (Ns * R);
+    if (lane >= lines) return;
+    for (int i = warp; i < nI; i += kWarps) {
+        V v[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) v[r] = src(i + r * nI, lane);
+        const int k = i % Ns;
+        if (Ns > 1) {
+            const int base = k * twstep;
+#pragma unroll
+            for (int r = 1; r < R; ++r) {
+                V w = tw[r * base];
+                v[r] = S > 0 ? cmul(v[r], w) : cmulc(v[r], w);
+            }
+        }
+        Dft<R, S>::run(v);
+        const int j = (i - k) * R + k;
+#pragma unroll
+        for (int r = 0; r < R; ++r) dst(j + r * Ns, lane, v[r]);
+    }
+}
+
+template <int S, typename V, class Src, class Dst>
+__device__ __forceinline__ void stage_dispatch(int R, int n, int Ns, const V* tw, const Src& src, const Dst& dst,
+                                               int lines) {
+    switch (R) {
+        case 2: fft_stage<2, S>(n, Ns, tw, src, dst, lines); break;
+        case 3: fft_stage<3, S>(n, Ns, tw, src, dst, lines); break;
+        case 4: fft_stage<4, S>(n, Ns, tw, src, dst, lines); break;
+        case 5: fft_stage<5, S>(n, Ns, tw, src, dst, lines); break;
+        case 6: fft_stage<6, S>(n, Ns, tw, src, dst, lines); break;
+        case 8: fft_stage<8, S>(n, Ns, tw, src, dst, lines); break;
+        case 9: fft_stage<9, S>(n, Ns, tw, src, dst, lines); break;
+        case 10: fft_stage<10, S>(n, Ns, tw, src, dst, lines); break;
+        case 12: fft_stage<12, S>(n, Ns, tw, src, dst, lines); break;
+        case 15: fft_stage<15, S>(n, Ns, tw, src, dst, lines); break;
+        case 16: fft_stage<16, S>(n, Ns, tw, src, dst, lines); break;
+        default: break;  // the host planner only emits the radices above
+    }
+}
+
+// Buffer that receives the transform when the output is a shared-memory
+// buffer and stages ping-pong P -> Q -> P ...: stage 0 writes P.
+template <typename V> __device__ __forceinline__ V* final_buf(int nst, V* P, V* Q) { return (nst & 1) ? P : Q; }
+
+// Full length-n transform of `lines` lines: stage 0 reads `in` (global or
+// shared, must not be P), intermediate results ping-pong between P and Q,
+// the last stage writes `out`.  Ends without a barrier.
+template <int S, typename V, class In, class Out>
+__device__ __forceinline__ void fft_lines(const AxisPlan& ap, const V* tw, const In& in, const Out& out, V* P, V* Q,
+                                          int lines) {
+    if (ap.nst == 1) {
+        stage_dispatch<S>(ap.radix[0], ap.n, 1, tw, in, out, lines);
+        return;
+    }
+    stage_dispatch<S>(ap.radix[0], ap.n, 1, tw, in, Smem<V>{P}, lines);
+    __syncthreads();
+    int Ns = ap.radix[0];
+    V* cur = P;
+    V* oth = Q;
+    for (int s = 1; s < ap.nst - 1; ++s) {
+        stage_dispatch<S>(ap.radix[s], ap.n, Ns, tw, Smem<V>{cur}, Smem<V>{oth}, lines);
+        __syncthreads();
+        Ns *= ap.radix[s];
+        V* t = cur; cur = oth; oth = t;
+    }
+    stage_dispatch<S>(ap.radix[ap.nst - 1], ap.n, Ns, tw, Smem<V>{cur}, out, lines);
+}
+
+}  // namespace vloc

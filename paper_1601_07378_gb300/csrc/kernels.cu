@@ -1,0 +1,65 @@
+// kernels.cu -- precision dispatch of the V_loc kernel launchers.  The
+// kernels are in kernels_impl.cuh, compiled once per precision in
+// kernels_f32.cu and kernels_f64.cu (two translation units built in
+// parallel).
+#include <cuda_runtime.h>
+
+#include <mutex>
+
+#include "internal.h"
+
+namespace vloc {
+
+__global__ void k_zero_f64(double* p, long long n) {
+    long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i < n) p[i] = 0.0;
+}
+
+int launch_zero_f64(double* p, long long n, cudaStream_t st) {
+    k_zero_f64<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(p, n);
+    return (int)cudaGetLastError();
+}
+
+size_t smem_bytes_for(int dbl, int n) { return dbl ? Launch<double>::smem(n) : Launch<float>::smem(n); }
+size_t grad_smem_bytes(int dbl, int n) { return dbl ? Launch<double>::smem_grad(n) : Launch<float>::smem_grad(n); }
+// The dynamic shared-memory limit is a per-kernel attribute shared by every
+// plan in the process, so it only ever grows.
+int set_smem_limits(int dbl, int nmax, int optin) {
+    static std::mutex mu;
+    static int cur[2] = {0, 0};
+    std::lock_guard<std::mutex> lock(mu);
+    if (nmax <= cur[dbl]) return 0;
+    const int rc = dbl ? Launch<double>::set_limits(nmax, optin) : Launch<float>::set_limits(nmax, optin);
+    if (rc == 0) cur[dbl] = nmax;
+    return rc;
+}
+int launch_twiddles(int dbl, void* tw, int n, cudaStream_t st) {
+    return dbl ? Launch<double>::twiddles(tw, n, st) : Launch<float>::twiddles(tw, n, st);
+}
+int launch_k1_scatter_zpass(int dbl, const DevTables& t, const LaunchAxes& ax, const void* tw3, const void* coeffs,
+                            long long nb, void* cyl, cudaStream_t st) {
+    return dbl ? Launch<double>::k1(t, ax, tw3, coeffs, nb, cyl, st) : Launch<float>::k1(t, ax, tw3, coeffs, nb, cyl, st);
+}
+int launch_k2_ypass(int dbl, int sign, const DevTables& t, const LaunchAxes& ax, const void* tw2, long long nb,
+                    void* cyl, void* slab, cudaStream_t st) {
+    return dbl ? Launch<double>::k2(sign, t, ax, tw2, nb, cyl, slab, st)
+               : Launch<float>::k2(sign, t, ax, tw2, nb, cyl, slab, st);
+}
+int launch_k3_xpass_v(int dbl, const DevTables& t, const LaunchAxes& ax, const void* tw1, const void* V,
+                      long long nb, void* slab, cudaStream_t st) {
+    return dbl ? Launch<double>::k3(t, ax, tw1, V, nb, slab, st) : Launch<float>::k3(t, ax, tw1, V, nb, slab, st);
+}
+int launch_k4_zpass_gather(int dbl, const DevTables& t, const LaunchAxes& ax, const void* tw3, const void* cyl,
+                           long long nb, void* out, cudaStream_t st) {
+    return dbl ? Launch<double>::k4(t, ax, tw3, cyl, nb, out, st) : Launch<float>::k4(t, ax, tw3, cyl, nb, out, st);
+}
+int launch_k3b_grad_v(int dbl, const DevTables& t, const LaunchAxes& ax, const void* tw1, const void* slab_c,
+                      const void* slab_g, long long nb, double* acc, cudaStream_t st) {
+    return dbl ? Launch<double>::k3b(t, ax, tw1, slab_c, slab_g, nb, acc, st)
+               : Launch<float>::k3b(t, ax, tw1, slab_c, slab_g, nb, acc, st);
+}
+int launch_finish_grad_v(int dbl, const double* acc, void* gradV, long long N, cudaStream_t st) {
+    return dbl ? Launch<double>::finish_grad(acc, gradV, N, st) : Launch<float>::finish_grad(acc, gradV, N, st);
+}
+
+}  // namespace vloc

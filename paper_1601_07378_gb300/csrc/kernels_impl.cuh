@@ -1,0 +1,355 @@
+// kernels_impl.cuh -- the hot path of the V_loc action on GB300 (sm_103a).
+//
+// One apply of a chunk of bands is five launches (Sec. 2's G->r FFT,
+// multiply by V_loc(r), r->G FFT, done as the compact 3-D FFT of Sec. 4.3 /
+// Fig. 5 with the pass order z, y, x and its mirror):
+//   K1 scatter_zpass : sphere -> cylinder.  One CTA per stick part (Sec. 3.2
+//                      greedy partition); scatter the part's plane waves into
+//                      shared memory, inverse z-FFT of each stick.
+//   K2 ypass<+1>     : cylinder -> slab.  One CTA per (plane, 32-z tile);
+//                      inverse y-FFT whose input rows are the plane's sticks.
+//   K3 xpass_v       : slab -> slab, in place.  One CTA per (y, 32-z tile);
+//                      inverse x-FFT over the occupied planes, multiply by
+//                      V(r), forward x-FFT keeping only the occupied planes.
+//   K2 ypass<-1>     : slab -> cylinder, output pruned to the sticks.
+//   K4 zpass_gather  : cylinder -> sphere, forward z-FFT, times 1/N, gather.
+// The "transposes" of the paper's distributed FFT are the cylinder and slab
+// round trips through L2/HBM; workspace chunks are sized to stay in L2.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "fft_core.cuh"
+#include "internal.h"
+
+namespace vloc {
+
+template <typename T> using V2 = c2<T>;
+
+// ------------------------------------------------------------- twiddles
+// exp(+2 pi i j / n) made in FP64 (sincospi) and rounded to the plan's type.
+template <typename T> __global__ void k_twiddles(V2<T>* tw, int n) {
+    int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    double s, c;
+    sincospi(2.0 * (double)j / (double)n, &s, &c);
+    tw[j] = cmk<V2<T>>((T)c, (T)s);
+}
+
+template <typename T> __device__ __forceinline__ void load_tw(V2<T>* stw, const V2<T>* tw, int n) {
+    for (int j = threadIdx.x; j < n; j += kThreads) stw[j] = tw[j];
+}
+
+// ------------------------------------------------------------------ K1
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k1_scatter_zpass(DevTables t, AxisPlan az, const V2<T>* __restrict__ tw3,
+                                                            const V2<T>* __restrict__ coeffs, V2<T>* __restrict__ cyl) {
+    using V = V2<T>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int n3 = t.n3;
+    V* P = reinterpret_cast<V*>(smem_raw);
+    V* Q = P + n3 * kLd;
+    V* stw = Q + n3 * kLd;
+    const int part = blockIdx.x;
+    const long long b = blockIdx.y;
+    const V* c = coeffs + b * t.npw;
+    V* cb = cyl + b * (long long)t.S * n3;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    load_tw<T>(stw, tw3, n3);
+    const int s0 = t.part_ptr[part], ns = t.part_ptr[part + 1] - s0;
+    for (int batch = 0; batch < ns; batch += kLines) {
+        const int lines = min(kLines, ns - batch);
+        for (int i = threadIdx.x; i < n3 * kLd; i += kThreads) Q[i] = czero<V>();
+        __syncthreads();
+        for (int l = warp; l < lines; l += kWarps) {
+            const int s = t.part_sticks[s0 + batch + l];
+            const int q1 = t.stick_pw_ptr[s + 1];
+            for (int q = t.stick_pw_ptr[s] + lane; q < q1; q += 32) Q[t.pw_z[q] * kLd + l] = c[t.pw_user[q]];
+        }
+        __syncthreads();
+        V* D = final_buf(az.nst, P, Q);
+        fft_lines<+1>(az, stw, Smem<V>{Q}, Smem<V>{D}, P, Q, lines);
+        __syncthreads();
+        for (int l = warp; l < lines; l += kWarps) {
+            const int s = t.part_sticks[s0 + batch + l];
+            V* row = cb + (long long)s * n3;
+            for (int z = lane; z < n3; z += 32) row[z] = D[z * kLd + l];
+        }
+        __syncthreads();
+    }
+}
+
+// ------------------------------------------------------------------ K2
+template <typename T> struct CylRows {  // input rows of a y-line tile: the plane's sticks
+    V2<T>* cb;
+    const int* rowmap;
+    int n3, z0;
+    __device__ __forceinline__ V2<T> operator()(int e, int l) const {
+        const int s = rowmap[e];
+        return s >= 0 ? cb[(long long)s * n3 + z0 + l] : czero<V2<T>>();
+    }
+    __device__ __forceinline__ void operator()(int e, int l, V2<T> v) const {
+        const int s = rowmap[e];
+        if (s >= 0) cb[(long long)s * n3 + z0 + l] = v;
+    }
+};
+template <typename T> struct SlabRows {  // all y rows of one plane's slab tile
+    V2<T>* p;  // points at slab[b][plane][0][z0]
+    int n3;
+    __device__ __forceinline__ V2<T> operator()(int e, int l) const { return p[(long long)e * n3 + l]; }
+    __device__ __forceinline__ void operator()(int e, int l, V2<T> v) const { p[(long long)e * n3 + l] = v; }
+};
+
+template <typename T, int S>
+__global__ void __launch_bounds__(kThreads) k2_ypass(DevTables t, AxisPlan ay, const V2<T>* __restrict__ tw2,
+                                                    V2<T>* cyl, V2<T>* slab) {
+    using V = V2<T>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int n2 = t.n2, n3 = t.n3;
+    V* P = reinterpret_cast<V*>(smem_raw);
+    V* Q = P + n2 * kLd;
+    V* stw = Q + n2 * kLd;
+    int* rowmap = reinterpret_cast<int*>(stw + n2);
+    const int plane = blockIdx.x;
+    const int z0 = blockIdx.y * kLines;
+    const long long b = blockIdx.z;
+    const int lines = min(kLines, n3 - z0);
+    load_tw<T>(stw, tw2, n2);
+    for (int e = threadIdx.x; e < n2; e += kThreads) rowmap[e] = -1;
+    __syncthreads();
+    for (int s = t.plane_ptr[plane] + threadIdx.x; s < t.plane_ptr[plane + 1]; s += kThreads) rowmap[t.stick_row[s]] = s;
+    __syncthreads();
+    CylRows<T> cr{cyl + b * (long long)t.S * n3, rowmap, n3, z0};
+    SlabRows<T> sr{slab + ((b * t.NP + plane) * (long long)n2) * n3 + z0, n3};
+    if (S > 0) fft_lines<+1>(ay, stw, cr, sr, P, Q, lines);
+    else fft_lines<-1>(ay, stw, sr, cr, P, Q, lines);
+}
+
+// ------------------------------------------------------------------ K3
+template <typename T> struct XRows {  // x-line tile at fixed y: rows = occupied planes
+    V2<T>* sb;  // slab[b][0][y][z0]
+    const int* xrow;
+    long long pstride;  // n2 * n3
+    __device__ __forceinline__ V2<T> operator()(int e, int l) const {
+        const int p = xrow[e];
+        return p >= 0 ? sb[p * pstride + l] : czero<V2<T>>();
+    }
+    __device__ __forceinline__ void operator()(int e, int l, V2<T> v) const {
+        const int p = xrow[e];
+        if (p >= 0) sb[p * pstride + l] = v;
+    }
+};
+template <typename T> struct TimesV {  // psi(x) * V(x, y, z) into shared memory
+    V2<T>* d;
+    const T* vrow;  // V[0][y][z0]
+    long long xstride;  // n2 * n3
+    __device__ __forceinline__ void operator()(int e, int l, V2<T> v) const {
+        const T w = vrow[e * xstride + l];
+        d[e * kLd + l] = cmk<V2<T>>(v.x * w, v.y * w);
+    }
+};
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k3_xpass_v(DevTables t, AxisPlan ax, const V2<T>* __restrict__ tw1,
+                                                      const T* __restrict__ Vr, V2<T>* slab) {
+    using V = V2<T>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int n1 = t.n1, n2 = t.n2, n3 = t.n3;
+    V* P = reinterpret_cast<V*>(smem_raw);
+    V* Q = P + n1 * kLd;
+    V* stw = Q + n1 * kLd;
+    int* xrow = reinterpret_cast<int*>(stw + n1);
+    const int y = blockIdx.x;
+    const int z0 = blockIdx.y * kLines;
+    const long long b = blockIdx.z;
+    const int lines = min(kLines, n3 - z0);
+    load_tw<T>(stw, tw1, n1);
+    for (int e = threadIdx.x; e < n1; e += kThreads) xrow[e] = t.xrow_plane[e];
+    __syncthreads();
+    const long long pstride = (long long)n2 * n3;
+    XRows<T> xr{slab + b * t.NP * pstride + (long long)y * n3 + z0, xrow, pstride};
+    V* D = final_buf(ax.nst, P, Q);
+    fft_lines<+1>(ax, stw, xr, TimesV<T>{D, Vr + (long long)y * n3 + z0, pstride}, P, Q, lines);
+    __syncthreads();
+    V* P2 = (D == P) ? Q : P;
+    fft_lines<-1>(ax, stw, Smem<V>{D}, xr, P2, D, lines);
+}
+
+// ------------------------------------------------------------------ K4
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k4_zpass_gather(DevTables t, AxisPlan az, const V2<T>* __restrict__ tw3,
+                                                           const V2<T>* __restrict__ cyl, V2<T>* __restrict__ out,
+                                                           T scale) {
+    using V = V2<T>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int n3 = t.n3;
+    V* P = reinterpret_cast<V*>(smem_raw);
+    V* Q = P + n3 * kLd;
+    V* stw = Q + n3 * kLd;
+    const int part = blockIdx.x;
+    const long long b = blockIdx.y;
+    V* o = out + b * t.npw;
+    const V* cb = cyl + b * (long long)t.S * n3;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    load_tw<T>(stw, tw3, n3);
+    const int s0 = t.part_ptr[part], ns = t.part_ptr[part + 1] - s0;
+    for (int batch = 0; batch < ns; batch += kLines) {
+        const int lines = min(kLines, ns - batch);
+        for (int l = warp; l < lines; l += kWarps) {
+            const V* row = cb + (long long)t.part_sticks[s0 + batch + l] * n3;
+            for (int z = lane; z < n3; z += 32) Q[z * kLd + l] = row[z];
+        }
+        __syncthreads();
+        V* D = final_buf(az.nst, P, Q);
+        fft_lines<-1>(az, stw, Smem<V>{Q}, Smem<V>{D}, P, Q, lines);
+        __syncthreads();
+        for (int l = warp; l < lines; l += kWarps) {
+            const int s = t.part_sticks[s0 + batch + l];
+            const int q1 = t.stick_pw_ptr[s + 1];
+            for (int q = t.stick_pw_ptr[s] + lane; q < q1; q += 32) o[t.pw_user[q]] = cscale(D[t.pw_z[q] * kLd + l], scale);
+        }
+        __syncthreads();
+    }
+}
+
+// ----------------------------------------------------------- K3b (dL/dV)
+// For each (y, z tile): psi = inverse x-FFT of the c-slab tile, g = inverse
+// x-FFT of the grad-slab tile, acc(x, y, z) += sum_b Re(conj(g) psi) / N,
+// bands in order (deterministic), FP64 accumulation.
+template <typename T> struct AccumProduct {
+    const V2<T>* psi;  // shared [n1][kLd]
+    double* acc;       // shared [n1][kLd]
+    __device__ __forceinline__ void operator()(int e, int l, V2<T> g) const {
+        const V2<T> p = psi[e * kLd + l];
+        acc[e * kLd + l] += (double)g.x * (double)p.x + (double)g.y * (double)p.y;
+    }
+};
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k3b_grad_v(DevTables t, AxisPlan ax, const V2<T>* __restrict__ tw1,
+                                                      const V2<T>* slab_c, const V2<T>* slab_g, int nb,
+                                                      double* __restrict__ accg, double invN) {
+    using V = V2<T>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int n1 = t.n1, n2 = t.n2, n3 = t.n3;
+    V* stw = reinterpret_cast<V*>(smem_raw);
+    V* P = stw + n1;
+    V* Q = P + n1 * kLd;
+    V* R3 = Q + n1 * kLd;
+    double* acc = reinterpret_cast<double*>(R3 + n1 * kLd);
+    int* xrow = reinterpret_cast<int*>(acc + n1 * kLd);
+    const int y = blockIdx.x;
+    const int z0 = blockIdx.y * kLines;
+    const int lines = min(kLines, n3 - z0);
+    load_tw<T>(stw, tw1, n1);
+    for (int e = threadIdx.x; e < n1; e += kThreads) xrow[e] = t.xrow_plane[e];
+    for (int i = threadIdx.x; i < n1 * kLd; i += kThreads) acc[i] = 0.0;
+    __syncthreads();
+    const long long pstride = (long long)n2 * n3;
+    // psi lands in D1 (a buffer of {P, Q}); g's transform ping-pongs in the
+    // two buffers that are not D1.
+    V* D1 = final_buf(ax.nst, P, Q);
+    V* G1 = (D1 == P) ? Q : P;
+    for (int b = 0; b < nb; ++b) {
+        XRows<T> xc{const_cast<V*>(slab_c) + (long long)b * t.NP * pstride + (long long)y * n3 + z0, xrow, pstride};
+        XRows<T> xg{const_cast<V*>(slab_g) + (long long)b * t.NP * pstride + (long long)y * n3 + z0, xrow, pstride};
+        fft_lines<+1>(ax, stw, xc, Smem<V>{D1}, P, Q, lines);
+        __syncthreads();
+        fft_lines<+1>(ax, stw, xg, AccumProduct<T>{D1, acc}, G1, R3, lines);
+        __syncthreads();
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane < lines) {
+        for (int e = warp; e < n1; e += kWarps) {
+            double* dst = accg + ((long long)e * n2 + y) * n3 + z0 + lane;
+            *dst += acc[e * kLd + lane] * invN;
+        }
+    }
+}
+
+template <typename T> __global__ void k_finish_grad_v(const double* __restrict__ acc, T* __restrict__ g, long long N) {
+    long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i < N) g[i] = (T)acc[i];
+}
+
+// ====================================================== typed launchers
+// Members of Launch<T> (declared in internal.h), instantiated once per
+// precision in kernels_f32.cu / kernels_f64.cu.
+inline AxisPlan axis_of(const LaunchAxes& ax, int a) {
+    AxisPlan p;
+    p.n = ax.n[a];
+    p.nst = ax.nst[a];
+    for (int i = 0; i < kMaxStages; ++i) p.radix[i] = ax.radix[a][i];
+    return p;
+}
+
+template <typename T> size_t Launch<T>::smem(int n) {
+    return 2 * (size_t)n * kLd * sizeof(V2<T>) + (size_t)n * sizeof(V2<T>) + (size_t)n * sizeof(int) + 16;
+}
+template <typename T> size_t Launch<T>::smem_grad(int n) {
+    return 3 * (size_t)n * kLd * sizeof(V2<T>) + (size_t)n * kLd * sizeof(double) + (size_t)n * sizeof(V2<T>) +
+           (size_t)n * sizeof(int) + 16;
+}
+template <typename T> int Launch<T>::set_limits(int nmax, int optin) {
+    const int b = (int)smem(nmax);
+    const int bg = (int)smem_grad(nmax);
+    cudaError_t e;
+    if ((e = cudaFuncSetAttribute(k1_scatter_zpass<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, b))) return e;
+    if ((e = cudaFuncSetAttribute(k2_ypass<T, +1>, cudaFuncAttributeMaxDynamicSharedMemorySize, b))) return e;
+    if ((e = cudaFuncSetAttribute(k2_ypass<T, -1>, cudaFuncAttributeMaxDynamicSharedMemorySize, b))) return e;
+    if ((e = cudaFuncSetAttribute(k3_xpass_v<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, b))) return e;
+    if ((e = cudaFuncSetAttribute(k4_zpass_gather<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, b))) return e;
+    if (bg <= optin && (e = cudaFuncSetAttribute(k3b_grad_v<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, bg))) return e;
+    return 0;
+}
+template <typename T> int Launch<T>::twiddles(void* tw, int n, cudaStream_t st) {
+    k_twiddles<T><<<(n + 127) / 128, 128, 0, st>>>((V2<T>*)tw, n);
+    return (int)cudaGetLastError();
+}
+template <typename T>
+int Launch<T>::k1(const DevTables& t, const LaunchAxes& ax, const void* tw3, const void* coeffs, long long nb, void* cyl,
+                  cudaStream_t st) {
+    k1_scatter_zpass<T><<<dim3(t.P, (unsigned)nb), kThreads, smem(t.n3), st>>>(t, axis_of(ax, 2), (const V2<T>*)tw3,
+                                                                               (const V2<T>*)coeffs, (V2<T>*)cyl);
+    return (int)cudaGetLastError();
+}
+template <typename T>
+int Launch<T>::k2(int sign, const DevTables& t, const LaunchAxes& ax, const void* tw2, long long nb, void* cyl,
+                  void* slab, cudaStream_t st) {
+    const dim3 grid(t.NP, (t.n3 + kLines - 1) / kLines, (unsigned)nb);
+    if (sign > 0)
+        k2_ypass<T, +1><<<grid, kThreads, smem(t.n2), st>>>(t, axis_of(ax, 1), (const V2<T>*)tw2, (V2<T>*)cyl, (V2<T>*)slab);
+    else
+        k2_ypass<T, -1><<<grid, kThreads, smem(t.n2), st>>>(t, axis_of(ax, 1), (const V2<T>*)tw2, (V2<T>*)cyl, (V2<T>*)slab);
+    return (int)cudaGetLastError();
+}
+template <typename T>
+int Launch<T>::k3(const DevTables& t, const LaunchAxes& ax, const void* tw1, const void* V, long long nb, void* slab,
+                  cudaStream_t st) {
+    const dim3 grid(t.n2, (t.n3 + kLines - 1) / kLines, (unsigned)nb);
+    k3_xpass_v<T><<<grid, kThreads, smem(t.n1), st>>>(t, axis_of(ax, 0), (const V2<T>*)tw1, (const T*)V, (V2<T>*)slab);
+    return (int)cudaGetLastError();
+}
+template <typename T>
+int Launch<T>::k4(const DevTables& t, const LaunchAxes& ax, const void* tw3, const void* cyl, long long nb, void* out,
+                  cudaStream_t st) {
+    const T scale = (T)(1.0 / ((double)t.n1 * t.n2 * t.n3));
+    k4_zpass_gather<T><<<dim3(t.P, (unsigned)nb), kThreads, smem(t.n3), st>>>(
+        t, axis_of(ax, 2), (const V2<T>*)tw3, (const V2<T>*)cyl, (V2<T>*)out, scale);
+    return (int)cudaGetLastError();
+}
+template <typename T>
+int Launch<T>::k3b(const DevTables& t, const LaunchAxes& ax, const void* tw1, const void* sc, const void* sg,
+                   long long nb, double* acc, cudaStream_t st) {
+    const dim3 grid(t.n2, (t.n3 + kLines - 1) / kLines);
+    const double invN = 1.0 / ((double)t.n1 * t.n2 * t.n3);
+    k3b_grad_v<T><<<grid, kThreads, smem_grad(t.n1), st>>>(t, axis_of(ax, 0), (const V2<T>*)tw1, (const V2<T>*)sc,
+                                                           (const V2<T>*)sg, (int)nb, acc, invN);
+    return (int)cudaGetLastError();
+}
+template <typename T> int Launch<T>::finish_grad(const double* acc, void* g, long long N, cudaStream_t st) {
+    k_finish_grad_v<T><<<(unsigned)((N + 255) / 256), 256, 0, st>>>(acc, (T*)g, N);
+    return (int)cudaGetLastError();
+}
+
+}  // namespace vloc

@@ -1,0 +1,631 @@
+// plan.cpp -- host plan builder and the C ABI of include/vloc.h.
+//
+// A plan turns a grid and a plane-wave list into the index tables the
+// kernels walk (Sec. 2 Eqs. 2-3: each G is one grid point; Sec. 4.3 /
+// Fig. 5: the occupied sticks form the cylinder, the occupied x-planes the
+// cuboid), deals the sticks to z-pass thread blocks with the paper's greedy
+// sorted round-robin (Sec. 3.2, Fig. 2) or one of its row/column schemes
+// (Sec. 4.1, 4.2), makes the twiddles on the device in FP64 and owns the
+// workspace that replaces the distributed FFT's transposes.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <numeric>
+#include <vector>
+
+#include "../../include/vloc.h"
+#include "internal.h"
+
+using namespace vloc;
+
+namespace {
+
+thread_local char g_last_cuda[256] = "";
+
+int cuda_fail(cudaError_t e, const char* what) {
+    snprintf(g_last_cuda, sizeof(g_last_cuda), "%s: %s", what, cudaGetErrorString(e));
+    return e == cudaErrorMemoryAllocation ? VLOC_ERR_ALLOC : VLOC_ERR_CUDA;
+}
+#define CK(call)                                              \
+    do {                                                      \
+        cudaError_t e_ = (call);                              \
+        if (e_ != cudaSuccess) return cuda_fail(e_, #call);   \
+    } while (0)
+
+const int kRadices[] = {16, 15, 12, 10, 9, 8, 6, 5, 4, 3, 2};
+constexpr int kLinesPerTile = 32;
+
+bool smooth235(int n) {
+    for (int p : {2, 3, 5})
+        while (n % p == 0) n /= p;
+    return n == 1;
+}
+
+// Fewest stages, then the smallest largest radix, then larger radices first.
+bool plan_radices(int n, int* nst, int radix[4]) {
+    for (int r : kRadices)
+        if (r == n) { *nst = 1; radix[0] = n; radix[1] = radix[2] = radix[3] = 0; return true; }
+    for (int k = 2; k <= 4; ++k) {
+        std::vector<int> best;
+        int idx[4] = {0, 0, 0, 0};
+        const int nr = (int)(sizeof(kRadices) / sizeof(int));
+        while (true) {
+            long long prod = 1;
+            for (int i = 0; i < k; ++i) prod *= kRadices[idx[i]];
+            if (prod == n) {
+                std::vector<int> c(k);
+                for (int i = 0; i < k; ++i) c[i] = kRadices[idx[i]];
+                auto key = [](const std::vector<int>& v) {
+                    int mx = *std::max_element(v.begin(), v.end());
+                    std::vector<int> neg(v.size());
+                    for (size_t i = 0; i < v.size(); ++i) neg[i] = -v[i];
+                    return std::make_pair(mx, neg);
+                };
+                if (best.empty() || key(c) < key(best)) best = c;
+            }
+            int i = k - 1;
+            while (i >= 0 && ++idx[i] == nr) { idx[i] = 0; --i; }
+            if (i < 0) break;
+        }
+        if (!best.empty()) {
+            *nst = k;
+            for (int i = 0; i < 4; ++i) radix[i] = i < k ? best[i] : 0;
+            return true;
+        }
+    }
+    return false;
+}
+
+int pmod(int a, int n) { int r = a % n; return r < 0 ? r + n : r; }
+bool valid_miller(int h, int n) { return h >= -(n / 2) && h <= (n + 1) / 2 - 1; }
+
+// Sec. 4.1: p = m x n with |m - n| minimal, m >= n.
+void process_grid(int p, int* m, int* n) {
+    int mm = (int)std::ceil(std::sqrt((double)p));
+    while (p % mm) ++mm;
+    *m = mm;
+    *n = p / mm;
+}
+
+}  // namespace
+
+struct vloc_plan_s {
+    int n1 = 0, n2 = 0, n3 = 0, dbl = 0, flags = 0;
+    long long npw = 0, N = 0;
+    int S = 0, NP = 0, P = 0;
+    long long chunk = 1, ws_bands = 2;
+    size_t elem = 8;
+    LaunchAxes ax{};
+    std::vector<int64_t> grid_index;  // caller order
+    std::vector<int32_t> stick_part;  // canonical stick order
+    // device
+    int* d_tables = nullptr;
+    DevTables dt{};
+    void* d_tw[3] = {nullptr, nullptr, nullptr};
+    void* d_cyl = nullptr;
+    void* d_slab = nullptr;
+    double* d_acc = nullptr;
+    size_t ws_bytes = 0;
+    // host-buffer path (allocated on first use)
+    void* d_stage = nullptr;
+    size_t stage_bytes = 0;
+    long long stage_bands = 0;
+    cudaStream_t copy_stream = nullptr;
+    cudaEvent_t ev[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+    int device = 0;
+    int smem_optin = 0;
+    std::mutex mu;
+    // launch accounting and optional per-launch event timing
+    long long launches = 0;
+    bool prof_on = false;
+    std::vector<cudaEvent_t> prof_pool;
+    std::vector<std::pair<int, size_t>> prof_recs;  // (kind, index of start event)
+};
+
+extern "C" {
+
+const char* vloc_strerror(int code) {
+    switch (code) {
+        case VLOC_OK: return "ok";
+        case VLOC_ERR_ARG: return "invalid argument (null or misaligned pointer, bad count or overlap)";
+        case VLOC_ERR_SIZE: return "unsupported size (grid must be 2..256 and 2/3/5-smooth)";
+        case VLOC_ERR_GLIST: return "invalid G-list (index out of range or duplicate)";
+        case VLOC_ERR_ALLOC: return "allocation failed";
+        case VLOC_ERR_CUDA: return "CUDA runtime error";
+        case VLOC_ERR_TIMEOUT: return "device-side wait timed out";
+        case VLOC_ERR_STATE: return "call not allowed by the plan's flags";
+        default: return "unknown error";
+    }
+}
+
+int vloc_version(void) { return 100; }
+
+const char* vloc_last_cuda_error(void) { return g_last_cuda; }
+
+static void free_plan(vloc_plan p) {
+    if (!p) return;
+    cudaFree(p->d_tables);
+    for (void* t : p->d_tw) cudaFree(t);
+    cudaFree(p->d_cyl);
+    cudaFree(p->d_slab);
+    cudaFree(p->d_acc);
+    cudaFree(p->d_stage);
+    for (cudaEvent_t e : p->prof_pool) cudaEventDestroy(e);
+    for (cudaEvent_t e : p->ev)
+        if (e) cudaEventDestroy(e);
+    if (p->copy_stream) cudaStreamDestroy(p->copy_stream);
+    delete p;
+}
+
+int vloc_plan_create(vloc_plan* out, int n1, int n2, int n3, const int32_t* g, int64_t npw, int flags,
+                     int64_t max_bands_per_chunk, void* stream) {
+    if (!out) return VLOC_ERR_ARG;
+    *out = nullptr;
+    if (!g || npw <= 0) return npw == 0 ? VLOC_ERR_GLIST : VLOC_ERR_ARG;
+    const int prec = flags & (VLOC_F32 | VLOC_F64);
+    if (prec != VLOC_F32 && prec != VLOC_F64) return VLOC_ERR_ARG;
+    const int part_flag = flags & 0x0F0;
+    if (part_flag != VLOC_PARTITION_GREEDY && part_flag != VLOC_PARTITION_BASIC && part_flag != VLOC_PARTITION_IMPROVED)
+        return VLOC_ERR_ARG;
+    if (flags & ~(0x003 | 0x0F0 | VLOC_GRAPH | VLOC_HOST_ONLY)) return VLOC_ERR_ARG;
+    const bool host_only = (flags & VLOC_HOST_ONLY) != 0;
+    const int ns[3] = {n1, n2, n3};
+    for (int a = 0; a < 3; ++a)
+        if (ns[a] < 2 || ns[a] > 256 || !smooth235(ns[a])) return VLOC_ERR_SIZE;
+    const long long N = (long long)n1 * n2 * n3;
+    if (npw > N) return VLOC_ERR_GLIST;
+    const int dbl = prec == VLOC_F64;
+    const size_t elem = dbl ? 16 : 8;
+    const int nmax = std::max(n1, std::max(n2, n3));
+
+    vloc_plan p = new (std::nothrow) vloc_plan_s();
+    if (!p) return VLOC_ERR_ALLOC;
+    p->n1 = n1; p->n2 = n2; p->n3 = n3; p->dbl = dbl; p->flags = flags; p->npw = npw; p->N = N;
+    p->elem = elem;
+    for (int a = 0; a < 3; ++a) {
+        p->ax.n[a] = ns[a];
+        if (!plan_radices(ns[a], &p->ax.nst[a], p->ax.radix[a])) { free_plan(p); return VLOC_ERR_SIZE; }
+    }
+
+    // ---- index map and validation (Eqs. 2-3)
+    p->grid_index.resize(npw);
+    {
+        std::vector<unsigned char> seen((size_t)N, 0);
+        for (int64_t q = 0; q < npw; ++q) {
+            const int h = g[3 * q], k = g[3 * q + 1], l = g[3 * q + 2];
+            if (!valid_miller(h, n1) || !valid_miller(k, n2) || !valid_miller(l, n3)) { free_plan(p); return VLOC_ERR_GLIST; }
+            const long long j = ((long long)pmod(h, n1) * n2 + pmod(k, n2)) * n3 + pmod(l, n3);
+            if (seen[(size_t)j]) { free_plan(p); return VLOC_ERR_GLIST; }
+            seen[(size_t)j] = 1;
+            p->grid_index[q] = j;
+        }
+    }
+    // ---- canonical order: by stick id (h mod n1) n2 + (k mod n2), then l
+    std::vector<int> order(npw);
+    std::iota(order.begin(), order.end(), 0);
+    auto stick_of = [&](int q) { return (long long)pmod(g[3 * q], n1) * n2 + pmod(g[3 * q + 1], n2); };
+    std::sort(order.begin(), order.end(), [&](int a, int b) {
+        const long long sa = stick_of(a), sb = stick_of(b);
+        if (sa != sb) return sa < sb;
+        return g[3 * a + 2] < g[3 * b + 2];
+    });
+    std::vector<int> pw_user(npw), pw_z(npw), stick_pw_ptr, stick_row, stick_x;
+    std::vector<long long> stick_id;
+    for (int64_t i = 0; i < npw; ++i) {
+        const int q = order[i];
+        pw_user[i] = q;
+        pw_z[i] = pmod(g[3 * q + 2], n3);
+        const long long sid = stick_of(q);
+        if (stick_id.empty() || stick_id.back() != sid) {
+            stick_id.push_back(sid);
+            stick_pw_ptr.push_back((int)i);
+            stick_row.push_back((int)(sid % n2));
+            stick_x.push_back((int)(sid / n2));
+        }
+    }
+    const int S = (int)stick_id.size();
+    stick_pw_ptr.push_back((int)npw);
+    // ---- planes (the cuboid of Fig. 5): occupied x = h mod n1
+    std::vector<int> plane_ptr, xrow_plane(n1, -1);
+    for (int s = 0; s < S; ++s)
+        if (s == 0 || stick_x[s] != stick_x[s - 1]) {
+            xrow_plane[stick_x[s]] = (int)plane_ptr.size();
+            plane_ptr.push_back(s);
+        }
+    const int NP = (int)plane_ptr.size();
+    plane_ptr.push_back(S);
+
+    // ---- partition of the sticks over z-pass thread blocks
+    int P = (S + kLinesPerTile - 1) / kLinesPerTile;
+    std::vector<int32_t> part(S);
+    std::vector<int> weight(S);
+    for (int s = 0; s < S; ++s) weight[s] = stick_pw_ptr[s + 1] - stick_pw_ptr[s];
+    if (part_flag == VLOC_PARTITION_GREEDY) {
+        // Sec. 3.2 / Fig. 2: sort by workload (#PW) descending, ties by stick
+        // id ascending; the k-th sorted stick goes to part k mod P.
+        std::vector<int> srt(S);
+        std::iota(srt.begin(), srt.end(), 0);
+        std::stable_sort(srt.begin(), srt.end(), [&](int a, int b) {
+            if (weight[a] != weight[b]) return weight[a] > weight[b];
+            return stick_id[a] < stick_id[b];
+        });
+        for (int r = 0; r < S; ++r) part[srt[r]] = r % P;
+    } else {
+        int m, ncol;
+        process_grid(P, &m, &ncol);
+        std::vector<long long> row_of(n1), col_of(n2);
+        if (part_flag == VLOC_PARTITION_BASIC) {
+            // Sec. 4.1: cyclic row groups by x, column groups by y.
+            for (int a = 0; a < n1; ++a) row_of[a] = a % m;
+            for (int b = 0; b < n2; ++b) col_of[b] = b % ncol;
+        } else {
+            // Sec. 4.2: planes sorted by #PW (descending, ties by index) dealt
+            // round-robin to row groups (x-planes) and column groups (y-planes).
+            std::vector<long long> wa(n1, 0), wb(n2, 0);
+            for (int s = 0; s < S; ++s) { wa[stick_x[s]] += weight[s]; wb[stick_row[s]] += weight[s]; }
+            std::vector<int> ia(n1), ib(n2);
+            std::iota(ia.begin(), ia.end(), 0);
+            std::iota(ib.begin(), ib.end(), 0);
+            std::stable_sort(ia.begin(), ia.end(), [&](int a, int b) { return wa[a] != wa[b] ? wa[a] > wa[b] : a < b; });
+            std::stable_sort(ib.begin(), ib.end(), [&](int a, int b) { return wb[a] != wb[b] ? wb[a] > wb[b] : a < b; });
+            for (int r = 0; r < n1; ++r) row_of[ia[r]] = r % m;
+            for (int r = 0; r < n2; ++r) col_of[ib[r]] = r % ncol;
+        }
+        for (int s = 0; s < S; ++s) part[s] = (int32_t)(row_of[stick_x[s]] * ncol + col_of[stick_row[s]]);
+    }
+    std::vector<int> part_ptr(P + 1, 0), part_sticks(S);
+    for (int s = 0; s < S; ++s) part_ptr[part[s] + 1]++;
+    for (int i = 0; i < P; ++i) part_ptr[i + 1] += part_ptr[i];
+    {
+        std::vector<int> fill(part_ptr.begin(), part_ptr.end() - 1);
+        for (int s = 0; s < S; ++s) part_sticks[fill[part[s]]++] = s;
+    }
+    p->S = S; p->NP = NP; p->P = P;
+    p->stick_part = part;
+
+    if (host_only) {
+        p->chunk = 0;
+        *out = p;
+        return VLOC_OK;
+    }
+    // shared-memory budget of the largest kernel tile
+    int dev = 0;
+    cudaError_t e;
+    if ((e = cudaGetDevice(&dev))) { free_plan(p); return cuda_fail(e, "cudaGetDevice"); }
+    p->device = dev;
+    int maxopt = 0;
+    if ((e = cudaDeviceGetAttribute(&maxopt, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev))) {
+        free_plan(p); return cuda_fail(e, "cudaDeviceGetAttribute");
+    }
+    if (smem_bytes_for(dbl, nmax) > (size_t)maxopt) { free_plan(p); return VLOC_ERR_SIZE; }
+    p->smem_optin = maxopt;
+
+    // ---- device tables (one allocation)
+    std::vector<int> blob;
+    auto append = [&](const std::vector<int>& v) { size_t off = blob.size(); blob.insert(blob.end(), v.begin(), v.end()); return off; };
+    const size_t o_spp = append(stick_pw_ptr), o_pwu = append(pw_user), o_pwz = append(pw_z), o_row = append(stick_row),
+                 o_pp = append(part_ptr), o_ps = append(part_sticks), o_plp = append(plane_ptr), o_xr = append(xrow_plane);
+    cudaStream_t st = (cudaStream_t)stream;
+    if ((e = cudaMalloc(&p->d_tables, blob.size() * sizeof(int)))) { free_plan(p); return cuda_fail(e, "cudaMalloc(tables)"); }
+    if ((e = cudaMemcpyAsync(p->d_tables, blob.data(), blob.size() * sizeof(int), cudaMemcpyHostToDevice, st))) {
+        free_plan(p); return cuda_fail(e, "upload tables");
+    }
+    DevTables& t = p->dt;
+    t.stick_pw_ptr = p->d_tables + o_spp; t.pw_user = p->d_tables + o_pwu; t.pw_z = p->d_tables + o_pwz;
+    t.stick_row = p->d_tables + o_row; t.part_ptr = p->d_tables + o_pp; t.part_sticks = p->d_tables + o_ps;
+    t.plane_ptr = p->d_tables + o_plp; t.xrow_plane = p->d_tables + o_xr;
+    t.S = S; t.P = P; t.NP = NP; t.n1 = n1; t.n2 = n2; t.n3 = n3; t.npw = npw;
+
+    // ---- twiddles exp(+2 pi i j / n), FP64-made
+    for (int a = 0; a < 3; ++a) {
+        if ((e = cudaMalloc(&p->d_tw[a], (size_t)ns[a] * elem))) { free_plan(p); return cuda_fail(e, "cudaMalloc(twiddles)"); }
+        if (launch_twiddles(dbl, p->d_tw[a], ns[a], st)) { free_plan(p); return cuda_fail(cudaGetLastError(), "twiddles"); }
+    }
+    if ((e = (cudaError_t)set_smem_limits(dbl, nmax, maxopt))) { free_plan(p); return cuda_fail(e, "cudaFuncSetAttribute"); }
+
+    // ---- workspace: cylinder [chunk][S][n3] + slab [chunk][NP][n2][n3]
+    const size_t per_band = ((size_t)S * n3 + (size_t)NP * n2 * n3) * elem;
+    long long chunk = max_bands_per_chunk;
+    if (chunk <= 0) {
+        const size_t target = (size_t)64 << 20;  // about half of L2
+        chunk = std::max<long long>(1, (long long)(target / per_band));
+    }
+    chunk = std::min<long long>(chunk, 65535);
+    p->chunk = chunk;
+    p->ws_bands = std::max<long long>(chunk, 2);
+    p->ws_bytes = per_band * (size_t)p->ws_bands + (size_t)N * sizeof(double);
+    if ((e = cudaMalloc(&p->d_cyl, (size_t)S * n3 * elem * p->ws_bands))) { free_plan(p); return cuda_fail(e, "cudaMalloc(cylinder)"); }
+    if ((e = cudaMalloc(&p->d_slab, (size_t)NP * n2 * n3 * elem * p->ws_bands))) { free_plan(p); return cuda_fail(e, "cudaMalloc(slab)"); }
+    if ((e = cudaMalloc(&p->d_acc, (size_t)N * sizeof(double)))) { free_plan(p); return cuda_fail(e, "cudaMalloc(acc)"); }
+    if ((e = cudaStreamSynchronize(st))) { free_plan(p); return cuda_fail(e, "plan create sync"); }
+    *out = p;
+    return VLOC_OK;
+}
+
+int vloc_plan_destroy(vloc_plan p) {
+    if (!p) return VLOC_OK;
+    if (p->flags & VLOC_HOST_ONLY) { delete p; return VLOC_OK; }
+    cudaError_t e = cudaDeviceSynchronize();
+    free_plan(p);
+    return e == cudaSuccess ? VLOC_OK : cuda_fail(e, "destroy sync");
+}
+
+static bool aligned(const void* q, size_t a) { return ((uintptr_t)q % a) == 0; }
+static bool overlap(const void* a, size_t na, const void* b, size_t nb) {
+    const char *pa = (const char*)a, *pb = (const char*)b;
+    return pa < pb + nb && pb < pa + na;
+}
+
+static int check_io(vloc_plan p, const void* c, const void* V, int64_t nb, const void* out) {
+    if (!p || nb < 0) return VLOC_ERR_ARG;
+    if (p->flags & VLOC_HOST_ONLY) return VLOC_ERR_STATE;
+    if (nb == 0) return VLOC_OK;
+    if (!c || !V || !out) return VLOC_ERR_ARG;
+    const size_t re = p->dbl ? 8 : 4;
+    if (!aligned(c, p->elem) || !aligned(out, p->elem) || !aligned(V, re)) return VLOC_ERR_ARG;
+    const size_t bytes = (size_t)nb * p->npw * p->elem;
+    if (c != out && overlap(c, bytes, out, bytes)) return VLOC_ERR_ARG;
+    if (overlap(V, (size_t)p->N * re, out, bytes)) return VLOC_ERR_ARG;
+    return VLOC_OK;
+}
+
+}  // extern "C"
+
+// Launch one kernel of the chain, bracketed by timing events when profiling.
+template <class F>
+static int launch(vloc_plan p, int kind, cudaStream_t st, F&& f) {
+    size_t i0 = 0;
+    if (p->prof_on) {
+        i0 = p->prof_recs.size() * 2;
+        while (p->prof_pool.size() < i0 + 2) {
+            cudaEvent_t e;
+            cudaError_t err = cudaEventCreate(&e);
+            if (err) return cuda_fail(err, "profiling event");
+            p->prof_pool.push_back(e);
+        }
+        cudaEventRecord(p->prof_pool[i0], st);
+    }
+    const int rc = f();
+    if (rc) return cuda_fail((cudaError_t)rc, "kernel launch");
+    ++p->launches;
+    if (p->prof_on) {
+        cudaEventRecord(p->prof_pool[i0 + 1], st);
+        p->prof_recs.push_back({kind, i0});
+    }
+    return VLOC_OK;
+}
+
+extern "C" {
+
+// out = A c over workspace chunks: K1, K2(+), K3, K2(-), K4 per chunk.
+static int apply_impl(vloc_plan p, const void* c, const void* V, int64_t nb, void* out, cudaStream_t st) {
+    const size_t bstride = (size_t)p->npw * p->elem;
+    const int dbl = p->dbl;
+    const DevTables& t = p->dt;
+    const LaunchAxes& ax = p->ax;
+    for (int64_t b0 = 0; b0 < nb; b0 += p->chunk) {
+        const long long cb = std::min<long long>(p->chunk, nb - b0);
+        const void* cc = (const char*)c + b0 * bstride;
+        void* oo = (char*)out + b0 * bstride;
+        int rc;
+        if ((rc = launch(p, KK_SCATTER_Z, st, [&] { return launch_k1_scatter_zpass(dbl, t, ax, p->d_tw[2], cc, cb, p->d_cyl, st); }))) return rc;
+        if ((rc = launch(p, KK_Y_INV, st, [&] { return launch_k2_ypass(dbl, +1, t, ax, p->d_tw[1], cb, p->d_cyl, p->d_slab, st); }))) return rc;
+        if ((rc = launch(p, KK_X_V, st, [&] { return launch_k3_xpass_v(dbl, t, ax, p->d_tw[0], V, cb, p->d_slab, st); }))) return rc;
+        if ((rc = launch(p, KK_Y_FWD, st, [&] { return launch_k2_ypass(dbl, -1, t, ax, p->d_tw[1], cb, p->d_cyl, p->d_slab, st); }))) return rc;
+        if ((rc = launch(p, KK_Z_GATHER, st, [&] { return launch_k4_zpass_gather(dbl, t, ax, p->d_tw[2], p->d_cyl, cb, oo, st); }))) return rc;
+    }
+    return VLOC_OK;
+}
+
+int vloc_apply(vloc_plan p, const void* c, const void* V, int64_t nb, void* out, void* stream) {
+    int rc = check_io(p, c, V, nb, out);
+    if (rc || nb == 0) return rc;
+    return apply_impl(p, c, V, nb, out, (cudaStream_t)stream);
+}
+
+int vloc_apply_adjoint(vloc_plan p, const void* c, const void* V, int64_t nb, void* out, void* stream) {
+    // A^H = (1/N) S^T F- diag(conj V) F+ S = A for real V.
+    return vloc_apply(p, c, V, nb, out, stream);
+}
+
+int vloc_backward(vloc_plan p, const void* c, const void* gout, const void* V, int64_t nb, void* gc, void* gV,
+                  void* stream) {
+    if (!p || nb < 0) return VLOC_ERR_ARG;
+    if (p->flags & VLOC_HOST_ONLY) return VLOC_ERR_STATE;
+    if (!gc && !gV) return VLOC_OK;
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t re = p->dbl ? 8 : 4;
+    const size_t bytes = (size_t)nb * p->npw * p->elem;
+    if (gc) {
+        int rc = check_io(p, gout, V, nb, gc);
+        if (rc) return rc;
+        if (c && nb > 0 && overlap(c, bytes, gc, bytes)) return VLOC_ERR_ARG;
+    }
+    if (gV) {
+        if (!aligned(gV, re) || (nb > 0 && (!c || !gout || !V))) return VLOC_ERR_ARG;
+        if (nb > 0 && (!aligned(c, p->elem) || !aligned(gout, p->elem))) return VLOC_ERR_ARG;
+        if (nb > 0 && (overlap(gV, (size_t)p->N * re, c, bytes) || overlap(gV, (size_t)p->N * re, gout, bytes)))
+            return VLOC_ERR_ARG;
+        if (gc && overlap(gV, (size_t)p->N * re, gc, bytes)) return VLOC_ERR_ARG;
+        const int dbl = p->dbl;
+        const DevTables& t = p->dt;
+        const LaunchAxes& ax = p->ax;
+        if (grad_smem_bytes(dbl, p->n1) > (size_t)p->smem_optin) return VLOC_ERR_SIZE;
+        int rc;
+        if ((rc = launch(p, KK_AUX, st, [&] { return launch_zero_f64(p->d_acc, p->N, st); }))) return rc;
+        const long long half = std::max<long long>(1, p->ws_bands / 2);
+        const size_t cyl_band = (size_t)p->S * p->n3 * p->elem;
+        const size_t slab_band = (size_t)p->NP * p->n2 * p->n3 * p->elem;
+        char* cylC = (char*)p->d_cyl;
+        char* cylG = cylC + half * cyl_band;
+        char* slabC = (char*)p->d_slab;
+        char* slabG = slabC + half * slab_band;
+        const size_t bstride = (size_t)p->npw * p->elem;
+        for (int64_t b0 = 0; b0 < nb; b0 += half) {
+            const long long cb = std::min<long long>(half, nb - b0);
+            const void* cc = (const char*)c + b0 * bstride;
+            const void* gg = (const char*)gout + b0 * bstride;
+            if ((rc = launch(p, KK_SCATTER_Z, st, [&] { return launch_k1_scatter_zpass(dbl, t, ax, p->d_tw[2], cc, cb, cylC, st); }))) return rc;
+            if ((rc = launch(p, KK_Y_INV, st, [&] { return launch_k2_ypass(dbl, +1, t, ax, p->d_tw[1], cb, cylC, slabC, st); }))) return rc;
+            if ((rc = launch(p, KK_SCATTER_Z, st, [&] { return launch_k1_scatter_zpass(dbl, t, ax, p->d_tw[2], gg, cb, cylG, st); }))) return rc;
+            if ((rc = launch(p, KK_Y_INV, st, [&] { return launch_k2_ypass(dbl, +1, t, ax, p->d_tw[1], cb, cylG, slabG, st); }))) return rc;
+            if ((rc = launch(p, KK_GRAD_V, st, [&] { return launch_k3b_grad_v(dbl, t, ax, p->d_tw[0], slabC, slabG, cb, p->d_acc, st); }))) return rc;
+        }
+        if ((rc = launch(p, KK_AUX, st, [&] { return launch_finish_grad_v(dbl, p->d_acc, gV, p->N, st); }))) return rc;
+    }
+    if (gc && nb > 0) {
+        int rc = apply_impl(p, gout, V, nb, gc, st);
+        if (rc) return rc;
+    }
+    return VLOC_OK;
+}
+
+int vloc_apply_batched(int ninst, const vloc_plan* plans, const void* const* c, const void* const* V,
+                       const int64_t* nb, void* const* out, void* stream) {
+    if (ninst < 0 || (ninst > 0 && (!plans || !c || !V || !nb || !out))) return VLOC_ERR_ARG;
+    for (int i = 0; i < ninst; ++i) {
+        if (!plans[i] || plans[i]->dbl != plans[0]->dbl) return VLOC_ERR_ARG;
+        int rc = check_io(plans[i], c[i], V[i], nb[i], out[i]);
+        if (rc) return rc;
+    }
+    for (int i = 0; i < ninst; ++i) {
+        if (nb[i] == 0) continue;
+        int rc = apply_impl(plans[i], c[i], V[i], nb[i], out[i], (cudaStream_t)stream);
+        if (rc) return rc;
+    }
+    return VLOC_OK;
+}
+
+int vloc_apply_host(vloc_plan p, const void* ch, const void* Vh, int64_t nb, void* oh, void* stream) {
+    if (!p || nb < 0) return VLOC_ERR_ARG;
+    if (p->flags & VLOC_HOST_ONLY) return VLOC_ERR_STATE;
+    if (nb == 0) return VLOC_OK;
+    if (!ch || !Vh || !oh) return VLOC_ERR_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    std::lock_guard<std::mutex> lock(p->mu);
+    const size_t re = p->dbl ? 8 : 4;
+    const size_t bstride = (size_t)p->npw * p->elem;
+    const long long sb = p->chunk;
+    const size_t vbytes = (size_t)p->N * re;
+    // staging: V + 2 slots of (in, out) for `sb` bands
+    const size_t need = vbytes + 4 * (size_t)sb * bstride + 256 * 5;
+    cudaError_t e;
+    if (p->stage_bytes < need) {
+        cudaFree(p->d_stage);
+        p->d_stage = nullptr;
+        p->stage_bytes = 0;
+        if ((e = cudaMalloc(&p->d_stage, need))) return cuda_fail(e, "cudaMalloc(staging)");
+        p->stage_bytes = need;
+        if (!p->copy_stream && (e = cudaStreamCreateWithFlags(&p->copy_stream, cudaStreamNonBlocking)))
+            return cuda_fail(e, "copy stream");
+        for (auto& ev : p->ev)
+            if (!ev && (e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming))) return cuda_fail(e, "events");
+    }
+    auto align = [](size_t x) { return (x + 255) & ~(size_t)255; };
+    char* base = (char*)p->d_stage;
+    char* dV = base;
+    char* slot_in[2];
+    char* slot_out[2];
+    size_t off = align(vbytes);
+    for (int s = 0; s < 2; ++s) {
+        slot_in[s] = base + off; off += align((size_t)sb * bstride);
+        slot_out[s] = base + off; off += align((size_t)sb * bstride);
+    }
+    if ((e = cudaMemcpyAsync(dV, Vh, vbytes, cudaMemcpyHostToDevice, st))) return cuda_fail(e, "H2D V");
+    // ev[s]: slot s input on device; ev[2+s]: slot s result computed;
+    // ev[4+s]: slot s result copied back to the host.
+    const int64_t nchunks = (nb + sb - 1) / sb;
+    for (int64_t i = 0; i < nchunks; ++i) {
+        const int s = (int)(i & 1);
+        const int64_t b0 = i * sb;
+        const long long cb = std::min<long long>(sb, nb - b0);
+        // copy stream: slot s input may be overwritten once chunk i-2 was
+        // consumed (its compute-done event was waited on before its copy-out,
+        // which precedes this copy on the same stream)
+        if ((e = cudaMemcpyAsync(slot_in[s], (const char*)ch + b0 * bstride, cb * bstride, cudaMemcpyHostToDevice, p->copy_stream)))
+            return cuda_fail(e, "H2D coeffs");
+        if ((e = cudaEventRecord(p->ev[s], p->copy_stream))) return cuda_fail(e, "record");
+        if ((e = cudaStreamWaitEvent(st, p->ev[s], 0))) return cuda_fail(e, "wait");
+        // compute stream: slot s output may be overwritten once chunk i-2's
+        // result has been copied back
+        if (i >= 2 && (e = cudaStreamWaitEvent(st, p->ev[4 + s], 0))) return cuda_fail(e, "wait");
+        int rc = apply_impl(p, slot_in[s], dV, cb, slot_out[s], st);
+        if (rc) return rc;
+        if ((e = cudaEventRecord(p->ev[2 + s], st))) return cuda_fail(e, "record");
+        if ((e = cudaStreamWaitEvent(p->copy_stream, p->ev[2 + s], 0))) return cuda_fail(e, "wait");
+        if ((e = cudaMemcpyAsync((char*)oh + b0 * bstride, slot_out[s], cb * bstride, cudaMemcpyDeviceToHost, p->copy_stream)))
+            return cuda_fail(e, "D2H out");
+        if ((e = cudaEventRecord(p->ev[4 + s], p->copy_stream))) return cuda_fail(e, "record");
+    }
+    if ((e = cudaStreamSynchronize(p->copy_stream))) return cuda_fail(e, "sync copy");
+    if ((e = cudaStreamSynchronize(st))) return cuda_fail(e, "sync");
+    return VLOC_OK;
+}
+
+int vloc_profile(vloc_plan p, int enable) {
+    if (!p) return VLOC_ERR_ARG;
+    if (p->flags & VLOC_HOST_ONLY) return VLOC_ERR_STATE;
+    p->prof_on = enable != 0;
+    p->prof_recs.clear();
+    return VLOC_OK;
+}
+
+int vloc_get_profile(vloc_plan p, vloc_kernel_stat* stats) {
+    if (!p || !stats) return VLOC_ERR_ARG;
+    for (int k = 0; k < VLOC_NKERNELS; ++k) { stats[k].launches = 0; stats[k].total_ms = 0.0; }
+    for (const auto& r : p->prof_recs) {
+        cudaError_t e = cudaEventSynchronize(p->prof_pool[r.second + 1]);
+        if (e) return cuda_fail(e, "profile sync");
+        float ms = 0.f;
+        if ((e = cudaEventElapsedTime(&ms, p->prof_pool[r.second], p->prof_pool[r.second + 1]))) return cuda_fail(e, "elapsed");
+        stats[r.first].launches += 1;
+        stats[r.first].total_ms += ms;
+    }
+    p->prof_recs.clear();
+    return VLOC_OK;
+}
+
+int vloc_get_launch_count(vloc_plan p, int64_t* count) {
+    if (!p || !count) return VLOC_ERR_ARG;
+    *count = p->launches;
+    return VLOC_OK;
+}
+
+int vloc_get_index_map(vloc_plan p, int64_t* gi) {
+    if (!p || !gi) return VLOC_ERR_ARG;
+    std::memcpy(gi, p->grid_index.data(), p->grid_index.size() * sizeof(int64_t));
+    return VLOC_OK;
+}
+
+int vloc_get_partition(vloc_plan p, int32_t* sp, int32_t* np) {
+    if (!p) return VLOC_ERR_ARG;
+    if (sp) std::memcpy(sp, p->stick_part.data(), p->stick_part.size() * sizeof(int32_t));
+    if (np) *np = p->P;
+    return VLOC_OK;
+}
+
+int vloc_get_info(vloc_plan p, vloc_info* info) {
+    if (!p || !info) return VLOC_ERR_ARG;
+    std::memset(info, 0, sizeof(*info));
+    info->n1 = p->n1; info->n2 = p->n2; info->n3 = p->n3;
+    info->precision = p->dbl ? VLOC_F64 : VLOC_F32;
+    info->npw = p->npw;
+    info->nsticks = p->S; info->nplanes = p->NP; info->nparts = p->P;
+    info->lines_per_tile = kLinesPerTile;
+    info->chunk_bands = p->chunk;
+    info->workspace_bytes = (int64_t)p->ws_bytes;
+    for (int a = 0; a < 3; ++a) {
+        info->nstages[a] = p->ax.nst[a];
+        for (int i = 0; i < 4; ++i) info->radix[a][i] = p->ax.radix[a][i];
+    }
+    return VLOC_OK;
+}
+
+}  // extern "C"

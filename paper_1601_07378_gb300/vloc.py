@@ -1,0 +1,346 @@
+"""Python binding of libvloc (argument marshalling only).
+
+Every step of the V_loc action runs in the CUDA kernels behind the C ABI of
+``include/vloc.h``; this module only passes device pointers, sizes and the
+current CUDA stream.  PyTorch supplies device memory and streams.  There is
+no CPU or library fallback: if the extension is missing, the first call
+raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libvloc.so")
+
+VLOC_OK = 0
+VLOC_ERR_ARG = -1
+VLOC_ERR_SIZE = -2
+VLOC_ERR_GLIST = -3
+VLOC_ERR_ALLOC = -4
+VLOC_ERR_CUDA = -5
+VLOC_ERR_TIMEOUT = -6
+VLOC_ERR_STATE = -7
+
+VLOC_F32 = 0x001
+VLOC_F64 = 0x002
+VLOC_PARTITION_GREEDY = 0x000
+VLOC_PARTITION_BASIC = 0x010
+VLOC_PARTITION_IMPROVED = 0x020
+VLOC_GRAPH = 0x100
+VLOC_HOST_ONLY = 0x200
+
+# every exported symbol declared in include/vloc.h
+EXPORTS = [
+    "vloc_plan_create", "vloc_plan_destroy", "vloc_apply", "vloc_apply_adjoint", "vloc_backward",
+    "vloc_apply_batched", "vloc_apply_host", "vloc_get_index_map", "vloc_get_partition",
+    "vloc_get_info", "vloc_strerror", "vloc_version", "vloc_last_cuda_error",
+    "vloc_profile", "vloc_get_profile", "vloc_get_launch_count",
+]
+
+KERNEL_NAMES = ["k1_scatter_zpass", "k2_ypass_inv", "k3_xpass_v", "k2_ypass_fwd", "k4_zpass_gather",
+                "k3b_grad_v", "aux", "unused"]
+
+
+class VlocKernelStat(ctypes.Structure):
+    _fields_ = [("launches", ctypes.c_int64), ("total_ms", ctypes.c_double)]
+
+
+class VlocInfo(ctypes.Structure):
+    _fields_ = [
+        ("n1", ctypes.c_int32), ("n2", ctypes.c_int32), ("n3", ctypes.c_int32),
+        ("precision", ctypes.c_int32), ("npw", ctypes.c_int64),
+        ("nsticks", ctypes.c_int32), ("nplanes", ctypes.c_int32), ("nparts", ctypes.c_int32),
+        ("lines_per_tile", ctypes.c_int32), ("chunk_bands", ctypes.c_int64),
+        ("workspace_bytes", ctypes.c_int64), ("radix", (ctypes.c_int32 * 4) * 3),
+        ("nstages", ctypes.c_int32 * 3),
+    ]
+
+
+class VlocError(RuntimeError):
+    def __init__(self, code: int, what: str = ""):
+        self.code = code
+        msg = f"{what}: {strerror(code)} ({code})"
+        extra = last_cuda_error()
+        if extra and code in (VLOC_ERR_CUDA, VLOC_ERR_ALLOC):
+            msg += f" [{extra}]"
+        super().__init__(msg)
+
+
+_lib = None
+_lock = threading.Lock()
+
+
+def load(path: str | None = None) -> ctypes.CDLL:
+    """Load libvloc.so (built by ``paper_1601_07378_gb300.build``)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        p = path or LIB_PATH
+        if not os.path.exists(p):
+            raise RuntimeError(f"libvloc.so is not built ({p}); run paper_1601_07378_gb300.build.build()")
+        lib = ctypes.CDLL(p)
+        vp, i64, i32, c_int = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_int
+        lib.vloc_plan_create.argtypes = [ctypes.POINTER(vp), c_int, c_int, c_int, ctypes.POINTER(i32), i64, c_int, i64, vp]
+        lib.vloc_plan_destroy.argtypes = [vp]
+        for f in (lib.vloc_apply, lib.vloc_apply_adjoint, lib.vloc_apply_host):
+            f.argtypes = [vp, vp, vp, i64, vp, vp]
+        lib.vloc_backward.argtypes = [vp, vp, vp, vp, i64, vp, vp, vp]
+        lib.vloc_apply_batched.argtypes = [c_int, ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(vp),
+                                           ctypes.POINTER(i64), ctypes.POINTER(vp), vp]
+        lib.vloc_get_index_map.argtypes = [vp, ctypes.POINTER(i64)]
+        lib.vloc_get_partition.argtypes = [vp, ctypes.POINTER(i32), ctypes.POINTER(i32)]
+        lib.vloc_get_info.argtypes = [vp, ctypes.POINTER(VlocInfo)]
+        lib.vloc_strerror.argtypes = [c_int]
+        lib.vloc_strerror.restype = ctypes.c_char_p
+        lib.vloc_last_cuda_error.argtypes = []
+        lib.vloc_last_cuda_error.restype = ctypes.c_char_p
+        lib.vloc_version.argtypes = []
+        lib.vloc_profile.argtypes = [vp, c_int]
+        lib.vloc_get_profile.argtypes = [vp, ctypes.POINTER(VlocKernelStat)]
+        lib.vloc_get_launch_count.argtypes = [vp, ctypes.POINTER(i64)]
+        for name in EXPORTS:
+            getattr(lib, name)
+        _lib = lib
+        return lib
+
+
+def strerror(code: int) -> str:
+    try:
+        return load().vloc_strerror(code).decode()
+    except RuntimeError:
+        return str(code)
+
+
+def last_cuda_error() -> str:
+    try:
+        return load().vloc_last_cuda_error().decode()
+    except RuntimeError:
+        return ""
+
+
+def _check(code: int, what: str):
+    if code != VLOC_OK:
+        raise VlocError(code, what)
+
+
+def _stream_ptr(stream=None):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _ptr(t) -> ctypes.c_void_p:
+    return ctypes.c_void_p(t.data_ptr())
+
+
+class VlocPlan:
+    """Plan of the V_loc action for one grid (n1, n2, n3) and one G-list.
+
+    ``glist`` is an int array [npw, 3] of Miller indices; ``dtype`` is
+    ``torch.complex64`` (FP32 path) or ``torch.complex128`` (FP64 path).
+    """
+
+    def __init__(self, grid, glist, dtype=None, *, partition: str = "greedy", chunk: int = 0,
+                 graph: bool = False, host_only: bool = False, stream=None):
+        import torch
+        dtype = dtype or torch.complex64
+        if dtype not in (torch.complex64, torch.complex128):
+            raise TypeError("dtype must be torch.complex64 or torch.complex128")
+        self.lib = load()
+        self.grid = tuple(int(x) for x in grid)
+        self.dtype = dtype
+        self.real_dtype = torch.float32 if dtype == torch.complex64 else torch.float64
+        g = np.ascontiguousarray(np.asarray(glist, dtype=np.int32).reshape(-1, 3))
+        self.npw = len(g)
+        flags = VLOC_F32 if dtype == torch.complex64 else VLOC_F64
+        flags |= {"greedy": VLOC_PARTITION_GREEDY, "basic": VLOC_PARTITION_BASIC,
+                  "improved": VLOC_PARTITION_IMPROVED}[partition]
+        if graph:
+            flags |= VLOC_GRAPH
+        if host_only:
+            flags |= VLOC_HOST_ONLY
+        h = ctypes.c_void_p()
+        sp = ctypes.c_void_p(None) if host_only else _stream_ptr(stream)
+        _check(self.lib.vloc_plan_create(ctypes.byref(h), *self.grid,
+                                         g.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), self.npw,
+                                         flags, int(chunk), sp), "vloc_plan_create")
+        self._h = h
+
+    @property
+    def handle(self) -> ctypes.c_void_p:
+        if self._h is None:
+            raise RuntimeError("plan destroyed")
+        return self._h
+
+    def close(self):
+        if getattr(self, "_h", None) is not None:
+            self.lib.vloc_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ---------------------------------------------------------------- info
+    def info(self) -> dict:
+        inf = VlocInfo()
+        _check(self.lib.vloc_get_info(self.handle, ctypes.byref(inf)), "vloc_get_info")
+        return {
+            "grid": (inf.n1, inf.n2, inf.n3), "precision": inf.precision, "npw": inf.npw,
+            "nsticks": inf.nsticks, "nplanes": inf.nplanes, "nparts": inf.nparts,
+            "lines_per_tile": inf.lines_per_tile, "chunk_bands": inf.chunk_bands,
+            "workspace_bytes": inf.workspace_bytes,
+            "radix": [[inf.radix[a][i] for i in range(inf.nstages[a])] for a in range(3)],
+        }
+
+    def profile(self, enable: bool = True):
+        _check(self.lib.vloc_profile(self.handle, int(enable)), "vloc_profile")
+
+    def get_profile(self) -> dict:
+        arr = (VlocKernelStat * 8)()
+        _check(self.lib.vloc_get_profile(self.handle, arr), "vloc_get_profile")
+        return {KERNEL_NAMES[i]: (int(arr[i].launches), float(arr[i].total_ms)) for i in range(8) if arr[i].launches}
+
+    def launch_count(self) -> int:
+        n = ctypes.c_int64()
+        _check(self.lib.vloc_get_launch_count(self.handle, ctypes.byref(n)), "vloc_get_launch_count")
+        return int(n.value)
+
+    def index_map(self) -> np.ndarray:
+        out = np.empty(self.npw, dtype=np.int64)
+        _check(self.lib.vloc_get_index_map(self.handle, out.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))),
+               "vloc_get_index_map")
+        return out
+
+    def partition(self) -> tuple[np.ndarray, int]:
+        n = ctypes.c_int32()
+        _check(self.lib.vloc_get_partition(self.handle, None, ctypes.byref(n)), "vloc_get_partition")
+        S = self.info()["nsticks"]
+        out = np.empty(S, dtype=np.int32)
+        _check(self.lib.vloc_get_partition(self.handle, out.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                                           ctypes.byref(n)), "vloc_get_partition")
+        return out, int(n.value)
+
+    # ------------------------------------------------------------- checks
+    def _check_c(self, c, name="coeffs"):
+        if not c.is_cuda or c.dtype != self.dtype or not c.is_contiguous():
+            raise ValueError(f"{name} must be a contiguous CUDA {self.dtype} tensor")
+        if c.shape[-1] != self.npw:
+            raise ValueError(f"{name} last dim must be npw={self.npw}")
+
+    def _check_V(self, V):
+        if not V.is_cuda or V.dtype != self.real_dtype or not V.is_contiguous() or V.numel() != np.prod(self.grid):
+            raise ValueError(f"V must be a contiguous CUDA {self.real_dtype} tensor with {np.prod(self.grid)} elements")
+
+    # ---------------------------------------------------------------- calls
+    def apply(self, c, V, out=None, *, adjoint: bool = False, stream=None):
+        """out = A c (or A^H c) for c of shape [..., npw]."""
+        import torch
+        self._check_c(c)
+        self._check_V(V)
+        if out is None:
+            out = torch.empty_like(c)
+        else:
+            self._check_c(out, "out")
+        nb = c.numel() // self.npw
+        fn = self.lib.vloc_apply_adjoint if adjoint else self.lib.vloc_apply
+        _check(fn(self.handle, _ptr(c), _ptr(V), nb, _ptr(out), _stream_ptr(stream)),
+               "vloc_apply_adjoint" if adjoint else "vloc_apply")
+        return out
+
+    def backward(self, c, grad_out, V, *, need_c: bool = True, need_V: bool = True, stream=None):
+        """(dL/dc, dL/dV) through out = A c (PyTorch complex-gradient convention)."""
+        import torch
+        self._check_c(c)
+        self._check_c(grad_out, "grad_out")
+        self._check_V(V)
+        gc = torch.empty_like(c) if need_c else None
+        gV = torch.empty(self.grid, dtype=self.real_dtype, device=c.device) if need_V else None
+        nb = c.numel() // self.npw
+        _check(self.lib.vloc_backward(self.handle, _ptr(c), _ptr(grad_out), _ptr(V), nb,
+                                      _ptr(gc) if gc is not None else None,
+                                      _ptr(gV) if gV is not None else None, _stream_ptr(stream)), "vloc_backward")
+        return gc, gV
+
+    def apply_host(self, c_host, V_host, out_host=None, *, stream=None):
+        """A c with host (CPU, preferably pinned) tensors; copies inside the call."""
+        import torch
+        if c_host.is_cuda or V_host.is_cuda:
+            raise ValueError("apply_host takes CPU tensors")
+        if c_host.dtype != self.dtype or not c_host.is_contiguous() or c_host.shape[-1] != self.npw:
+            raise ValueError("bad host coefficients")
+        if V_host.dtype != self.real_dtype or not V_host.is_contiguous():
+            raise ValueError("bad host V")
+        if out_host is None:
+            out_host = torch.empty_like(c_host, pin_memory=c_host.is_pinned())
+        nb = c_host.numel() // self.npw
+        _check(self.lib.vloc_apply_host(self.handle, _ptr(c_host), _ptr(V_host), nb, _ptr(out_host),
+                                        _stream_ptr(stream)), "vloc_apply_host")
+        return out_host
+
+
+def apply_batched(plans, cs, Vs, outs=None, *, stream=None):
+    """Several plans (different grids / spheres) applied back to back in one call."""
+    import torch
+    n = len(plans)
+    if outs is None:
+        outs = [torch.empty_like(c) for c in cs]
+    for p, c, V, o in zip(plans, cs, Vs, outs):
+        p._check_c(c)
+        p._check_V(V)
+        p._check_c(o, "out")
+    arr = lambda xs: (ctypes.c_void_p * n)(*[ctypes.c_void_p(x) for x in xs])
+    nbs = (ctypes.c_int64 * n)(*[c.numel() // p.npw for p, c in zip(plans, cs)])
+    lib = load()
+    _check(lib.vloc_apply_batched(n, arr([p.handle.value for p in plans]), arr([c.data_ptr() for c in cs]),
+                                  arr([V.data_ptr() for V in Vs]), nbs, arr([o.data_ptr() for o in outs]),
+                                  _stream_ptr(stream)), "vloc_apply_batched")
+    return outs
+
+
+def _autograd_function():
+    import torch
+
+    class VlocApply(torch.autograd.Function):
+        """out = A(V) c with the hand-written backward kernels.
+
+        backward: dL/dc = A grad_out (A is Hermitian for real V),
+        dL/dV(r) = (1/N) sum_n Re(conj(g_n(r)) psi_n(r)), psi_n recomputed.
+        """
+
+        @staticmethod
+        def forward(ctx, c, V, plan):
+            ctx.plan = plan
+            ctx.save_for_backward(c, V)
+            return plan.apply(c.contiguous(), V.contiguous())
+
+        @staticmethod
+        def backward(ctx, grad_out):
+            c, V = ctx.saved_tensors
+            plan = ctx.plan
+            gc, gV = plan.backward(c.contiguous(), grad_out.contiguous(), V.contiguous(),
+                                   need_c=ctx.needs_input_grad[0], need_V=ctx.needs_input_grad[1])
+            if gV is not None:
+                gV = gV.reshape(V.shape)
+            return gc, gV, None
+
+    return VlocApply
+
+
+_VlocApply = None
+
+
+def vloc_apply(c, V, plan):
+    """Differentiable out = A(V) c (torch.autograd)."""
+    global _VlocApply
+    if _VlocApply is None:
+        _VlocApply = _autograd_function()
+    return _VlocApply.apply(c, V, plan)

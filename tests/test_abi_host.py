@@ -1,0 +1,114 @@
+"""C-ABI library: loads, exports every declared symbol, and its host-side
+plan logic (validation, index map, stick partition) is bit-exact against the
+oracle's independent Python restatement.  No GPU and no compute calls."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_1601_07378_gb300 import synth, vloc
+from paper_1601_07378_gb300.build import build
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build()
+    return vloc.load()
+
+
+def _declared_functions():
+    src = open(os.path.join(ROOT, "include", "vloc.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(vloc_[a-z_]+)\s*\(", src)))
+
+
+def test_exports_every_declared_symbol(lib):
+    names = _declared_functions()
+    assert len(names) >= 12
+    for n in names:
+        assert hasattr(lib, n), n
+    assert sorted(vloc.EXPORTS) == names
+
+
+def test_strerror_and_version(lib):
+    assert lib.vloc_version() >= 100
+    for code in (0, -1, -2, -3, -4, -5, -6, -7, -99):
+        assert isinstance(vloc.strerror(code), str) and vloc.strerror(code)
+
+
+def _create(lib, n, g, flags=vloc.VLOC_F32 | vloc.VLOC_HOST_ONLY):
+    h = ctypes.c_void_p()
+    g = np.ascontiguousarray(np.asarray(g, dtype=np.int32).reshape(-1, 3))
+    rc = lib.vloc_plan_create(ctypes.byref(h), n[0], n[1], n[2], g.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                              len(g), flags, 0, None)
+    return rc, h
+
+
+@pytest.mark.parametrize("n,code", [((1, 8, 8), vloc.VLOC_ERR_SIZE), ((7, 8, 8), vloc.VLOC_ERR_SIZE),
+                                    ((8, 257, 8), vloc.VLOC_ERR_SIZE), ((8, 8, 14), vloc.VLOC_ERR_SIZE),
+                                    ((8, 8, 512), vloc.VLOC_ERR_SIZE)])
+def test_rejects_bad_grids(lib, n, code):
+    rc, _ = _create(lib, n, [[0, 0, 0]])
+    assert rc == code
+
+
+@pytest.mark.parametrize("g", [[[0, 0, 0], [0, 0, 0]], [[4, 0, 0]], [[0, -5, 0]], [[0, 0, 3]]])
+def test_rejects_bad_glists(lib, g):
+    rc, _ = _create(lib, (8, 9, 6), g)  # h in [-4, 3], k in [-4, 4], l in [-3, 2]
+    assert rc == vloc.VLOC_ERR_GLIST
+
+
+def test_rejects_bad_arguments(lib):
+    g = np.zeros((1, 3), dtype=np.int32)
+    gp = g.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
+    h = ctypes.c_void_p()
+    assert lib.vloc_plan_create(None, 8, 8, 8, gp, 1, vloc.VLOC_F32, 0, None) == vloc.VLOC_ERR_ARG
+    assert lib.vloc_plan_create(ctypes.byref(h), 8, 8, 8, None, 1, vloc.VLOC_F32, 0, None) == vloc.VLOC_ERR_ARG
+    assert lib.vloc_plan_create(ctypes.byref(h), 8, 8, 8, gp, 0, vloc.VLOC_F32, 0, None) == vloc.VLOC_ERR_GLIST
+    assert lib.vloc_plan_create(ctypes.byref(h), 8, 8, 8, gp, 1, 0, 0, None) == vloc.VLOC_ERR_ARG
+    assert lib.vloc_plan_create(ctypes.byref(h), 8, 8, 8, gp, 1, vloc.VLOC_F32 | vloc.VLOC_F64, 0, None) == vloc.VLOC_ERR_ARG
+    assert lib.vloc_plan_create(ctypes.byref(h), 8, 8, 8, gp, 1, vloc.VLOC_F32 | 0x8000, 0, None) == vloc.VLOC_ERR_ARG
+
+
+def test_host_only_plan_refuses_device_calls(lib):
+    rc, h = _create(lib, (8, 8, 8), synth.sphere_glist(8, 8, 8, 2))
+    assert rc == 0
+    assert lib.vloc_apply(h, ctypes.c_void_p(16), ctypes.c_void_p(16), 1, ctypes.c_void_p(16), None) == vloc.VLOC_ERR_STATE
+    assert lib.vloc_backward(h, None, None, None, 1, ctypes.c_void_p(16), None, None) == vloc.VLOC_ERR_STATE
+    assert lib.vloc_plan_destroy(h) == 0
+
+
+@pytest.mark.parametrize("n,R,order", [((24, 24, 24), 6, "canonical"), ((64, 64, 64), 16, "shuffled"),
+                                       ((96, 96, 120), 24, "canonical"), ((6, 5, 4), 2.0, "shuffled"),
+                                       ((96, 96, 96), 24, "shuffled")])
+def test_index_map_and_partition_bit_exact(lib, n, R, order):
+    import torch  # noqa: F401  (VlocPlan imports torch lazily)
+    g = synth.sphere_glist(*n, R, order=order, seed=7)
+    plan = vloc.VlocPlan(n, g, host_only=True)
+    assert np.array_equal(plan.index_map(), O.index_map(n, g))
+    ids, w = O.sticks(n, g)
+    info = plan.info()
+    assert info["nsticks"] == len(ids)
+    assert info["nplanes"] == len(np.unique(ids // n[1]))
+    part, P = plan.partition()
+    assert P == (len(ids) + 31) // 32
+    assert np.array_equal(part, O.greedy_partition(ids, w, P))
+    for kind, fn in (("basic", O.basic_partition), ("improved", O.improved_partition)):
+        p2 = vloc.VlocPlan(n, g, partition=kind, host_only=True)
+        part2, P2 = p2.partition()
+        assert P2 == P
+        assert np.array_equal(part2, fn(n, g, P))
+
+
+def test_radix_schedules(lib):
+    import torch  # noqa: F401
+    for n, rad in [(24, [6, 4]), (64, [8, 8]), (96, [12, 8]), (120, [12, 10]), (144, [12, 12]),
+                   (125, [5, 5, 5]), (16, [16]), (2, [2]), (256, [16, 16]), (243, [9, 9, 3])]:
+        plan = vloc.VlocPlan((n, 8, 8), [[0, 0, 0]], host_only=True)
+        assert plan.info()["radix"][0] == rad
+        assert int(np.prod(rad)) == n

@@ -1,0 +1,224 @@
+"""GPU parity of the CUDA path (through the C ABI) against the FP64 oracle.
+
+Tolerances (relative L2 per band, max over bands): 2e-6 for the FP32 path
+and 1e-12 for the FP64 path; the FP32 comparison feeds the oracle the same
+FP32-rounded inputs, upcast.  Integer work (index map, partition) is checked
+bit-exactly in test_abi_host.py.
+"""
+import numpy as np
+import pytest
+
+from helpers import TOL, make_case, oracle_apply, rel_l2_per_band
+from oracle import oracle as O
+from paper_1601_07378_gb300 import synth, vloc
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+DT = {"f32": (torch.complex64, torch.float32), "f64": (torch.complex128, torch.float64)}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_1601_07378_gb300.build import build
+    build()
+
+
+def run(n, g, c, V, prec, **kw):
+    cd, rd = DT[prec]
+    plan = vloc.VlocPlan(n, g, cd, **kw)
+    ct = torch.from_numpy(np.ascontiguousarray(c)).to("cuda", cd)
+    Vt = torch.from_numpy(np.ascontiguousarray(V)).to("cuda", rd)
+    out = plan.apply(ct, Vt)
+    torch.cuda.synchronize()
+    return plan, ct, Vt, out
+
+
+@pytest.mark.parametrize("prec", ["f32", "f64"])
+@pytest.mark.parametrize("n,R,nb,order", [
+    ((24, 24, 24), 6, 1, "canonical"),        # config 0 (ragged: 24 < one 32-line tile)
+    ((24, 24, 24), 6, 5, "shuffled"),
+    ((4, 6, 5), 2.2, 3, "shuffled"),          # tiny, odd radices
+    ((6, 5, 4), 2.0, 2, "canonical"),
+    ((8, 8, 8), 2.5, 2, "shuffled"),
+    ((20, 18, 22), 4, 3, "shuffled"),
+    ((40, 36, 50), 8, 3, "canonical"),        # several z tiles with a ragged tail
+    ((30, 45, 27), 7, 2, "shuffled"),         # radices 3, 5, 9, 15
+    ((64, 64, 64), 16, 4, "canonical"),
+])
+def test_apply_matches_oracle(prec, n, R, nb, order):
+    g, c, V = make_case(n, R, nb, seed=11, order=order, prec=prec)
+    _, _, _, out = run(n, g, c, V, prec)
+    err = rel_l2_per_band(out.cpu().numpy(), oracle_apply(n, g, c, V))
+    assert err.max() < TOL[prec], err.max()
+
+
+@pytest.mark.parametrize("prec", ["f32", "f64"])
+def test_config1_64cubed_256_bands_sampled(prec):
+    n, R, nb = (64, 64, 64), 16, 256
+    g, c, V = make_case(n, R, nb, seed=1, prec=prec)
+    _, _, _, out = run(n, g, c, V, prec)
+    bands = [0, 1, 77, 128, 200, 255]
+    err = rel_l2_per_band(out.cpu().numpy()[bands], oracle_apply(n, g, c, V, bands))
+    assert err.max() < TOL[prec], err.max()
+
+
+@pytest.mark.parametrize("prec", ["f32", "f64"])
+@pytest.mark.parametrize("n", [(96, 96, 120), (96, 96, 96)])
+def test_full_size_1024_bands_sampled(prec, n):
+    # The bench's launch configuration (default plan, 1024 bands), sampled
+    # bands from the first, middle and last workspace chunks.
+    R, nb = 24, 1024
+    g, c, V = make_case(n, R, nb, seed=2, prec=prec)
+    plan, _, _, out = run(n, g, c, V, prec)
+    chunk = plan.info()["chunk_bands"]
+    bands = sorted({0, chunk - 1, chunk, nb // 2, nb - 1})
+    err = rel_l2_per_band(out.cpu().numpy()[bands], oracle_apply(n, g, c, V, bands))
+    assert err.max() < TOL[prec], err.max()
+
+
+def test_chunk_boundaries_and_alias():
+    n, R, nb = (24, 20, 30), 5, 7
+    g, c, V = make_case(n, R, nb, seed=3, order="shuffled", prec="f64")
+    ref = oracle_apply(n, g, c, V)
+    for chunk in (1, 2, 3, 7, 100):
+        plan, ct, Vt, out = run(n, g, c, V, "f64", chunk=chunk)
+        assert plan.info()["chunk_bands"] == chunk
+        assert rel_l2_per_band(out.cpu().numpy(), ref).max() < TOL["f64"]
+        # exact alias out == coeffs
+        plan.apply(ct, Vt, out=ct)
+        torch.cuda.synchronize()
+        assert torch.equal(ct, out)
+
+
+def test_empty_batch_and_bad_arguments():
+    n = (16, 16, 16)
+    g, c, V = make_case(n, 4, 4, seed=4, prec="f32")
+    plan, ct, Vt, out = run(n, g, c, V, "f32")
+    e = torch.empty((0, len(g)), dtype=torch.complex64, device="cuda")
+    assert plan.apply(e, Vt).shape == (0, len(g))
+    with pytest.raises(vloc.VlocError) as ei:   # partial overlap of input and output
+        plan.apply(ct[:3], Vt, out=ct[1:])
+    assert ei.value.code == vloc.VLOC_ERR_ARG
+    lib = vloc.load()
+    assert lib.vloc_apply(plan.handle, vloc._ptr(ct), vloc._ptr(Vt), -1, vloc._ptr(out), None) == vloc.VLOC_ERR_ARG
+    assert lib.vloc_apply(plan.handle, None, vloc._ptr(Vt), 1, vloc._ptr(out), None) == vloc.VLOC_ERR_ARG
+    mis = torch.empty(2 * len(g) + 1, dtype=torch.float32, device="cuda")
+    assert lib.vloc_apply(plan.handle, mis.data_ptr() + 4, vloc._ptr(Vt), 1, vloc._ptr(out), None) == vloc.VLOC_ERR_ARG
+
+
+@pytest.mark.parametrize("prec", ["f32", "f64"])
+def test_non_sphere_lists(prec):
+    # Any G-list is accepted: a random subset of the cube (sticks with gaps),
+    # the strict-inequality sphere of Eq. 3, and every grid point.
+    rng = np.random.default_rng(5)
+    n = (8, 6, 10)
+    cube = np.array(np.meshgrid(np.arange(-4, 4), np.arange(-3, 3), np.arange(-5, 5), indexing="ij")).reshape(3, -1).T
+    for g in (cube[rng.random(len(cube)) < 0.3], cube[rng.permutation(len(cube))],
+              synth.sphere_glist(*n, 3, strict=True)):
+        g = np.ascontiguousarray(g.astype(np.int32))
+        c = synth.coefficients(g, 2, seed=6)
+        V, _ = synth.potential(*n, "smooth", seed=7)
+        if prec == "f32":
+            c, V = c.astype(np.complex64), V.astype(np.float32)
+        _, _, _, out = run(n, g, c, V, prec)
+        err = rel_l2_per_band(out.cpu().numpy(), oracle_apply(n, g, c, V))
+        assert err.max() < TOL[prec], err.max()
+
+
+def test_partitions_do_not_change_results():
+    n, R = (32, 32, 32), 8
+    g, c, V = make_case(n, R, 3, seed=8, prec="f32")
+    outs = [run(n, g, c, V, "f32", partition=k)[3] for k in ("greedy", "basic", "improved")]
+    assert torch.equal(outs[0], outs[1]) and torch.equal(outs[0], outs[2])
+
+
+@pytest.mark.parametrize("prec", ["f32", "f64"])
+def test_adjoint_and_hermiticity(prec):
+    n, R = (24, 30, 20), 6
+    g, c, V = make_case(n, R, 2, seed=9, order="shuffled", prec=prec)
+    plan, ct, Vt, out = run(n, g, c, V, prec)
+    adj = plan.apply(ct, Vt, adjoint=True)
+    torch.cuda.synchronize()
+    assert torch.equal(adj, out)
+    a = out.cpu().numpy().astype(np.complex128)
+    x = c.astype(np.complex128)
+    lhs = np.vdot(x[0], a[1])
+    rhs = np.vdot(a[0], x[1])
+    assert abs(lhs - rhs) < (1e-5 if prec == "f32" else 1e-13) * abs(lhs)
+
+
+def test_deterministic():
+    n, R = (48, 48, 48), 12
+    g, c, V = make_case(n, R, 6, seed=10, prec="f32")
+    plan, ct, Vt, out = run(n, g, c, V, "f32")
+    again = plan.apply(ct, Vt)
+    torch.cuda.synchronize()
+    assert torch.equal(out, again)
+
+
+@pytest.mark.parametrize("prec", ["f32", "f64"])
+def test_host_buffer_entry_matches_device_entry(prec):
+    n, R, nb = (32, 36, 40), 8, 13
+    g, c, V = make_case(n, R, nb, seed=12, prec=prec)
+    plan, ct, Vt, out = run(n, g, c, V, prec, chunk=4)
+    ch = ct.cpu().pin_memory()
+    Vh = Vt.cpu().pin_memory()
+    oh = plan.apply_host(ch, Vh)
+    assert torch.equal(oh, out.cpu())
+
+
+def test_batched_matches_individual():
+    cases = []
+    for i, m in enumerate([16, 24, 30]):
+        n = (m, m, m)
+        g, c, V = make_case(n, m / 4, 3 + i, seed=20 + i, prec="f32")
+        cases.append(run(n, g, c, V, "f32"))
+    outs = vloc.apply_batched([p for p, *_ in cases], [c for _, c, _, _ in cases], [V for _, _, V, _ in cases])
+    torch.cuda.synchronize()
+    for o, (_, _, _, ref) in zip(outs, cases):
+        assert torch.equal(o, ref)
+
+
+@pytest.mark.parametrize("prec", ["f32", "f64"])
+def test_backward_matches_oracle(prec):
+    n, R, nb = (32, 32, 32), 8, 3
+    g, c, V = make_case(n, R, nb, seed=4, prec=prec)
+    rng = np.random.default_rng(13)
+    gout = (rng.standard_normal(c.shape) + 1j * rng.standard_normal(c.shape)).astype(c.dtype)
+    plan, ct, Vt, _ = run(n, g, c, V, prec)
+    gt = torch.from_numpy(gout).to("cuda")
+    gc, gV = plan.backward(ct, gt, Vt)
+    torch.cuda.synchronize()
+    dc_ref, dV_ref = O.grads(n, g, c.astype(np.complex128), V.astype(np.float64), gout.astype(np.complex128))
+    assert rel_l2_per_band(gc.cpu().numpy(), dc_ref).max() < TOL[prec]
+    dV = gV.cpu().numpy().astype(np.float64)
+    assert np.linalg.norm(dV - dV_ref) / np.linalg.norm(dV_ref) < TOL[prec]
+
+
+def test_autograd_finite_differences_fp64():
+    # loss = sum_n <psi_n|V|psi_n> + ||V psi - t||^2 at 32^3 (R = 8), FP64.
+    n, R, nb = (32, 32, 32), 8, 2
+    g, c, V = make_case(n, R, nb, seed=14, prec="f64")
+    plan = vloc.VlocPlan(n, g, torch.complex128)
+    rng = np.random.default_rng(15)
+    t = torch.from_numpy(rng.standard_normal(c.shape) + 1j * rng.standard_normal(c.shape)).cuda() * 0.01
+    ct = torch.from_numpy(c).cuda().requires_grad_(True)
+    Vt = torch.from_numpy(V).cuda().requires_grad_(True)
+
+    def loss(cc, VV):
+        out = vloc.vloc_apply(cc, VV, plan)
+        return (torch.conj(cc) * out).real.sum() + ((out - t).abs() ** 2).sum()
+
+    L = loss(ct, Vt)
+    L.backward()
+    d = torch.from_numpy(rng.standard_normal(c.shape) + 1j * rng.standard_normal(c.shape)).cuda()
+    dv = torch.from_numpy(rng.standard_normal(V.shape)).cuda()
+    eps = 1e-6
+    with torch.no_grad():
+        fd_c = (loss(ct + eps * d, Vt) - loss(ct - eps * d, Vt)) / (2 * eps)
+        fd_v = (loss(ct, Vt + eps * dv) - loss(ct, Vt - eps * dv)) / (2 * eps)
+    an_c = (torch.conj(ct.grad) * d).real.sum()
+    an_v = (Vt.grad * dv).sum()
+    assert abs(fd_c - an_c) < 1e-7 * abs(an_c)
+    assert abs(fd_v - an_v) < 1e-7 * abs(an_v)
