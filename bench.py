@@ -245,6 +245,18 @@ def run_ours(args, rank, world, local_rank):
 
     stream = torch.cuda.current_stream()
     g = synth.sphere_glist(*GRID, R)
+    if args.only == "headline":
+        # profiler driver: the headline steps alone, nothing else
+        cdt, rdt = (torch.complex64, torch.float32) if args.prec == "f32" else (torch.complex128, torch.float64)
+        c_d = torch.from_numpy(synth.coefficients(g, NBANDS, seed=SEED)).to("cuda", cdt)
+        V_d = torch.from_numpy(synth.potential(*GRID, "smooth", SEED + 1000)[0]).to("cuda", rdt)
+        out_d = torch.empty_like(c_d)
+        plan = vloc.VlocPlan(GRID, g, cdt)
+        ms = time_steps(lambda: plan.apply(c_d, V_d, out=out_d), args.steps, args.warmup, stream, dist_on)
+        if rank == 0:
+            print(json.dumps({"only": "headline", "prec": args.prec, "bands": NBANDS, "steps": args.steps,
+                              "ms_per_step": ms / args.steps, "bands_per_s": world * NBANDS * args.steps / ms * 1e3}))
+        return
     c64 = synth.coefficients(g, NBANDS, seed=SEED + rank, dtype=np.complex64)
     V96 = synth.potential(*GRID, "smooth", SEED + 1000)[0]
     V120 = synth.potential(*GRID2, "smooth", SEED + 1000)[0]
@@ -392,6 +404,7 @@ def run_ours(args, rank, world, local_rank):
 
 
 def main():
+    global NBANDS
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=20)
@@ -399,9 +412,14 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-cufft", action="store_true", help="skip the torch.fft comparison")
+    ap.add_argument("--only", choices=["all", "headline"], default="all",
+                    help="headline: only the FP32 forward steps (for profiler launch lists)")
+    ap.add_argument("--bands", type=int, default=NBANDS, help="bands per GPU per step (default 1024)")
+    ap.add_argument("--prec", choices=["f32", "f64"], default="f32", help="precision of --only headline")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3
+    NBANDS = args.bands
     rank = env_int("RANK", 0)
     world = env_int("WORLD_SIZE", 1)
     local_rank = env_int("LOCAL_RANK", 0)

@@ -41,7 +41,7 @@ def run(n, g, c, V, prec, **kw):
     ((4, 6, 5), 2.2, 3, "shuffled"),          # tiny, odd radices
     ((6, 5, 4), 2.0, 2, "canonical"),
     ((8, 8, 8), 2.5, 2, "shuffled"),
-    ((20, 18, 22), 4, 3, "shuffled"),
+    ((20, 18, 25), 4, 3, "shuffled"),
     ((40, 36, 50), 8, 3, "canonical"),        # several z tiles with a ragged tail
     ((30, 45, 27), 7, 2, "shuffled"),         # radices 3, 5, 9, 15
     ((64, 64, 64), 16, 4, "canonical"),
