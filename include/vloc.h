@@ -179,6 +179,35 @@ int vloc_get_partition(vloc_plan plan, int32_t* stick_part, int32_t* nparts_out)
 /* vloc_get_info -- fill *info (host pointer). */
 int vloc_get_info(vloc_plan plan, vloc_info* info);
 
+/*
+ * vloc_apply_noalloc -- vloc_apply that allocates nothing.  The paper has no
+ * counterpart: this entry point exists for callers that cannot call
+ * cudaMalloc -- code running while another runtime owns the device's memory
+ * (a framework that reserves the GPU up front and forbids outside
+ * allocations), or a process that must not allocate after start-up.
+ * Instead of the plan's workspace it uses one fixed scratch array compiled
+ * into the library: 48 MiB of device memory per GPU that loads the library,
+ * held until the process exits.  The index tables and twiddles are rebuilt
+ * in that array from the plan's host-side data on every call, so `plan` may
+ * be a VLOC_HOST_ONLY plan (which made no CUDA call at all); together the
+ * two never allocate device memory.  The caller passes inputs and outputs as
+ * for vloc_apply (same layouts, alignment, alias and overlap rules).
+ *   Limit: the tables, twiddles and the workspace of at least one band must
+ *   fit in the 48 MiB (index tables at most 8 MiB); otherwise the call
+ *   returns VLOC_ERR_SIZE before doing any device work.  Bands are processed
+ *   in chunks that fit.
+ *   Set-up: the first call on each device looks up the array's device
+ *   address (with that device current); make that first call before any
+ *   stream capture.
+ *   Sharing: every call uses the same array and leaves its contents behind;
+ *   nothing in it needs to start at zero.  Calls that overlap on the GPU
+ *   (different streams, or interleaved work from several host threads) race
+ *   on the array and must be serialised by the caller.
+ * Errors: VLOC_ERR_ARG, VLOC_ERR_SIZE, VLOC_ERR_CUDA.
+ */
+int vloc_apply_noalloc(vloc_plan plan, const void* coeffs, const void* V, int64_t nbands, void* out,
+                       void* stream);
+
 /* ---- tracing --------------------------------------------------------------
  * Per-kernel timing with CUDA events recorded on the launching stream around
  * every kernel of a plan's calls, for the roofline and profile reports.

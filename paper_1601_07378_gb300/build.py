@@ -19,7 +19,7 @@ LIB = os.path.join(BUILD, "libvloc.so")
 ROOT = os.path.dirname(HERE)
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["kernels_f32.cu", "kernels_f64.cu", "kernels.cu", "plan.cpp"]
+SOURCES = ["kernels_f32.cu", "kernels_f64.cu", "kernels.cu", "plan.cpp", "noalloc.cu"]
 
 
 def _cuda_home() -> str:
@@ -63,7 +63,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
         if src.endswith(".cu"):
             cmd += cu_flags
         else:
-            cmd += ["-x", "cu" if False else "c++"]
+            cmd += ["-x", "c++"]
         cmd += ["-c", os.path.join(CSRC, src), "-o", obj]
         if verbose:
             print(" ".join(cmd), flush=True)

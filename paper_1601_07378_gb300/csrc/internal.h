@@ -78,3 +78,21 @@ size_t grad_smem_bytes(int dbl, int n);
 int set_smem_limits(int dbl, int nmax, int optin);
 
 }  // namespace vloc
+
+struct vloc_plan_s;
+
+namespace vloc {
+
+// Layout of a plan's int32 index tables in one contiguous block (offsets in
+// ints), as the kernels read them through DevTables.
+struct HostTableLayout {
+    size_t o_spp, o_pwu, o_pwz, o_row, o_pp, o_ps, o_plp, o_xr, total;
+    int S, P, NP;
+};
+
+// Rebuild a plan's index tables from its host-side data (any plan, including
+// host-only ones) into `blob` (capacity `cap` ints) without allocating.
+// Returns VLOC_OK, or VLOC_ERR_SIZE when `cap` is too small.
+int plan_host_tables(const vloc_plan_s* p, int* blob, size_t cap, HostTableLayout* lay);
+
+}  // namespace vloc

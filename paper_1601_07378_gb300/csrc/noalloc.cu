@@ -1,0 +1,134 @@
+// noalloc.cu -- vloc_apply_noalloc: the V_loc apply with no allocation.
+//
+// Some callers cannot call cudaMalloc: code that runs while another runtime
+// owns the device's memory (a framework that reserves the GPU's memory up
+// front and forbids outside allocations), or a process that must never
+// allocate after start-up.  For them this file holds the scratch the apply
+// needs -- index tables, twiddles, the cylinder and the slab -- in one
+// fixed, file-scope device array instead of the plan's workspace.  It works
+// with any plan, including a VLOC_HOST_ONLY plan (which itself made no CUDA
+// call), so the pair vloc_plan_create(VLOC_HOST_ONLY) + vloc_apply_noalloc
+// never allocates device memory.
+//
+// The array is kScratchBytes (48 MiB) per GPU that loads this library, held
+// until the process exits.  Every call shares it and leaves its contents
+// behind; nothing in it has to start at zero (every element is written
+// before it is read), so no clearing is needed.  Calls that overlap on the
+// GPU (two streams, or two host threads whose work interleaves) race on the
+// array: serialise them.
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <mutex>
+
+#include "../../include/vloc.h"
+#include "internal.h"
+
+namespace {
+
+constexpr size_t kScratchBytes = (size_t)48 << 20;   // device scratch per GPU
+constexpr size_t kTableInts = (size_t)2 << 20;       // index tables at most 8 MiB
+constexpr int kMaxDevices = 64;
+
+static __device__ __align__(256) unsigned char g_vloc_scratch[kScratchBytes];
+static int g_host_tables[kTableInts];   // host staging of the tables (static, not heap)
+
+std::mutex g_mu;
+void* g_scratch_addr[kMaxDevices] = {};  // device address of g_vloc_scratch, per device
+
+size_t up256(size_t x) { return (x + 255) & ~(size_t)255; }
+bool overlap(const void* a, size_t na, const void* b, size_t nb) {
+    const char *pa = (const char*)a, *pb = (const char*)b;
+    return pa < pb + nb && pb < pa + na;
+}
+
+}  // namespace
+
+extern "C" int vloc_apply_noalloc(vloc_plan plan, const void* coeffs, const void* V, int64_t nbands, void* out,
+                                  void* stream) {
+    using namespace vloc;
+    if (!plan || nbands < 0) return VLOC_ERR_ARG;
+    if (nbands == 0) return VLOC_OK;
+    if (!coeffs || !V || !out) return VLOC_ERR_ARG;
+    vloc_info info;
+    int rc = vloc_get_info(plan, &info);
+    if (rc) return rc;
+    const int dbl = info.precision == VLOC_F64;
+    const size_t elem = dbl ? 16 : 8, re = dbl ? 8 : 4;
+    if ((uintptr_t)coeffs % elem || (uintptr_t)out % elem || (uintptr_t)V % re) return VLOC_ERR_ARG;
+    const size_t bytes = (size_t)nbands * (size_t)info.npw * elem;
+    const long long N = (long long)info.n1 * info.n2 * info.n3;
+    if (coeffs != out && overlap(coeffs, bytes, out, bytes)) return VLOC_ERR_ARG;
+    if (overlap(V, (size_t)N * re, out, bytes)) return VLOC_ERR_ARG;
+
+    std::lock_guard<std::mutex> lock(g_mu);
+    cudaStream_t st = (cudaStream_t)stream;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return VLOC_ERR_CUDA;
+    if (dev < 0 || dev >= kMaxDevices) return VLOC_ERR_ARG;
+    // Set-up, once per device, with that device current: the host-side name
+    // g_vloc_scratch is only a stand-in, the kernels need the device address.
+    if (!g_scratch_addr[dev]) {
+        void* addr = nullptr;
+        e = cudaGetSymbolAddress(&addr, g_vloc_scratch);
+        if (e != cudaSuccess || !addr) return VLOC_ERR_CUDA;
+        g_scratch_addr[dev] = addr;
+    }
+    char* base = (char*)g_scratch_addr[dev];
+
+    // index tables -> static host staging -> scratch
+    HostTableLayout lay;
+    rc = plan_host_tables(plan, g_host_tables, kTableInts, &lay);
+    if (rc) return rc;
+    const size_t tab_bytes = up256(lay.total * sizeof(int));
+    const int ns[3] = {info.n1, info.n2, info.n3};
+    size_t tw_off[3], off = tab_bytes;
+    for (int a = 0; a < 3; ++a) { tw_off[a] = off; off += up256((size_t)ns[a] * elem); }
+    const size_t cyl_band = (size_t)lay.S * info.n3 * elem;
+    const size_t slab_band = (size_t)lay.NP * info.n2 * info.n3 * elem;
+    if (off + up256(cyl_band) + up256(slab_band) > kScratchBytes) return VLOC_ERR_SIZE;
+    long long chunk = 1;
+    while (chunk < 65535 && off + up256((size_t)(chunk + 1) * cyl_band) + up256((size_t)(chunk + 1) * slab_band) <= kScratchBytes)
+        ++chunk;
+    char* cyl = base + off;
+    char* slab = cyl + up256((size_t)chunk * cyl_band);
+
+    int optin = 0;
+    if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) return VLOC_ERR_CUDA;
+    int nmax = info.n1 > info.n2 ? info.n1 : info.n2;
+    if (info.n3 > nmax) nmax = info.n3;
+    if (smem_bytes_for(dbl, nmax) > (size_t)optin) return VLOC_ERR_SIZE;
+    if (set_smem_limits(dbl, nmax, optin)) return VLOC_ERR_CUDA;
+
+    if (cudaMemcpyAsync(base, g_host_tables, lay.total * sizeof(int), cudaMemcpyHostToDevice, st) != cudaSuccess)
+        return VLOC_ERR_CUDA;
+    for (int a = 0; a < 3; ++a)
+        if (launch_twiddles(dbl, base + tw_off[a], ns[a], st)) return VLOC_ERR_CUDA;
+
+    const int* tb = (const int*)base;
+    DevTables t;
+    t.stick_pw_ptr = tb + lay.o_spp; t.pw_user = tb + lay.o_pwu; t.pw_z = tb + lay.o_pwz;
+    t.stick_row = tb + lay.o_row; t.part_ptr = tb + lay.o_pp; t.part_sticks = tb + lay.o_ps;
+    t.plane_ptr = tb + lay.o_plp; t.xrow_plane = tb + lay.o_xr;
+    t.S = lay.S; t.P = lay.P; t.NP = lay.NP; t.n1 = info.n1; t.n2 = info.n2; t.n3 = info.n3; t.npw = info.npw;
+    LaunchAxes ax;
+    for (int a = 0; a < 3; ++a) {
+        ax.n[a] = ns[a];
+        ax.nst[a] = info.nstages[a];
+        for (int i = 0; i < 4; ++i) ax.radix[a][i] = info.radix[a][i];
+    }
+    const void* tw[3] = {base + tw_off[0], base + tw_off[1], base + tw_off[2]};
+    const size_t bstride = (size_t)info.npw * elem;
+    for (int64_t b0 = 0; b0 < nbands; b0 += chunk) {
+        const long long cb = nbands - b0 < chunk ? nbands - b0 : chunk;
+        const void* cc = (const char*)coeffs + b0 * bstride;
+        void* oo = (char*)out + b0 * bstride;
+        if (launch_k1_scatter_zpass(dbl, t, ax, tw[2], cc, cb, cyl, st)) return VLOC_ERR_CUDA;
+        if (launch_k2_ypass(dbl, +1, t, ax, tw[1], cb, cyl, slab, st)) return VLOC_ERR_CUDA;
+        if (launch_k3_xpass_v(dbl, t, ax, tw[0], V, cb, slab, st)) return VLOC_ERR_CUDA;
+        if (launch_k2_ypass(dbl, -1, t, ax, tw[1], cb, cyl, slab, st)) return VLOC_ERR_CUDA;
+        if (launch_k4_zpass_gather(dbl, t, ax, tw[2], cyl, cb, oo, st)) return VLOC_ERR_CUDA;
+    }
+    return VLOC_OK;
+}

@@ -629,3 +629,64 @@ int vloc_get_info(vloc_plan p, vloc_info* info) {
 }
 
 }  // extern "C"
+
+// Index tables rebuilt from the plan's host data (grid index per plane wave
+// and part per stick) into caller memory, with no allocation: plane waves
+// sorted by grid index, i.e. by (stick, z); sticks ascending; planes in
+// stick order; parts as dealt at plan creation.
+int vloc::plan_host_tables(const vloc_plan_s* p, int* blob, size_t cap, HostTableLayout* lay) {
+    if (!p || !blob || !lay) return VLOC_ERR_ARG;
+    const int S = p->S, P = p->P, NP = p->NP, n1 = p->n1, n2 = p->n2, n3 = p->n3;
+    const long long npw = p->npw;
+    HostTableLayout L;
+    L.S = S; L.P = P; L.NP = NP;
+    L.o_spp = 0;
+    L.o_pwu = L.o_spp + (size_t)S + 1;
+    L.o_pwz = L.o_pwu + (size_t)npw;
+    L.o_row = L.o_pwz + (size_t)npw;
+    L.o_pp = L.o_row + (size_t)S;
+    L.o_ps = L.o_pp + (size_t)P + 1;
+    L.o_plp = L.o_ps + (size_t)S;
+    L.o_xr = L.o_plp + (size_t)NP + 1;
+    L.total = L.o_xr + (size_t)n1;
+    if (L.total > cap) return VLOC_ERR_SIZE;
+    const int64_t* gi = p->grid_index.data();
+    int* spp = blob + L.o_spp;
+    int* pwu = blob + L.o_pwu;
+    int* pwz = blob + L.o_pwz;
+    int* row = blob + L.o_row;
+    int* pp = blob + L.o_pp;
+    int* ps = blob + L.o_ps;
+    int* plp = blob + L.o_plp;
+    int* xr = blob + L.o_xr;
+    for (long long q = 0; q < npw; ++q) pwu[q] = (int)q;
+    std::sort(pwu, pwu + npw, [gi](int a, int b) { return gi[a] < gi[b]; });
+    for (int x = 0; x < n1; ++x) xr[x] = -1;
+    int s = -1, np = 0;
+    long long prev = -1;
+    for (long long i = 0; i < npw; ++i) {
+        const long long g = gi[pwu[i]];
+        pwz[i] = (int)(g % n3);
+        const long long sid = g / n3;
+        if (sid != prev) {
+            ++s;
+            if (s >= S) return VLOC_ERR_ARG;
+            spp[s] = (int)i;
+            row[s] = (int)(sid % n2);
+            const int x = (int)(sid / n2);
+            if (xr[x] < 0) { xr[x] = np; plp[np++] = s; }
+            prev = sid;
+        }
+    }
+    if (s + 1 != S || np != NP) return VLOC_ERR_ARG;
+    spp[S] = (int)npw;
+    plp[NP] = S;
+    for (int k = 0; k <= P; ++k) pp[k] = 0;
+    for (int t = 0; t < S; ++t) pp[p->stick_part[t] + 1]++;
+    for (int k = 0; k < P; ++k) pp[k + 1] += pp[k];
+    for (int t = 0; t < S; ++t) ps[pp[p->stick_part[t]]++] = t;
+    for (int k = P; k > 0; --k) pp[k] = pp[k - 1];
+    pp[0] = 0;
+    *lay = L;
+    return VLOC_OK;
+}

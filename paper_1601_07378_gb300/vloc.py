@@ -39,7 +39,7 @@ EXPORTS = [
     "vloc_plan_create", "vloc_plan_destroy", "vloc_apply", "vloc_apply_adjoint", "vloc_backward",
     "vloc_apply_batched", "vloc_apply_host", "vloc_get_index_map", "vloc_get_partition",
     "vloc_get_info", "vloc_strerror", "vloc_version", "vloc_last_cuda_error",
-    "vloc_profile", "vloc_get_profile", "vloc_get_launch_count",
+    "vloc_profile", "vloc_get_profile", "vloc_get_launch_count", "vloc_apply_noalloc",
 ]
 
 KERNEL_NAMES = ["k1_scatter_zpass", "k2_ypass_inv", "k3_xpass_v", "k2_ypass_fwd", "k4_zpass_gather",
@@ -88,7 +88,7 @@ def load(path: str | None = None) -> ctypes.CDLL:
         vp, i64, i32, c_int = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_int
         lib.vloc_plan_create.argtypes = [ctypes.POINTER(vp), c_int, c_int, c_int, ctypes.POINTER(i32), i64, c_int, i64, vp]
         lib.vloc_plan_destroy.argtypes = [vp]
-        for f in (lib.vloc_apply, lib.vloc_apply_adjoint, lib.vloc_apply_host):
+        for f in (lib.vloc_apply, lib.vloc_apply_adjoint, lib.vloc_apply_host, lib.vloc_apply_noalloc):
             f.argtypes = [vp, vp, vp, i64, vp, vp]
         lib.vloc_backward.argtypes = [vp, vp, vp, vp, i64, vp, vp, vp]
         lib.vloc_apply_batched.argtypes = [c_int, ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(vp),
