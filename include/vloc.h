@@ -63,6 +63,9 @@ extern "C" {
 #define VLOC_PARTITION_BASIC    0x010  /* Sec. 4.1 cyclic row/column groups         */
 #define VLOC_PARTITION_IMPROVED 0x020  /* Sec. 4.2 plane-sorted row/column groups   */
 #define VLOC_GRAPH              0x100  /* replay apply chains as CUDA graphs        */
+#define VLOC_GENERIC_KERNELS    0x400  /* use the runtime-radix kernels for every   */
+                                       /* axis (the compile-time-length kernels are */
+                                       /* the default where one exists)             */
 #define VLOC_HOST_ONLY          0x200  /* build host tables only (no device memory, */
                                        /* no CUDA call); for introspection: the     */
                                        /* device calls then return VLOC_ERR_STATE   */
@@ -97,7 +100,8 @@ typedef struct vloc_info {
  *                may free it after the call.
  *   npw        : number of plane waves, >= 1.
  *   flags      : exactly one of VLOC_F32 / VLOC_F64, optionally one
- *                partition flag, VLOC_GRAPH and VLOC_HOST_ONLY.
+ *                partition flag, VLOC_GRAPH, VLOC_HOST_ONLY and
+ *                VLOC_GENERIC_KERNELS.
  *   max_bands_per_chunk : bands per workspace chunk (<= 0: automatic, sized
  *                to keep the chunk's intermediates in L2).
  *   stream     : stream used for the one-time table uploads (synchronised

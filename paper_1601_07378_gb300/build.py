@@ -19,7 +19,8 @@ LIB = os.path.join(BUILD, "libvloc.so")
 ROOT = os.path.dirname(HERE)
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["kernels_f32.cu", "kernels_f64.cu", "kernels.cu", "plan.cpp", "noalloc.cu"]
+SOURCES = ["kernels_ct_a.cu", "kernels_ct_b.cu", "kernels_ct_c.cu", "kernels_f32.cu", "kernels_f64.cu",
+           "kernels.cu", "plan.cpp", "noalloc.cu"]
 
 
 def _cuda_home() -> str:

@@ -1,0 +1,164 @@
+// fft_ct.cuh -- compile-time-sized Stockham stages (the fast path).
+//
+// Same algorithm as fft_core.cuh's runtime stages, but the transform length
+// N, each stage's radix R and stride Ns are template constants, so the index
+// arithmetic folds into immediates and every unit's registers are known at
+// compile time.  Two further differences:
+//  * one shared-memory buffer per tile: a stage that reads and writes the
+//    buffer first computes all of its warp's units into registers, waits at a
+//    barrier, then stores (halves the footprint, doubling resident CTAs);
+//  * `ct_stage<...>::compute` / `store` are separate so a kernel can chain
+//    the last inverse stage, a pointwise product and the first forward stage
+//    of the reverse schedule in registers (the forward's first radix equals
+//    the inverse's last, so a unit holds exactly the same elements).
+#pragma once
+
+#include "fft_core.cuh"
+
+namespace vloc {
+
+struct Radices {
+    int nst;
+    int r[kMaxStages];
+};
+
+// Compile-time copy of the host planner: fewest stages, then the smallest
+// largest radix, then larger radices first (radix set of fft_core.cuh).
+constexpr int kRadixSet[11] = {16, 15, 12, 10, 9, 8, 6, 5, 4, 3, 2};
+constexpr bool radices_better(const int* a, const int* b, int k) {
+    int ma = 0, mb = 0;
+    for (int i = 0; i < k; ++i) { ma = a[i] > ma ? a[i] : ma; mb = b[i] > mb ? b[i] : mb; }
+    if (ma != mb) return ma < mb;
+    for (int i = 0; i < k; ++i)
+        if (a[i] != b[i]) return a[i] > b[i];
+    return false;
+}
+constexpr Radices plan_ct(int n) {
+    Radices best{0, {0, 0, 0, 0}};
+    for (int i = 0; i < 11; ++i)
+        if (kRadixSet[i] == n) { best.nst = 1; best.r[0] = n; return best; }
+    for (int k = 2; k <= 4; ++k) {
+        int idx[4] = {0, 0, 0, 0};
+        bool found = false;
+        while (true) {
+            long long prod = 1;
+            int c[4] = {0, 0, 0, 0};
+            for (int i = 0; i < k; ++i) { c[i] = kRadixSet[idx[i]]; prod *= c[i]; }
+            if (prod == n && (!found || radices_better(c, best.r, k))) {
+                found = true;
+                best.nst = k;
+                for (int i = 0; i < 4; ++i) best.r[i] = i < k ? c[i] : 0;
+            }
+            int i = k - 1;
+            while (i >= 0 && ++idx[i] == 11) { idx[i] = 0; --i; }
+            if (i < 0) break;
+        }
+        if (found) return best;
+    }
+    return best;
+}
+
+template <int N> struct Sched {
+    static constexpr Radices P = plan_ct(N);
+    static constexpr int nst = P.nst;
+    static_assert(P.nst > 0, "length must be 2/3/5-smooth and <= 4 stages");
+    // radix and stride of stage s of the inverse (natural) schedule
+    static constexpr int R(int s) { return P.r[s]; }
+    static constexpr int NS(int s) { int p = 1; for (int i = 0; i < s; ++i) p *= P.r[i]; return p; }
+    // reversed schedule (used for the forward transform chained after the inverse)
+    static constexpr int RR(int s) { return P.r[P.nst - 1 - s]; }
+    static constexpr int NSR(int s) { int p = 1; for (int i = 0; i < s; ++i) p *= P.r[P.nst - 1 - i]; return p; }
+};
+
+// One compile-time Stockham stage over a 32-line tile held across lanes,
+// units spread over the CTA's warps.
+template <int N, int R, int NS, int S, int W> struct CtStage {
+    static constexpr int NI = N / R;
+    static constexpr int U = (NI + W - 1) / W;
+    static constexpr int TWS = N / (NS * R);
+
+    template <typename V, class Src>
+    __device__ __forceinline__ static void compute(V (&h)[U][R], const V* __restrict__ tw, const Src& src, int lane,
+                                                  int warp) {
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int i = warp + u * W;
+            if (NI % W == 0 || i < NI) {
+#pragma unroll
+                for (int r = 0; r < R; ++r) h[u][r] = src(i + r * NI, lane);
+                if constexpr (NS > 1) {
+                    const int base = (i % NS) * TWS;
+#pragma unroll
+                    for (int r = 1; r < R; ++r) {
+                        const V w = tw[r * base];
+                        h[u][r] = S > 0 ? cmul(h[u][r], w) : cmulc(h[u][r], w);
+                    }
+                }
+                Dft<R, S>::run(h[u]);
+            }
+        }
+    }
+
+    template <typename V, class Dst>
+    __device__ __forceinline__ static void store(const V (&h)[U][R], const Dst& dst, int lane, int warp) {
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int i = warp + u * W;
+            if (NI % W == 0 || i < NI) {
+                const int k = i % NS;
+                const int j = (i - k) * R + k;
+#pragma unroll
+                for (int r = 0; r < R; ++r) dst(j + r * NS, lane, h[u][r]);
+            }
+        }
+    }
+
+    // compute + store; `hold` puts a CTA barrier between them (the stage
+    // reads and writes the same shared buffer).
+    template <bool HOLD, typename V, class Src, class Dst>
+    __device__ __forceinline__ static void run(const V* __restrict__ tw, const Src& src, const Dst& dst, int lane,
+                                              int warp, bool act) {
+        V h[U][R];
+        if (act) compute(h, tw, src, lane, warp);
+        if constexpr (HOLD) __syncthreads();
+        if (act) store(h, dst, lane, warp);
+    }
+};
+
+// Stage s of the natural (sign S) schedule of length N.
+template <int N, int S, int W, int s> using NatStage = CtStage<N, Sched<N>::R(s), Sched<N>::NS(s), S, W>;
+// Stage s of the reversed schedule.
+template <int N, int S, int W, int s> using RevStage = CtStage<N, Sched<N>::RR(s), Sched<N>::NSR(s), S, W>;
+
+// Full transform with one shared buffer `buf` ([N][kLd]).  `in` may be
+// global or `buf` itself (IN_BUF), `out` may be global or `buf` (OUT_BUF).
+// The caller provides a barrier before the call if `buf` was in use; the
+// call ends without a barrier.
+template <int N, int S, int W, bool REV, bool IN_BUF, bool OUT_BUF, typename V, class In, class Out>
+__device__ __forceinline__ void fft_ct(const V* __restrict__ tw, const In& in, const Out& out, V* buf, int lane,
+                                       int warp, bool act) {
+    constexpr int nst = Sched<N>::nst;
+    Smem<V> sb{buf};
+    auto stage = [&](auto sc, const auto& src, const auto& dst, auto hold) {
+        constexpr int s = decltype(sc)::value;
+        using St = std::conditional_t<REV, RevStage<N, S, W, s>, NatStage<N, S, W, s>>;
+        St::template run<decltype(hold)::value>(tw, src, dst, lane, warp, act);
+    };
+    if constexpr (nst == 1) {
+        stage(std::integral_constant<int, 0>{}, in, out, std::integral_constant<bool, IN_BUF && OUT_BUF>{});
+    } else {
+        stage(std::integral_constant<int, 0>{}, in, sb, std::integral_constant<bool, IN_BUF>{});
+        __syncthreads();
+        if constexpr (nst >= 3) {
+            stage(std::integral_constant<int, 1>{}, sb, sb, std::true_type{});
+            __syncthreads();
+        }
+        if constexpr (nst >= 4) {
+            stage(std::integral_constant<int, 2>{}, sb, sb, std::true_type{});
+            __syncthreads();
+        }
+        stage(std::integral_constant<int, nst - 1>{}, sb, out, std::integral_constant<bool, OUT_BUF>{});
+    }
+}
+
+}  // namespace vloc

@@ -8,20 +8,21 @@
 namespace vloc {
 
 
-// Device-resident index tables of one plan (all int32, one allocation).
+// Device-resident index tables of one plan (int32, one allocation).
 //  Sticks are the occupied (h mod n1, k mod n2) z-columns in ascending
-//  id (h mod n1) * n2 + (k mod n2) order ("canonical"); plane waves are
-//  sorted by (stick, l).  Planes are the occupied h mod n1 values.
+//  id (h mod n1) * n2 + (k mod n2) order ("canonical"); planes are the
+//  occupied h mod n1 values.  A tile is a run of at most 32 sticks of one
+//  partition part (one z-pass CTA); its plane waves form a flat list of
+//  {caller index, z | line << 16} entries, sticks in tile order, l ascending.
 struct DevTables {
-    const int* stick_pw_ptr;  // [S+1] first canonical plane wave of each stick
-    const int* pw_user;       // [npw] caller's index of the q-th canonical plane wave
-    const int* pw_z;          // [npw] l mod n3
     const int* stick_row;     // [S]   k mod n2
-    const int* part_ptr;      // [P+1] sticks of each part in part_sticks
-    const int* part_sticks;   // [S]   canonical stick ids, part by part
+    const int* tile_ptr;      // [T+1] sticks of each tile in tile_sticks
+    const int* tile_sticks;   // [S]   canonical stick ids, tile by tile
+    const int* tile_pw_ptr;   // [T+1] plane-wave entries of each tile
+    const int2* tile_pw;      // [npw] {caller index, z | line << 16}
     const int* plane_ptr;     // [NP+1] canonical stick range of each plane
     const int* xrow_plane;    // [n1]  plane index of x = h mod n1, or -1
-    int S, P, NP;
+    int S, T, NP;
     int n1, n2, n3;
     long long npw;
 };
@@ -59,15 +60,26 @@ template <typename T> struct Launch {
 extern template struct Launch<float>;
 extern template struct Launch<double>;
 
-// Precision dispatch (kernels.cu): dbl = 0 for float, 1 for double.
+// Compile-time-length launchers (kernels_ct.cuh), instantiated for the axis
+// lengths of VLOC_CT_SIZES in kernels_ct_*.cu (FP32).
+#define VLOC_CT_SIZES(X) X(24) X(32) X(48) X(60) X(64) X(72) X(80) X(96) X(100) X(120) X(128) X(144)
+template <typename T, int N> struct LaunchCT {
+    static int k1(const DevTables& t, const void* tw3, const void* coeffs, long long nb, void* cyl, cudaStream_t st);
+    static int k2(int sign, const DevTables& t, const void* tw2, long long nb, void* cyl, void* slab, cudaStream_t st);
+    static int k3(const DevTables& t, const void* tw1, const void* V, long long nb, void* slab, cudaStream_t st);
+    static int k4(const DevTables& t, const void* tw3, const void* cyl, long long nb, void* out, cudaStream_t st);
+};
+
+// Precision dispatch (kernels.cu): dbl = 0 for float, 1 for double; `fast`
+// selects the compile-time-length kernels when one exists for the axis.
 int launch_twiddles(int dbl, void* tw, int n, cudaStream_t st);
-int launch_k1_scatter_zpass(int dbl, const DevTables& t, const LaunchAxes& ax, const void* tw3, const void* coeffs,
+int launch_k1_scatter_zpass(int dbl, int fast, const DevTables& t, const LaunchAxes& ax, const void* tw3, const void* coeffs,
                             long long nb, void* cyl, cudaStream_t st);
-int launch_k2_ypass(int dbl, int sign, const DevTables& t, const LaunchAxes& ax, const void* tw2, long long nb,
+int launch_k2_ypass(int dbl, int fast, int sign, const DevTables& t, const LaunchAxes& ax, const void* tw2, long long nb,
                     void* cyl, void* slab, cudaStream_t st);
-int launch_k3_xpass_v(int dbl, const DevTables& t, const LaunchAxes& ax, const void* tw1, const void* V,
+int launch_k3_xpass_v(int dbl, int fast, const DevTables& t, const LaunchAxes& ax, const void* tw1, const void* V,
                       long long nb, void* slab, cudaStream_t st);
-int launch_k4_zpass_gather(int dbl, const DevTables& t, const LaunchAxes& ax, const void* tw3, const void* cyl,
+int launch_k4_zpass_gather(int dbl, int fast, const DevTables& t, const LaunchAxes& ax, const void* tw3, const void* cyl,
                            long long nb, void* out, cudaStream_t st);
 int launch_k3b_grad_v(int dbl, const DevTables& t, const LaunchAxes& ax, const void* tw1, const void* slab_c,
                       const void* slab_g, long long nb, double* acc, cudaStream_t st);
@@ -86,11 +98,14 @@ namespace vloc {
 // Layout of a plan's int32 index tables in one contiguous block (offsets in
 // ints), as the kernels read them through DevTables.
 struct HostTableLayout {
-    size_t o_spp, o_pwu, o_pwz, o_row, o_pp, o_ps, o_plp, o_xr, total;
-    int S, P, NP;
+    size_t o_row, o_tp, o_ts, o_tpp, o_tpw, o_plp, o_xr, total;
+    int S, T, NP;
 };
 
-// Rebuild a plan's index tables from its host-side data (any plan, including
+// DevTables pointing into a device copy of the table block at `base`.
+DevTables device_tables(const int* base, const HostTableLayout& L, int n1, int n2, int n3, long long npw);
+
+// Copy a plan's index tables (kept on the host for any plan, including
 // host-only ones) into `blob` (capacity `cap` ints) without allocating.
 // Returns VLOC_OK, or VLOC_ERR_SIZE when `cap` is too small.
 int plan_host_tables(const vloc_plan_s* p, int* blob, size_t cap, HostTableLayout* lay);

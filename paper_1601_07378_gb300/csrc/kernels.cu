@@ -36,21 +36,55 @@ int set_smem_limits(int dbl, int nmax, int optin) {
 int launch_twiddles(int dbl, void* tw, int n, cudaStream_t st) {
     return dbl ? Launch<double>::twiddles(tw, n, st) : Launch<float>::twiddles(tw, n, st);
 }
-int launch_k1_scatter_zpass(int dbl, const DevTables& t, const LaunchAxes& ax, const void* tw3, const void* coeffs,
-                            long long nb, void* cyl, cudaStream_t st) {
+bool has_ct(int n) {
+    switch (n) {
+#define VLOC_CASE(N) case N:
+        VLOC_CT_SIZES(VLOC_CASE)
+#undef VLOC_CASE
+        return true;
+        default: return false;
+    }
+}
+
+int launch_k1_scatter_zpass(int dbl, int fast, const DevTables& t, const LaunchAxes& ax, const void* tw3,
+                            const void* coeffs, long long nb, void* cyl, cudaStream_t st) {
+    if (!dbl && fast) switch (t.n3) {
+#define VLOC_CASE(N) case N: return LaunchCT<float, N>::k1(t, tw3, coeffs, nb, cyl, st);
+        VLOC_CT_SIZES(VLOC_CASE)
+#undef VLOC_CASE
+        default: break;
+    }
     return dbl ? Launch<double>::k1(t, ax, tw3, coeffs, nb, cyl, st) : Launch<float>::k1(t, ax, tw3, coeffs, nb, cyl, st);
 }
-int launch_k2_ypass(int dbl, int sign, const DevTables& t, const LaunchAxes& ax, const void* tw2, long long nb,
-                    void* cyl, void* slab, cudaStream_t st) {
+int launch_k2_ypass(int dbl, int fast, int sign, const DevTables& t, const LaunchAxes& ax, const void* tw2,
+                    long long nb, void* cyl, void* slab, cudaStream_t st) {
+    if (!dbl && fast) switch (t.n2) {
+#define VLOC_CASE(N) case N: return LaunchCT<float, N>::k2(sign, t, tw2, nb, cyl, slab, st);
+        VLOC_CT_SIZES(VLOC_CASE)
+#undef VLOC_CASE
+        default: break;
+    }
     return dbl ? Launch<double>::k2(sign, t, ax, tw2, nb, cyl, slab, st)
                : Launch<float>::k2(sign, t, ax, tw2, nb, cyl, slab, st);
 }
-int launch_k3_xpass_v(int dbl, const DevTables& t, const LaunchAxes& ax, const void* tw1, const void* V,
+int launch_k3_xpass_v(int dbl, int fast, const DevTables& t, const LaunchAxes& ax, const void* tw1, const void* V,
                       long long nb, void* slab, cudaStream_t st) {
+    if (!dbl && fast) switch (t.n1) {
+#define VLOC_CASE(N) case N: return LaunchCT<float, N>::k3(t, tw1, V, nb, slab, st);
+        VLOC_CT_SIZES(VLOC_CASE)
+#undef VLOC_CASE
+        default: break;
+    }
     return dbl ? Launch<double>::k3(t, ax, tw1, V, nb, slab, st) : Launch<float>::k3(t, ax, tw1, V, nb, slab, st);
 }
-int launch_k4_zpass_gather(int dbl, const DevTables& t, const LaunchAxes& ax, const void* tw3, const void* cyl,
-                           long long nb, void* out, cudaStream_t st) {
+int launch_k4_zpass_gather(int dbl, int fast, const DevTables& t, const LaunchAxes& ax, const void* tw3,
+                           const void* cyl, long long nb, void* out, cudaStream_t st) {
+    if (!dbl && fast) switch (t.n3) {
+#define VLOC_CASE(N) case N: return LaunchCT<float, N>::k4(t, tw3, cyl, nb, out, st);
+        VLOC_CT_SIZES(VLOC_CASE)
+#undef VLOC_CASE
+        default: break;
+    }
     return dbl ? Launch<double>::k4(t, ax, tw3, cyl, nb, out, st) : Launch<float>::k4(t, ax, tw3, cyl, nb, out, st);
 }
 int launch_k3b_grad_v(int dbl, const DevTables& t, const LaunchAxes& ax, const void* tw1, const void* slab_c,

@@ -40,6 +40,73 @@ template <typename T> __device__ __forceinline__ void load_tw(V2<T>* stw, const 
     for (int j = threadIdx.x; j < n; j += kThreads) stw[j] = tw[j];
 }
 
+// ------------------------------------------------------------- tile I/O
+// Flat, batched loops over a tile's plane-wave entries and stick rows: each
+// thread issues its independent loads before the dependent stores, so a CTA
+// keeps many requests in flight instead of walking one stick at a time.
+constexpr int kBatch = 4;
+
+template <typename V>
+__device__ __forceinline__ void scatter_entries(const int2* __restrict__ ent, int e0, int e1, const V* __restrict__ c,
+                                                V* buf) {
+    for (int base = e0 + (int)threadIdx.x; base < e1; base += kBatch * kThreads) {
+        int2 en[kBatch];
+        V val[kBatch];
+#pragma unroll
+        for (int u = 0; u < kBatch; ++u) {
+            const int e = base + u * kThreads;
+            en[u] = e < e1 ? ent[e] : make_int2(0, -1);
+        }
+#pragma unroll
+        for (int u = 0; u < kBatch; ++u) val[u] = en[u].y >= 0 ? c[en[u].x] : czero<V>();
+#pragma unroll
+        for (int u = 0; u < kBatch; ++u)
+            if (en[u].y >= 0) buf[(en[u].y & 0xffff) * kLd + (en[u].y >> 16)] = val[u];
+    }
+}
+
+template <typename V, typename T>
+__device__ __forceinline__ void gather_entries(const int2* __restrict__ ent, int e0, int e1, const V* buf,
+                                               V* __restrict__ o, T scale) {
+    for (int e = e0 + (int)threadIdx.x; e < e1; e += kThreads) {
+        const int2 en = ent[e];
+        o[en.x] = cscale(buf[(en.y & 0xffff) * kLd + (en.y >> 16)], scale);
+    }
+}
+
+// rows of a tile: line l <-> stick sticks[l], element z of that stick's row
+template <typename V>
+__device__ __forceinline__ void rows_out(const V* buf, V* __restrict__ cb, const int* sticks, int lines, int n) {
+    const int total = lines * n;
+    for (int i = threadIdx.x; i < total; i += kThreads) {
+        const int l = i / n, z = i - l * n;
+        cb[(long long)sticks[l] * n + z] = buf[z * kLd + l];
+    }
+}
+template <typename V>
+__device__ __forceinline__ void rows_in(V* buf, const V* __restrict__ cb, const int* sticks, int lines, int n) {
+    const int total = lines * n;
+    for (int base = threadIdx.x; base < total; base += kBatch * kThreads) {
+        V val[kBatch];
+#pragma unroll
+        for (int u = 0; u < kBatch; ++u) {
+            const int i = base + u * kThreads;
+            if (i < total) {
+                const int l = i / n, z = i - l * n;
+                val[u] = cb[(long long)sticks[l] * n + z];
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < kBatch; ++u) {
+            const int i = base + u * kThreads;
+            if (i < total) {
+                const int l = i / n, z = i - l * n;
+                buf[z * kLd + l] = val[u];
+            }
+        }
+    }
+}
+
 // ------------------------------------------------------------------ K1
 template <typename T>
 __global__ void __launch_bounds__(kThreads) k1_scatter_zpass(DevTables t, AxisPlan az, const V2<T>* __restrict__ tw3,
@@ -50,33 +117,18 @@ __global__ void __launch_bounds__(kThreads) k1_scatter_zpass(DevTables t, AxisPl
     V* P = reinterpret_cast<V*>(smem_raw);
     V* Q = P + n3 * kLd;
     V* stw = Q + n3 * kLd;
-    const int part = blockIdx.x;
+    const int tile = blockIdx.x;
     const long long b = blockIdx.y;
-    const V* c = coeffs + b * t.npw;
-    V* cb = cyl + b * (long long)t.S * n3;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     load_tw<T>(stw, tw3, n3);
-    const int s0 = t.part_ptr[part], ns = t.part_ptr[part + 1] - s0;
-    for (int batch = 0; batch < ns; batch += kLines) {
-        const int lines = min(kLines, ns - batch);
-        for (int i = threadIdx.x; i < n3 * kLd; i += kThreads) Q[i] = czero<V>();
-        __syncthreads();
-        for (int l = warp; l < lines; l += kWarps) {
-            const int s = t.part_sticks[s0 + batch + l];
-            const int q1 = t.stick_pw_ptr[s + 1];
-            for (int q = t.stick_pw_ptr[s] + lane; q < q1; q += 32) Q[t.pw_z[q] * kLd + l] = c[t.pw_user[q]];
-        }
-        __syncthreads();
-        V* D = final_buf(az.nst, P, Q);
-        fft_lines<+1>(az, stw, Smem<V>{Q}, Smem<V>{D}, P, Q, lines);
-        __syncthreads();
-        for (int l = warp; l < lines; l += kWarps) {
-            const int s = t.part_sticks[s0 + batch + l];
-            V* row = cb + (long long)s * n3;
-            for (int z = lane; z < n3; z += 32) row[z] = D[z * kLd + l];
-        }
-        __syncthreads();
-    }
+    const int s0 = t.tile_ptr[tile], lines = t.tile_ptr[tile + 1] - s0;
+    for (int i = threadIdx.x; i < n3 * kLd; i += kThreads) Q[i] = czero<V>();
+    __syncthreads();
+    scatter_entries(t.tile_pw, t.tile_pw_ptr[tile], t.tile_pw_ptr[tile + 1], coeffs + b * t.npw, Q);
+    __syncthreads();
+    V* D = final_buf(az.nst, P, Q);
+    fft_lines<+1>(az, stw, Smem<V>{Q}, Smem<V>{D}, P, Q, lines);
+    __syncthreads();
+    rows_out(D, cyl + b * (long long)t.S * n3, t.tile_sticks + s0, lines, n3);
 }
 
 // ------------------------------------------------------------------ K2
@@ -186,30 +238,16 @@ __global__ void __launch_bounds__(kThreads) k4_zpass_gather(DevTables t, AxisPla
     V* P = reinterpret_cast<V*>(smem_raw);
     V* Q = P + n3 * kLd;
     V* stw = Q + n3 * kLd;
-    const int part = blockIdx.x;
+    const int tile = blockIdx.x;
     const long long b = blockIdx.y;
-    V* o = out + b * t.npw;
-    const V* cb = cyl + b * (long long)t.S * n3;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     load_tw<T>(stw, tw3, n3);
-    const int s0 = t.part_ptr[part], ns = t.part_ptr[part + 1] - s0;
-    for (int batch = 0; batch < ns; batch += kLines) {
-        const int lines = min(kLines, ns - batch);
-        for (int l = warp; l < lines; l += kWarps) {
-            const V* row = cb + (long long)t.part_sticks[s0 + batch + l] * n3;
-            for (int z = lane; z < n3; z += 32) Q[z * kLd + l] = row[z];
-        }
-        __syncthreads();
-        V* D = final_buf(az.nst, P, Q);
-        fft_lines<-1>(az, stw, Smem<V>{Q}, Smem<V>{D}, P, Q, lines);
-        __syncthreads();
-        for (int l = warp; l < lines; l += kWarps) {
-            const int s = t.part_sticks[s0 + batch + l];
-            const int q1 = t.stick_pw_ptr[s + 1];
-            for (int q = t.stick_pw_ptr[s] + lane; q < q1; q += 32) o[t.pw_user[q]] = cscale(D[t.pw_z[q] * kLd + l], scale);
-        }
-        __syncthreads();
-    }
+    const int s0 = t.tile_ptr[tile], lines = t.tile_ptr[tile + 1] - s0;
+    rows_in(Q, cyl + b * (long long)t.S * n3, t.tile_sticks + s0, lines, n3);
+    __syncthreads();
+    V* D = final_buf(az.nst, P, Q);
+    fft_lines<-1>(az, stw, Smem<V>{Q}, Smem<V>{D}, P, Q, lines);
+    __syncthreads();
+    gather_entries(t.tile_pw, t.tile_pw_ptr[tile], t.tile_pw_ptr[tile + 1], D, out + b * t.npw, scale);
 }
 
 // ----------------------------------------------------------- K3b (dL/dV)
@@ -309,7 +347,7 @@ template <typename T> int Launch<T>::twiddles(void* tw, int n, cudaStream_t st) 
 template <typename T>
 int Launch<T>::k1(const DevTables& t, const LaunchAxes& ax, const void* tw3, const void* coeffs, long long nb, void* cyl,
                   cudaStream_t st) {
-    k1_scatter_zpass<T><<<dim3(t.P, (unsigned)nb), kThreads, smem(t.n3), st>>>(t, axis_of(ax, 2), (const V2<T>*)tw3,
+    k1_scatter_zpass<T><<<dim3(t.T, (unsigned)nb), kThreads, smem(t.n3), st>>>(t, axis_of(ax, 2), (const V2<T>*)tw3,
                                                                                (const V2<T>*)coeffs, (V2<T>*)cyl);
     return (int)cudaGetLastError();
 }
@@ -334,7 +372,7 @@ template <typename T>
 int Launch<T>::k4(const DevTables& t, const LaunchAxes& ax, const void* tw3, const void* cyl, long long nb, void* out,
                   cudaStream_t st) {
     const T scale = (T)(1.0 / ((double)t.n1 * t.n2 * t.n3));
-    k4_zpass_gather<T><<<dim3(t.P, (unsigned)nb), kThreads, smem(t.n3), st>>>(
+    k4_zpass_gather<T><<<dim3(t.T, (unsigned)nb), kThreads, smem(t.n3), st>>>(
         t, axis_of(ax, 2), (const V2<T>*)tw3, (const V2<T>*)cyl, (V2<T>*)out, scale);
     return (int)cudaGetLastError();
 }

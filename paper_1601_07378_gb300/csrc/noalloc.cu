@@ -106,12 +106,7 @@ extern "C" int vloc_apply_noalloc(vloc_plan plan, const void* coeffs, const void
     for (int a = 0; a < 3; ++a)
         if (launch_twiddles(dbl, base + tw_off[a], ns[a], st)) return VLOC_ERR_CUDA;
 
-    const int* tb = (const int*)base;
-    DevTables t;
-    t.stick_pw_ptr = tb + lay.o_spp; t.pw_user = tb + lay.o_pwu; t.pw_z = tb + lay.o_pwz;
-    t.stick_row = tb + lay.o_row; t.part_ptr = tb + lay.o_pp; t.part_sticks = tb + lay.o_ps;
-    t.plane_ptr = tb + lay.o_plp; t.xrow_plane = tb + lay.o_xr;
-    t.S = lay.S; t.P = lay.P; t.NP = lay.NP; t.n1 = info.n1; t.n2 = info.n2; t.n3 = info.n3; t.npw = info.npw;
+    const DevTables t = device_tables((const int*)base, lay, info.n1, info.n2, info.n3, info.npw);
     LaunchAxes ax;
     for (int a = 0; a < 3; ++a) {
         ax.n[a] = ns[a];
@@ -124,11 +119,11 @@ extern "C" int vloc_apply_noalloc(vloc_plan plan, const void* coeffs, const void
         const long long cb = nbands - b0 < chunk ? nbands - b0 : chunk;
         const void* cc = (const char*)coeffs + b0 * bstride;
         void* oo = (char*)out + b0 * bstride;
-        if (launch_k1_scatter_zpass(dbl, t, ax, tw[2], cc, cb, cyl, st)) return VLOC_ERR_CUDA;
-        if (launch_k2_ypass(dbl, +1, t, ax, tw[1], cb, cyl, slab, st)) return VLOC_ERR_CUDA;
-        if (launch_k3_xpass_v(dbl, t, ax, tw[0], V, cb, slab, st)) return VLOC_ERR_CUDA;
-        if (launch_k2_ypass(dbl, -1, t, ax, tw[1], cb, cyl, slab, st)) return VLOC_ERR_CUDA;
-        if (launch_k4_zpass_gather(dbl, t, ax, tw[2], cyl, cb, oo, st)) return VLOC_ERR_CUDA;
+        if (launch_k1_scatter_zpass(dbl, 1, t, ax, tw[2], cc, cb, cyl, st)) return VLOC_ERR_CUDA;
+        if (launch_k2_ypass(dbl, 1, +1, t, ax, tw[1], cb, cyl, slab, st)) return VLOC_ERR_CUDA;
+        if (launch_k3_xpass_v(dbl, 1, t, ax, tw[0], V, cb, slab, st)) return VLOC_ERR_CUDA;
+        if (launch_k2_ypass(dbl, 1, -1, t, ax, tw[1], cb, cyl, slab, st)) return VLOC_ERR_CUDA;
+        if (launch_k4_zpass_gather(dbl, 1, t, ax, tw[2], cyl, cb, oo, st)) return VLOC_ERR_CUDA;
     }
     return VLOC_OK;
 }

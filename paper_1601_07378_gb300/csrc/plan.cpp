@@ -99,12 +99,15 @@ void process_grid(int p, int* m, int* n) {
 struct vloc_plan_s {
     int n1 = 0, n2 = 0, n3 = 0, dbl = 0, flags = 0;
     long long npw = 0, N = 0;
-    int S = 0, NP = 0, P = 0;
+    int S = 0, NP = 0, P = 0, T = 0;
+    int fast = 1;  // compile-time-length kernels where available
     long long chunk = 1, ws_bands = 2;
     size_t elem = 8;
     LaunchAxes ax{};
     std::vector<int64_t> grid_index;  // caller order
     std::vector<int32_t> stick_part;  // canonical stick order
+    std::vector<int> host_tables;     // index tables as uploaded (layout `lay`)
+    HostTableLayout lay{};
     // device
     int* d_tables = nullptr;
     DevTables dt{};
@@ -174,7 +177,7 @@ int vloc_plan_create(vloc_plan* out, int n1, int n2, int n3, const int32_t* g, i
     const int part_flag = flags & 0x0F0;
     if (part_flag != VLOC_PARTITION_GREEDY && part_flag != VLOC_PARTITION_BASIC && part_flag != VLOC_PARTITION_IMPROVED)
         return VLOC_ERR_ARG;
-    if (flags & ~(0x003 | 0x0F0 | VLOC_GRAPH | VLOC_HOST_ONLY)) return VLOC_ERR_ARG;
+    if (flags & ~(0x003 | 0x0F0 | VLOC_GRAPH | VLOC_HOST_ONLY | VLOC_GENERIC_KERNELS)) return VLOC_ERR_ARG;
     const bool host_only = (flags & VLOC_HOST_ONLY) != 0;
     const int ns[3] = {n1, n2, n3};
     for (int a = 0; a < 3; ++a)
@@ -189,6 +192,7 @@ int vloc_plan_create(vloc_plan* out, int n1, int n2, int n3, const int32_t* g, i
     if (!p) return VLOC_ERR_ALLOC;
     p->n1 = n1; p->n2 = n2; p->n3 = n3; p->dbl = dbl; p->flags = flags; p->npw = npw; p->N = N;
     p->elem = elem;
+    p->fast = (flags & VLOC_GENERIC_KERNELS) ? 0 : 1;
     for (int a = 0; a < 3; ++a) {
         p->ax.n[a] = ns[a];
         if (!plan_radices(ns[a], &p->ax.nst[a], p->ax.radix[a])) { free_plan(p); return VLOC_ERR_SIZE; }
@@ -280,15 +284,54 @@ int vloc_plan_create(vloc_plan* out, int n1, int n2, int n3, const int32_t* g, i
         }
         for (int s = 0; s < S; ++s) part[s] = (int32_t)(row_of[stick_x[s]] * ncol + col_of[stick_row[s]]);
     }
-    std::vector<int> part_ptr(P + 1, 0), part_sticks(S);
-    for (int s = 0; s < S; ++s) part_ptr[part[s] + 1]++;
-    for (int i = 0; i < P; ++i) part_ptr[i + 1] += part_ptr[i];
+    // ---- tiles: each part's sticks (ascending id) in runs of at most 32
+    // lines; one z-pass CTA per tile.  With the greedy partition every part is
+    // exactly one tile.  Per tile, the flat list of its plane waves as
+    // {caller index, z | line << 16}, sticks in tile order, l ascending.
+    std::vector<int> tile_ptr(1, 0), tile_sticks;
+    tile_sticks.reserve(S);
     {
-        std::vector<int> fill(part_ptr.begin(), part_ptr.end() - 1);
-        for (int s = 0; s < S; ++s) part_sticks[fill[part[s]]++] = s;
+        std::vector<std::vector<int>> members(P);
+        for (int s = 0; s < S; ++s) members[part[s]].push_back(s);
+        for (int q = 0; q < P; ++q)
+            for (size_t i = 0; i < members[q].size(); i += kLinesPerTile) {
+                const size_t e = std::min(members[q].size(), i + (size_t)kLinesPerTile);
+                tile_sticks.insert(tile_sticks.end(), members[q].begin() + i, members[q].begin() + e);
+                tile_ptr.push_back((int)tile_sticks.size());
+            }
     }
-    p->S = S; p->NP = NP; p->P = P;
+    const int T = (int)tile_ptr.size() - 1;
+    std::vector<int> tile_pw_ptr(T + 1, 0), tile_pw;
+    tile_pw.reserve(2 * (size_t)npw);
+    for (int tt = 0; tt < T; ++tt) {
+        for (int i = tile_ptr[tt]; i < tile_ptr[tt + 1]; ++i) {
+            const int s = tile_sticks[i], line = i - tile_ptr[tt];
+            for (int q = stick_pw_ptr[s]; q < stick_pw_ptr[s + 1]; ++q) {
+                tile_pw.push_back(pw_user[q]);
+                tile_pw.push_back(pw_z[q] | (line << 16));
+            }
+        }
+        tile_pw_ptr[tt + 1] = (int)(tile_pw.size() / 2);
+    }
+    p->S = S; p->NP = NP; p->P = P; p->T = T;
     p->stick_part = part;
+
+    // ---- host copy of the index tables, as the kernels read them
+    {
+        std::vector<int>& blob = p->host_tables;
+        HostTableLayout& L = p->lay;
+        auto append = [&](const std::vector<int>& v) { size_t off = blob.size(); blob.insert(blob.end(), v.begin(), v.end()); return off; };
+        L.o_row = append(stick_row);
+        L.o_tp = append(tile_ptr);
+        L.o_ts = append(tile_sticks);
+        L.o_tpp = append(tile_pw_ptr);
+        if (blob.size() & 1) blob.push_back(0);  // int2 alignment of the entry list
+        L.o_tpw = append(tile_pw);
+        L.o_plp = append(plane_ptr);
+        L.o_xr = append(xrow_plane);
+        L.total = blob.size();
+        L.S = S; L.T = T; L.NP = NP;
+    }
 
     if (host_only) {
         p->chunk = 0;
@@ -308,20 +351,13 @@ int vloc_plan_create(vloc_plan* out, int n1, int n2, int n3, const int32_t* g, i
     p->smem_optin = maxopt;
 
     // ---- device tables (one allocation)
-    std::vector<int> blob;
-    auto append = [&](const std::vector<int>& v) { size_t off = blob.size(); blob.insert(blob.end(), v.begin(), v.end()); return off; };
-    const size_t o_spp = append(stick_pw_ptr), o_pwu = append(pw_user), o_pwz = append(pw_z), o_row = append(stick_row),
-                 o_pp = append(part_ptr), o_ps = append(part_sticks), o_plp = append(plane_ptr), o_xr = append(xrow_plane);
     cudaStream_t st = (cudaStream_t)stream;
+    const std::vector<int>& blob = p->host_tables;
     if ((e = cudaMalloc(&p->d_tables, blob.size() * sizeof(int)))) { free_plan(p); return cuda_fail(e, "cudaMalloc(tables)"); }
     if ((e = cudaMemcpyAsync(p->d_tables, blob.data(), blob.size() * sizeof(int), cudaMemcpyHostToDevice, st))) {
         free_plan(p); return cuda_fail(e, "upload tables");
     }
-    DevTables& t = p->dt;
-    t.stick_pw_ptr = p->d_tables + o_spp; t.pw_user = p->d_tables + o_pwu; t.pw_z = p->d_tables + o_pwz;
-    t.stick_row = p->d_tables + o_row; t.part_ptr = p->d_tables + o_pp; t.part_sticks = p->d_tables + o_ps;
-    t.plane_ptr = p->d_tables + o_plp; t.xrow_plane = p->d_tables + o_xr;
-    t.S = S; t.P = P; t.NP = NP; t.n1 = n1; t.n2 = n2; t.n3 = n3; t.npw = npw;
+    p->dt = device_tables(p->d_tables, p->lay, n1, n2, n3, npw);
 
     // ---- twiddles exp(+2 pi i j / n), FP64-made
     for (int a = 0; a < 3; ++a) {
@@ -415,11 +451,11 @@ static int apply_impl(vloc_plan p, const void* c, const void* V, int64_t nb, voi
         const void* cc = (const char*)c + b0 * bstride;
         void* oo = (char*)out + b0 * bstride;
         int rc;
-        if ((rc = launch(p, KK_SCATTER_Z, st, [&] { return launch_k1_scatter_zpass(dbl, t, ax, p->d_tw[2], cc, cb, p->d_cyl, st); }))) return rc;
-        if ((rc = launch(p, KK_Y_INV, st, [&] { return launch_k2_ypass(dbl, +1, t, ax, p->d_tw[1], cb, p->d_cyl, p->d_slab, st); }))) return rc;
-        if ((rc = launch(p, KK_X_V, st, [&] { return launch_k3_xpass_v(dbl, t, ax, p->d_tw[0], V, cb, p->d_slab, st); }))) return rc;
-        if ((rc = launch(p, KK_Y_FWD, st, [&] { return launch_k2_ypass(dbl, -1, t, ax, p->d_tw[1], cb, p->d_cyl, p->d_slab, st); }))) return rc;
-        if ((rc = launch(p, KK_Z_GATHER, st, [&] { return launch_k4_zpass_gather(dbl, t, ax, p->d_tw[2], p->d_cyl, cb, oo, st); }))) return rc;
+        if ((rc = launch(p, KK_SCATTER_Z, st, [&] { return launch_k1_scatter_zpass(dbl, p->fast, t, ax, p->d_tw[2], cc, cb, p->d_cyl, st); }))) return rc;
+        if ((rc = launch(p, KK_Y_INV, st, [&] { return launch_k2_ypass(dbl, p->fast, +1, t, ax, p->d_tw[1], cb, p->d_cyl, p->d_slab, st); }))) return rc;
+        if ((rc = launch(p, KK_X_V, st, [&] { return launch_k3_xpass_v(dbl, p->fast, t, ax, p->d_tw[0], V, cb, p->d_slab, st); }))) return rc;
+        if ((rc = launch(p, KK_Y_FWD, st, [&] { return launch_k2_ypass(dbl, p->fast, -1, t, ax, p->d_tw[1], cb, p->d_cyl, p->d_slab, st); }))) return rc;
+        if ((rc = launch(p, KK_Z_GATHER, st, [&] { return launch_k4_zpass_gather(dbl, p->fast, t, ax, p->d_tw[2], p->d_cyl, cb, oo, st); }))) return rc;
     }
     return VLOC_OK;
 }
@@ -472,10 +508,10 @@ int vloc_backward(vloc_plan p, const void* c, const void* gout, const void* V, i
             const long long cb = std::min<long long>(half, nb - b0);
             const void* cc = (const char*)c + b0 * bstride;
             const void* gg = (const char*)gout + b0 * bstride;
-            if ((rc = launch(p, KK_SCATTER_Z, st, [&] { return launch_k1_scatter_zpass(dbl, t, ax, p->d_tw[2], cc, cb, cylC, st); }))) return rc;
-            if ((rc = launch(p, KK_Y_INV, st, [&] { return launch_k2_ypass(dbl, +1, t, ax, p->d_tw[1], cb, cylC, slabC, st); }))) return rc;
-            if ((rc = launch(p, KK_SCATTER_Z, st, [&] { return launch_k1_scatter_zpass(dbl, t, ax, p->d_tw[2], gg, cb, cylG, st); }))) return rc;
-            if ((rc = launch(p, KK_Y_INV, st, [&] { return launch_k2_ypass(dbl, +1, t, ax, p->d_tw[1], cb, cylG, slabG, st); }))) return rc;
+            if ((rc = launch(p, KK_SCATTER_Z, st, [&] { return launch_k1_scatter_zpass(dbl, p->fast, t, ax, p->d_tw[2], cc, cb, cylC, st); }))) return rc;
+            if ((rc = launch(p, KK_Y_INV, st, [&] { return launch_k2_ypass(dbl, p->fast, +1, t, ax, p->d_tw[1], cb, cylC, slabC, st); }))) return rc;
+            if ((rc = launch(p, KK_SCATTER_Z, st, [&] { return launch_k1_scatter_zpass(dbl, p->fast, t, ax, p->d_tw[2], gg, cb, cylG, st); }))) return rc;
+            if ((rc = launch(p, KK_Y_INV, st, [&] { return launch_k2_ypass(dbl, p->fast, +1, t, ax, p->d_tw[1], cb, cylG, slabG, st); }))) return rc;
             if ((rc = launch(p, KK_GRAD_V, st, [&] { return launch_k3b_grad_v(dbl, t, ax, p->d_tw[0], slabC, slabG, cb, p->d_acc, st); }))) return rc;
         }
         if ((rc = launch(p, KK_AUX, st, [&] { return launch_finish_grad_v(dbl, p->d_acc, gV, p->N, st); }))) return rc;
@@ -630,63 +666,26 @@ int vloc_get_info(vloc_plan p, vloc_info* info) {
 
 }  // extern "C"
 
-// Index tables rebuilt from the plan's host data (grid index per plane wave
-// and part per stick) into caller memory, with no allocation: plane waves
-// sorted by grid index, i.e. by (stick, z); sticks ascending; planes in
-// stick order; parts as dealt at plan creation.
+// The plan's index tables (kept on the host for every plan, including
+// host-only ones) copied into caller memory, with no allocation.
 int vloc::plan_host_tables(const vloc_plan_s* p, int* blob, size_t cap, HostTableLayout* lay) {
     if (!p || !blob || !lay) return VLOC_ERR_ARG;
-    const int S = p->S, P = p->P, NP = p->NP, n1 = p->n1, n2 = p->n2, n3 = p->n3;
-    const long long npw = p->npw;
-    HostTableLayout L;
-    L.S = S; L.P = P; L.NP = NP;
-    L.o_spp = 0;
-    L.o_pwu = L.o_spp + (size_t)S + 1;
-    L.o_pwz = L.o_pwu + (size_t)npw;
-    L.o_row = L.o_pwz + (size_t)npw;
-    L.o_pp = L.o_row + (size_t)S;
-    L.o_ps = L.o_pp + (size_t)P + 1;
-    L.o_plp = L.o_ps + (size_t)S;
-    L.o_xr = L.o_plp + (size_t)NP + 1;
-    L.total = L.o_xr + (size_t)n1;
-    if (L.total > cap) return VLOC_ERR_SIZE;
-    const int64_t* gi = p->grid_index.data();
-    int* spp = blob + L.o_spp;
-    int* pwu = blob + L.o_pwu;
-    int* pwz = blob + L.o_pwz;
-    int* row = blob + L.o_row;
-    int* pp = blob + L.o_pp;
-    int* ps = blob + L.o_ps;
-    int* plp = blob + L.o_plp;
-    int* xr = blob + L.o_xr;
-    for (long long q = 0; q < npw; ++q) pwu[q] = (int)q;
-    std::sort(pwu, pwu + npw, [gi](int a, int b) { return gi[a] < gi[b]; });
-    for (int x = 0; x < n1; ++x) xr[x] = -1;
-    int s = -1, np = 0;
-    long long prev = -1;
-    for (long long i = 0; i < npw; ++i) {
-        const long long g = gi[pwu[i]];
-        pwz[i] = (int)(g % n3);
-        const long long sid = g / n3;
-        if (sid != prev) {
-            ++s;
-            if (s >= S) return VLOC_ERR_ARG;
-            spp[s] = (int)i;
-            row[s] = (int)(sid % n2);
-            const int x = (int)(sid / n2);
-            if (xr[x] < 0) { xr[x] = np; plp[np++] = s; }
-            prev = sid;
-        }
-    }
-    if (s + 1 != S || np != NP) return VLOC_ERR_ARG;
-    spp[S] = (int)npw;
-    plp[NP] = S;
-    for (int k = 0; k <= P; ++k) pp[k] = 0;
-    for (int t = 0; t < S; ++t) pp[p->stick_part[t] + 1]++;
-    for (int k = 0; k < P; ++k) pp[k + 1] += pp[k];
-    for (int t = 0; t < S; ++t) ps[pp[p->stick_part[t]]++] = t;
-    for (int k = P; k > 0; --k) pp[k] = pp[k - 1];
-    pp[0] = 0;
-    *lay = L;
+    if (p->lay.total > cap) return VLOC_ERR_SIZE;
+    std::memcpy(blob, p->host_tables.data(), p->lay.total * sizeof(int));
+    *lay = p->lay;
     return VLOC_OK;
+}
+
+DevTables vloc::device_tables(const int* base, const HostTableLayout& L, int n1, int n2, int n3, long long npw) {
+    DevTables t;
+    t.stick_row = base + L.o_row;
+    t.tile_ptr = base + L.o_tp;
+    t.tile_sticks = base + L.o_ts;
+    t.tile_pw_ptr = base + L.o_tpp;
+    t.tile_pw = reinterpret_cast<const int2*>(base + L.o_tpw);
+    t.plane_ptr = base + L.o_plp;
+    t.xrow_plane = base + L.o_xr;
+    t.S = L.S; t.T = L.T; t.NP = L.NP;
+    t.n1 = n1; t.n2 = n2; t.n3 = n3; t.npw = npw;
+    return t;
 }

@@ -33,6 +33,7 @@ VLOC_PARTITION_BASIC = 0x010
 VLOC_PARTITION_IMPROVED = 0x020
 VLOC_GRAPH = 0x100
 VLOC_HOST_ONLY = 0x200
+VLOC_GENERIC_KERNELS = 0x400
 
 # every exported symbol declared in include/vloc.h
 EXPORTS = [
@@ -147,7 +148,7 @@ class VlocPlan:
     """
 
     def __init__(self, grid, glist, dtype=None, *, partition: str = "greedy", chunk: int = 0,
-                 graph: bool = False, host_only: bool = False, stream=None):
+                 graph: bool = False, host_only: bool = False, generic: bool = False, stream=None):
         import torch
         dtype = dtype or torch.complex64
         if dtype not in (torch.complex64, torch.complex128):
@@ -165,6 +166,8 @@ class VlocPlan:
             flags |= VLOC_GRAPH
         if host_only:
             flags |= VLOC_HOST_ONLY
+        if generic:
+            flags |= VLOC_GENERIC_KERNELS
         h = ctypes.c_void_p()
         sp = ctypes.c_void_p(None) if host_only else _stream_ptr(stream)
         _check(self.lib.vloc_plan_create(ctypes.byref(h), *self.grid,

@@ -34,6 +34,7 @@ def run(n, g, c, V, prec, **kw):
     return plan, ct, Vt, out
 
 
+@pytest.mark.parametrize("generic", [False, True])
 @pytest.mark.parametrize("prec", ["f32", "f64"])
 @pytest.mark.parametrize("n,R,nb,order", [
     ((24, 24, 24), 6, 1, "canonical"),        # config 0 (ragged: 24 < one 32-line tile)
@@ -46,9 +47,11 @@ def run(n, g, c, V, prec, **kw):
     ((30, 45, 27), 7, 2, "shuffled"),         # radices 3, 5, 9, 15
     ((64, 64, 64), 16, 4, "canonical"),
 ])
-def test_apply_matches_oracle(prec, n, R, nb, order):
+def test_apply_matches_oracle(prec, n, R, nb, order, generic):
+    # generic=True forces the runtime-radix kernels on every axis; otherwise
+    # the compile-time-length kernels run wherever one exists (24, 32, 48, 64)
     g, c, V = make_case(n, R, nb, seed=11, order=order, prec=prec)
-    _, _, _, out = run(n, g, c, V, prec)
+    _, _, _, out = run(n, g, c, V, prec, generic=generic)
     err = rel_l2_per_band(out.cpu().numpy(), oracle_apply(n, g, c, V))
     assert err.max() < TOL[prec], err.max()
 
@@ -64,11 +67,11 @@ def test_config1_64cubed_256_bands_sampled(prec):
 
 
 @pytest.mark.parametrize("prec", ["f32", "f64"])
-@pytest.mark.parametrize("n", [(96, 96, 120), (96, 96, 96)])
+@pytest.mark.parametrize("n", [(96, 96, 120), (96, 96, 96), (128, 128, 128), (144, 144, 144)])
 def test_full_size_1024_bands_sampled(prec, n):
     # The bench's launch configuration (default plan, 1024 bands), sampled
     # bands from the first, middle and last workspace chunks.
-    R, nb = 24, 1024
+    R, nb = n[0] // 4, (1024 if n[0] == 96 else 64)
     g, c, V = make_case(n, R, nb, seed=2, prec=prec)
     plan, _, _, out = run(n, g, c, V, prec)
     chunk = plan.info()["chunk_bands"]
@@ -126,11 +129,27 @@ def test_non_sphere_lists(prec):
         assert err.max() < TOL[prec], err.max()
 
 
-def test_partitions_do_not_change_results():
+@pytest.mark.parametrize("generic", [False, True])
+def test_partitions_do_not_change_results(generic):
     n, R = (32, 32, 32), 8
     g, c, V = make_case(n, R, 3, seed=8, prec="f32")
-    outs = [run(n, g, c, V, "f32", partition=k)[3] for k in ("greedy", "basic", "improved")]
+    outs = [run(n, g, c, V, "f32", partition=k, generic=generic)[3] for k in ("greedy", "basic", "improved")]
     assert torch.equal(outs[0], outs[1]) and torch.equal(outs[0], outs[2])
+
+
+def test_every_fast_length_matches_oracle():
+    # each compile-time length on every axis, against the oracle and against
+    # the runtime-radix kernels
+    for m in (24, 32, 48, 60, 64, 72, 80, 96, 100, 120, 128, 144):
+        n = (m, 24 if m != 24 else 32, 48 if m != 48 else 60)
+        for nn in (n, n[::-1], (n[1], m, n[2])):
+            R = min(nn) / 4
+            g, c, V = make_case(nn, R, 2, seed=m, order="shuffled", prec="f32")
+            _, _, _, fast = run(nn, g, c, V, "f32")
+            _, _, _, gen = run(nn, g, c, V, "f32", generic=True)
+            ref = oracle_apply(nn, g, c, V)
+            assert rel_l2_per_band(fast.cpu().numpy(), ref).max() < TOL["f32"], (nn, "fast")
+            assert rel_l2_per_band(gen.cpu().numpy(), ref).max() < TOL["f32"], (nn, "generic")
 
 
 @pytest.mark.parametrize("prec", ["f32", "f64"])
