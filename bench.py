@@ -251,11 +251,19 @@ def run_ours(args, rank, world, local_rank):
         c_d = torch.from_numpy(synth.coefficients(g, NBANDS, seed=SEED)).to("cuda", cdt)
         V_d = torch.from_numpy(synth.potential(*GRID, "smooth", SEED + 1000)[0]).to("cuda", rdt)
         out_d = torch.empty_like(c_d)
-        plan = vloc.VlocPlan(GRID, g, cdt)
+        plan = vloc.VlocPlan(GRID, g, cdt, chunk=args.chunk, generic=args.generic)
         ms = time_steps(lambda: plan.apply(c_d, V_d, out=out_d), args.steps, args.warmup, stream, dist_on)
+        plan.profile(True)
+        for _ in range(args.steps):
+            plan.apply(c_d, V_d, out=out_d)
+        prof = plan.get_profile()
+        plan.profile(False)
         if rank == 0:
             print(json.dumps({"only": "headline", "prec": args.prec, "bands": NBANDS, "steps": args.steps,
-                              "ms_per_step": ms / args.steps, "bands_per_s": world * NBANDS * args.steps / ms * 1e3}))
+                              "chunk": plan.info()["chunk_bands"], "generic": args.generic,
+                              "ms_per_step": ms / args.steps, "bands_per_s": world * NBANDS * args.steps / ms * 1e3,
+                              "kernel_ms_per_step": sum(t for _, t in prof.values()) / args.steps,
+                              "kernels": {k: [n // args.steps, round(t / args.steps, 4)] for k, (n, t) in prof.items()}}))
         return
     c64 = synth.coefficients(g, NBANDS, seed=SEED + rank, dtype=np.complex64)
     V96 = synth.potential(*GRID, "smooth", SEED + 1000)[0]
@@ -416,6 +424,8 @@ def main():
                     help="headline: only the FP32 forward steps (for profiler launch lists)")
     ap.add_argument("--bands", type=int, default=NBANDS, help="bands per GPU per step (default 1024)")
     ap.add_argument("--prec", choices=["f32", "f64"], default="f32", help="precision of --only headline")
+    ap.add_argument("--chunk", type=int, default=0, help="bands per workspace chunk (0: the plan's default)")
+    ap.add_argument("--generic", action="store_true", help="runtime-radix kernels only (--only headline)")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3

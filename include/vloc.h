@@ -102,8 +102,9 @@ typedef struct vloc_info {
  *   flags      : exactly one of VLOC_F32 / VLOC_F64, optionally one
  *                partition flag, VLOC_GRAPH, VLOC_HOST_ONLY and
  *                VLOC_GENERIC_KERNELS.
- *   max_bands_per_chunk : bands per workspace chunk (<= 0: automatic, sized
- *                to keep the chunk's intermediates in L2).
+ *   max_bands_per_chunk : bands per workspace chunk (<= 0: automatic, a
+ *                2 GiB workspace capped at 1/8 of the free device memory;
+ *                large chunks keep every kernel many waves deep).
  *   stream     : stream used for the one-time table uploads (synchronised
  *                before return).
  * Errors: VLOC_ERR_ARG, VLOC_ERR_SIZE, VLOC_ERR_GLIST, VLOC_ERR_ALLOC,

@@ -370,7 +370,13 @@ int vloc_plan_create(vloc_plan* out, int n1, int n2, int n3, const int32_t* g, i
     const size_t per_band = ((size_t)S * n3 + (size_t)NP * n2 * n3) * elem;
     long long chunk = max_bands_per_chunk;
     if (chunk <= 0) {
-        const size_t target = (size_t)64 << 20;  // about half of L2
+        // Enough bands per launch that every kernel runs many waves over the
+        // 152 SMs (kernel tails and launch gaps dominate small chunks, which
+        // measured slower even when their workspace stays in L2): a 2 GiB
+        // workspace, at most an eighth of the free device memory.
+        size_t free_b = 0, total_b = 0;
+        size_t target = (size_t)2 << 30;
+        if (cudaMemGetInfo(&free_b, &total_b) == cudaSuccess) target = std::min(target, free_b / 8);
         chunk = std::max<long long>(1, (long long)(target / per_band));
     }
     chunk = std::min<long long>(chunk, 65535);
