@@ -34,23 +34,53 @@ template <> struct Cplx<float> { using type = float2; };
 template <> struct Cplx<double> { using type = double2; };
 template <typename T> using c2 = typename Cplx<T>::type;
 
-template <typename V> __device__ __forceinline__ V cmk(decltype(V{}.x) re, decltype(V{}.x) im) {
+template <typename V> struct ScalarOf { using type = decltype(V{}.x); };
+template <typename V> using scalar_t = typename ScalarOf<V>::type;
+
+template <typename V> __device__ __forceinline__ V cmk(scalar_t<V> re, scalar_t<V> im) {
     V r; r.x = re; r.y = im; return r;
 }
 template <typename V> __device__ __forceinline__ V cadd(V a, V b) { return cmk<V>(a.x + b.x, a.y + b.y); }
 template <typename V> __device__ __forceinline__ V csub(V a, V b) { return cmk<V>(a.x - b.x, a.y - b.y); }
-template <typename V> __device__ __forceinline__ V cmul(V a, V b) {
+template <typename V> __device__ __forceinline__ V cneg(V a) { return cmk<V>(-a.x, -a.y); }
+// a * b and a * conj(b) for a twiddle b of the scalar complex type
+template <typename V, typename W> __device__ __forceinline__ V cmul(V a, W b) {
     return cmk<V>(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
 }
-template <typename V> __device__ __forceinline__ V cmulc(V a, V b) {  // a * conj(b)
+template <typename V, typename W> __device__ __forceinline__ V cmulc(V a, W b) {
     return cmk<V>(a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y);
 }
-template <typename V> __device__ __forceinline__ V cscale(V a, decltype(V{}.x) s) { return cmk<V>(a.x * s, a.y * s); }
+template <typename V> __device__ __forceinline__ V cscale(V a, scalar_t<V> s) { return cmk<V>(a.x * s, a.y * s); }
+// a + s * b, s real
+template <typename V> __device__ __forceinline__ V cfma(V a, scalar_t<V> s, V b) {
+    return cmk<V>(a.x + s * b.x, a.y + s * b.y);
+}
+// x * (c + i s), c and s real constants
+template <typename V> __device__ __forceinline__ V cmul_cs(V x, scalar_t<V> c, scalar_t<V> s) {
+    return cmk<V>(x.x * c - x.y * s, x.x * s + x.y * c);
+}
 // multiply by S*i (S = +1 or -1)
 template <int S, typename V> __device__ __forceinline__ V mul_si(V a) {
     return S > 0 ? cmk<V>(-a.y, a.x) : cmk<V>(a.y, -a.x);
 }
 template <typename V> __device__ __forceinline__ V czero() { return cmk<V>(0, 0); }
+
+// Two FP32 complex values of adjacent lines carried by one lane (one 16-byte
+// vector): every operation applies to both; twiddles are shared.
+struct __align__(16) P2f {
+    float2 a, b;
+};
+template <> struct ScalarOf<P2f> { using type = float; };
+__device__ __forceinline__ P2f cadd(P2f x, P2f y) { return {cadd(x.a, y.a), cadd(x.b, y.b)}; }
+__device__ __forceinline__ P2f csub(P2f x, P2f y) { return {csub(x.a, y.a), csub(x.b, y.b)}; }
+__device__ __forceinline__ P2f cneg(P2f x) { return {cneg(x.a), cneg(x.b)}; }
+__device__ __forceinline__ P2f cmul(P2f x, float2 w) { return {cmul(x.a, w), cmul(x.b, w)}; }
+__device__ __forceinline__ P2f cmulc(P2f x, float2 w) { return {cmulc(x.a, w), cmulc(x.b, w)}; }
+__device__ __forceinline__ P2f cscale(P2f x, float s) { return {cscale(x.a, s), cscale(x.b, s)}; }
+__device__ __forceinline__ P2f cfma(P2f x, float s, P2f y) { return {cfma(x.a, s, y.a), cfma(x.b, s, y.b)}; }
+__device__ __forceinline__ P2f cmul_cs(P2f x, float c, float s) { return {cmul_cs(x.a, c, s), cmul_cs(x.b, c, s)}; }
+template <int S> __device__ __forceinline__ P2f mul_si(P2f x) { return {mul_si<S>(x.a), mul_si<S>(x.b)}; }
+template <> __device__ __forceinline__ P2f czero<P2f>() { return {make_float2(0.f, 0.f), make_float2(0.f, 0.f)}; }
 
 // ------------------------------------------------- compile-time cos / sin
 // exp(2 pi i m / R) from Taylor series on the first octant (|x| <= pi/4,
@@ -115,16 +145,16 @@ template <int R, int S, int M, typename V> __device__ __forceinline__ V tw_const
     if constexpr (m == 0) {
         return x;
     } else if constexpr (2 * m == R) {
-        return cmk<V>(-x.x, -x.y);
+        return cneg(x);
     } else if constexpr (4 * m == R) {
         return mul_si<S>(x);
     } else if constexpr (4 * m == 3 * R) {
         return mul_si<-S>(x);
     } else {
-        using T = decltype(V{}.x);
+        using T = scalar_t<V>;
         constexpr T c = (T)ct::cos_turn(m, R);
         constexpr T s = (T)(S * ct::sin_turn(m, R));
-        return cmk<V>(x.x * c - x.y * s, x.x * s + x.y * c);
+        return cmul_cs(x, c, s);
     }
 }
 
@@ -144,11 +174,11 @@ template <int S> struct Dft<2, S> {
 };
 template <int S> struct Dft<3, S> {
     template <typename V> __device__ __forceinline__ static void run(V* v) {
-        using T = decltype(V{}.x);
+        using T = scalar_t<V>;
         constexpr T h = (T)0.866025403784438646763723170752936183;  // sqrt(3)/2
         V t = cadd(v[1], v[2]);
         V d = csub(v[1], v[2]);
-        V m = cmk<V>(v[0].x - (T)0.5 * t.x, v[0].y - (T)0.5 * t.y);
+        V m = cfma(v[0], (T)-0.5, t);
         V r = mul_si<S>(cscale(d, h));
         v[0] = cadd(v[0], t);
         v[1] = cadd(m, r);
@@ -167,17 +197,17 @@ template <int S> struct Dft<4, S> {
 };
 template <int S> struct Dft<5, S> {
     template <typename V> __device__ __forceinline__ static void run(V* v) {
-        using T = decltype(V{}.x);
+        using T = scalar_t<V>;
         constexpr T c1 = (T)ct::cos_turn(1, 5), c2 = (T)ct::cos_turn(2, 5);
         constexpr T s1 = (T)ct::sin_turn(1, 5), s2 = (T)ct::sin_turn(2, 5);
         V a1 = cadd(v[1], v[4]), b1 = csub(v[1], v[4]);
         V a2 = cadd(v[2], v[3]), b2 = csub(v[2], v[3]);
         V x0 = v[0];
-        V p1 = cmk<V>(x0.x + c1 * a1.x + c2 * a2.x, x0.y + c1 * a1.y + c2 * a2.y);
-        V p2 = cmk<V>(x0.x + c2 * a1.x + c1 * a2.x, x0.y + c2 * a1.y + c1 * a2.y);
-        V q1 = mul_si<S>(cmk<V>(s1 * b1.x + s2 * b2.x, s1 * b1.y + s2 * b2.y));
-        V q2 = mul_si<S>(cmk<V>(s2 * b1.x - s1 * b2.x, s2 * b1.y - s1 * b2.y));
-        v[0] = cmk<V>(x0.x + a1.x + a2.x, x0.y + a1.y + a2.y);
+        V p1 = cfma(cfma(x0, c1, a1), c2, a2);
+        V p2 = cfma(cfma(x0, c2, a1), c1, a2);
+        V q1 = mul_si<S>(cfma(cscale(b1, s1), s2, b2));
+        V q2 = mul_si<S>(cfma(cscale(b1, s2), -s1, b2));
+        v[0] = cadd(cadd(x0, a1), a2);
         v[1] = cadd(p1, q1);
         v[4] = csub(p1, q1);
         v[2] = cadd(p2, q2);

@@ -3,7 +3,10 @@
 // Same algorithm as fft_core.cuh's runtime stages, but the transform length
 // N, each stage's radix R and stride Ns are template constants, so the index
 // arithmetic folds into immediates and every unit's registers are known at
-// compile time.  Two further differences:
+// compile time.  FP32 only.  Three further differences:
+//  * each lane carries two adjacent lines as one 16-byte vector (P2f), so a
+//    shared or global access moves two elements and the address and
+//    predicate work per element halves, while tiles stay 32 lines wide;
 //  * one shared-memory buffer per tile: a stage that reads and writes the
 //    buffer first computes all of its warp's units into registers, waits at a
 //    barrier, then stores (halves the footprint, doubling resident CTAs);
@@ -70,27 +73,41 @@ template <int N> struct Sched {
     static constexpr int NSR(int s) { int p = 1; for (int i = 0; i < s; ++i) p *= P.r[P.nst - 1 - i]; return p; }
 };
 
-// One compile-time Stockham stage over a 32-line tile held across lanes,
-// units spread over the CTA's warps.
+// Shared line buffer for lane pairs: [N][kLdP] FP32 complex, pitch even so a
+// pair of adjacent lines is one aligned 16-byte vector.
+constexpr int kLdP = kLines + 2;
+struct SmemP {
+    float2* p;
+    __device__ __forceinline__ P2f operator()(int e, int slot) const {
+        return *reinterpret_cast<const P2f*>(p + e * kLdP + 2 * slot);
+    }
+    __device__ __forceinline__ void operator()(int e, int slot, P2f v) const {
+        *reinterpret_cast<P2f*>(p + e * kLdP + 2 * slot) = v;
+    }
+};
+
+// One compile-time Stockham stage over a 32-line tile.  Each lane carries
+// the pair of lines (2 slot, 2 slot + 1), slot = lane % 16, so a warp works
+// on two units at once (sub = lane / 16); the CTA's W warps share the units.
 template <int N, int R, int NS, int S, int W> struct CtStage {
     static constexpr int NI = N / R;
-    static constexpr int U = (NI + W - 1) / W;
+    static constexpr int U = (NI + 2 * W - 1) / (2 * W);
     static constexpr int TWS = N / (NS * R);
 
-    template <typename V, class Src>
-    __device__ __forceinline__ static void compute(V (&h)[U][R], const V* __restrict__ tw, const Src& src, int lane,
-                                                  int warp) {
+    template <class Src>
+    __device__ __forceinline__ static void compute(P2f (&h)[U][R], const float2* __restrict__ tw, const Src& src,
+                                                  int slot, int sub, int warp) {
 #pragma unroll
         for (int u = 0; u < U; ++u) {
-            const int i = warp + u * W;
-            if (NI % W == 0 || i < NI) {
+            const int i = 2 * (warp + u * W) + sub;
+            if (NI % (2 * W) == 0 || i < NI) {
 #pragma unroll
-                for (int r = 0; r < R; ++r) h[u][r] = src(i + r * NI, lane);
+                for (int r = 0; r < R; ++r) h[u][r] = src(i + r * NI, slot);
                 if constexpr (NS > 1) {
                     const int base = (i % NS) * TWS;
 #pragma unroll
                     for (int r = 1; r < R; ++r) {
-                        const V w = tw[r * base];
+                        const float2 w = tw[r * base];
                         h[u][r] = S > 0 ? cmul(h[u][r], w) : cmulc(h[u][r], w);
                     }
                 }
@@ -99,29 +116,29 @@ template <int N, int R, int NS, int S, int W> struct CtStage {
         }
     }
 
-    template <typename V, class Dst>
-    __device__ __forceinline__ static void store(const V (&h)[U][R], const Dst& dst, int lane, int warp) {
+    template <class Dst>
+    __device__ __forceinline__ static void store(const P2f (&h)[U][R], const Dst& dst, int slot, int sub, int warp) {
 #pragma unroll
         for (int u = 0; u < U; ++u) {
-            const int i = warp + u * W;
-            if (NI % W == 0 || i < NI) {
+            const int i = 2 * (warp + u * W) + sub;
+            if (NI % (2 * W) == 0 || i < NI) {
                 const int k = i % NS;
                 const int j = (i - k) * R + k;
 #pragma unroll
-                for (int r = 0; r < R; ++r) dst(j + r * NS, lane, h[u][r]);
+                for (int r = 0; r < R; ++r) dst(j + r * NS, slot, h[u][r]);
             }
         }
     }
 
-    // compute + store; `hold` puts a CTA barrier between them (the stage
-    // reads and writes the same shared buffer).
-    template <bool HOLD, typename V, class Src, class Dst>
-    __device__ __forceinline__ static void run(const V* __restrict__ tw, const Src& src, const Dst& dst, int lane,
-                                              int warp, bool act) {
-        V h[U][R];
-        if (act) compute(h, tw, src, lane, warp);
+    // compute + store; HOLD puts a CTA barrier between them (the stage reads
+    // and writes the same shared buffer).
+    template <bool HOLD, class Src, class Dst>
+    __device__ __forceinline__ static void run(const float2* __restrict__ tw, const Src& src, const Dst& dst, int slot,
+                                              int sub, int warp, bool act) {
+        P2f h[U][R];
+        if (act) compute(h, tw, src, slot, sub, warp);
         if constexpr (HOLD) __syncthreads();
-        if (act) store(h, dst, lane, warp);
+        if (act) store(h, dst, slot, sub, warp);
     }
 };
 
@@ -130,19 +147,19 @@ template <int N, int S, int W, int s> using NatStage = CtStage<N, Sched<N>::R(s)
 // Stage s of the reversed schedule.
 template <int N, int S, int W, int s> using RevStage = CtStage<N, Sched<N>::RR(s), Sched<N>::NSR(s), S, W>;
 
-// Full transform with one shared buffer `buf` ([N][kLd]).  `in` may be
-// global or `buf` itself (IN_BUF), `out` may be global or `buf` (OUT_BUF).
-// The caller provides a barrier before the call if `buf` was in use; the
-// call ends without a barrier.
-template <int N, int S, int W, bool REV, bool IN_BUF, bool OUT_BUF, typename V, class In, class Out>
-__device__ __forceinline__ void fft_ct(const V* __restrict__ tw, const In& in, const Out& out, V* buf, int lane,
-                                       int warp, bool act) {
+// Full transform with one shared buffer `buf` ([N][kLdP] FP32 complex).
+// `in` may be global or `buf` itself (IN_BUF), `out` may be global or `buf`
+// (OUT_BUF).  The caller provides a barrier before the call if `buf` was in
+// use; the call ends without a barrier.
+template <int N, int S, int W, bool REV, bool IN_BUF, bool OUT_BUF, class In, class Out>
+__device__ __forceinline__ void fft_ct(const float2* __restrict__ tw, const In& in, const Out& out, float2* buf,
+                                       int slot, int sub, int warp, bool act) {
     constexpr int nst = Sched<N>::nst;
-    Smem<V> sb{buf};
+    SmemP sb{buf};
     auto stage = [&](auto sc, const auto& src, const auto& dst, auto hold) {
         constexpr int s = decltype(sc)::value;
         using St = std::conditional_t<REV, RevStage<N, S, W, s>, NatStage<N, S, W, s>>;
-        St::template run<decltype(hold)::value>(tw, src, dst, lane, warp, act);
+        St::template run<decltype(hold)::value>(tw, src, dst, slot, sub, warp, act);
     };
     if constexpr (nst == 1) {
         stage(std::integral_constant<int, 0>{}, in, out, std::integral_constant<bool, IN_BUF && OUT_BUF>{});

@@ -4,6 +4,7 @@
 // parallel).
 #include <cuda_runtime.h>
 
+#include <cstdint>
 #include <mutex>
 
 #include "internal.h"
@@ -69,7 +70,8 @@ int launch_k2_ypass(int dbl, int fast, int sign, const DevTables& t, const Launc
 }
 int launch_k3_xpass_v(int dbl, int fast, const DevTables& t, const LaunchAxes& ax, const void* tw1, const void* V,
                       long long nb, void* slab, cudaStream_t st) {
-    if (!dbl && fast) switch (t.n1) {
+    // the compile-time x-pass reads V two lines at a time (8-byte loads)
+    if (!dbl && fast && ((uintptr_t)V & 7) == 0) switch (t.n1) {
 #define VLOC_CASE(N) case N: return LaunchCT<float, N>::k3(t, tw1, V, nb, slab, st);
         VLOC_CT_SIZES(VLOC_CASE)
 #undef VLOC_CASE

@@ -1,13 +1,15 @@
-// kernels_ct.cuh -- the chain kernels with compile-time axis lengths.
+// kernels_ct.cuh -- the chain kernels with compile-time axis lengths (FP32).
 //
 // Same five steps as kernels_impl.cuh (K1 scatter + inverse z-pass, K2
 // y-passes, K3 x-pass with V(r), K4 forward z-pass + gather), specialised
 // for one axis length N per instantiation so the Stockham stages of
-// fft_ct.cuh fold their index arithmetic, use one shared buffer per tile,
-// and K3 chains the inverse x-FFT's last stage, the multiply by V and the
-// forward x-FFT's first stage in registers (no shared-memory round trip
-// between the two transforms).  Instantiated for the common grid lengths in
-// kernels_ct_*.cu; other lengths use the runtime-radix kernels.
+// fft_ct.cuh fold their index arithmetic.  Each lane carries two adjacent
+// lines (one 16-byte vector), a tile uses one shared buffer, and K3 chains
+// the inverse x-FFT's last stage, the multiply by V and the forward x-FFT's
+// first stage in registers (no shared-memory round trip between the two
+// transforms).  Instantiated for the common grid lengths (even, so a line
+// pair is always 16-byte aligned) in kernels_ct_*.cu; other lengths use the
+// runtime-radix kernels.
 #pragma once
 
 #include "fft_ct.cuh"
@@ -15,24 +17,59 @@
 
 namespace vloc {
 
-template <int N> __host__ __device__ constexpr size_t ct_smem(size_t elem) {
-    return (size_t)N * kLd * elem + (size_t)N * elem + (size_t)N * sizeof(int) + 16;
+template <int N> __host__ __device__ constexpr size_t ct_smem() {
+    return (size_t)N * kLdP * sizeof(float2) + (size_t)N * sizeof(float2) + (size_t)N * sizeof(int) + 16;
 }
 
-// rows of a tile with a compile-time row length
-template <int NN, typename V>
-__device__ __forceinline__ void rows_out_ct(const V* buf, V* __restrict__ cb, const int* sticks, int lines) {
+__device__ __forceinline__ int slot_of() { return threadIdx.x & 15; }
+__device__ __forceinline__ int sub_of() { return (threadIdx.x >> 4) & 1; }
+__device__ __forceinline__ int warp_of() { return threadIdx.x >> 5; }
+
+// ------------------------------------------------------------- tile I/O
+__device__ __forceinline__ void scatter_entries_p(const int2* __restrict__ ent, int e0, int e1,
+                                                  const float2* __restrict__ c, float2* buf) {
+    for (int base = e0 + (int)threadIdx.x; base < e1; base += kBatch * kThreads) {
+        int2 en[kBatch];
+        float2 val[kBatch];
+#pragma unroll
+        for (int u = 0; u < kBatch; ++u) {
+            const int e = base + u * kThreads;
+            en[u] = e < e1 ? ent[e] : make_int2(0, -1);
+        }
+#pragma unroll
+        for (int u = 0; u < kBatch; ++u) val[u] = en[u].y >= 0 ? c[en[u].x] : make_float2(0.f, 0.f);
+#pragma unroll
+        for (int u = 0; u < kBatch; ++u)
+            if (en[u].y >= 0) buf[(en[u].y & 0xffff) * kLdP + (en[u].y >> 16)] = val[u];
+    }
+}
+__device__ __forceinline__ void gather_entries_p(const int2* __restrict__ ent, int e0, int e1, const float2* buf,
+                                                 float2* __restrict__ o, float scale) {
+    for (int base = e0 + (int)threadIdx.x; base < e1; base += kBatch * kThreads) {
+        int2 en[kBatch];
+#pragma unroll
+        for (int u = 0; u < kBatch; ++u) {
+            const int e = base + u * kThreads;
+            en[u] = e < e1 ? ent[e] : make_int2(0, -1);
+        }
+#pragma unroll
+        for (int u = 0; u < kBatch; ++u)
+            if (en[u].y >= 0) o[en[u].x] = cscale(buf[(en[u].y & 0xffff) * kLdP + (en[u].y >> 16)], scale);
+    }
+}
+template <int NN>
+__device__ __forceinline__ void rows_out_p(const float2* buf, float2* __restrict__ cb, const int* sticks, int lines) {
     const int total = lines * NN;
     for (int i = threadIdx.x; i < total; i += kThreads) {
         const int l = i / NN, z = i - l * NN;
-        cb[(long long)sticks[l] * NN + z] = buf[z * kLd + l];
+        cb[(long long)sticks[l] * NN + z] = buf[z * kLdP + l];
     }
 }
-template <int NN, typename V>
-__device__ __forceinline__ void rows_in_ct(V* buf, const V* __restrict__ cb, const int* sticks, int lines) {
+template <int NN>
+__device__ __forceinline__ void rows_in_p(float2* buf, const float2* __restrict__ cb, const int* sticks, int lines) {
     const int total = lines * NN;
     for (int base = threadIdx.x; base < total; base += kBatch * kThreads) {
-        V val[kBatch];
+        float2 val[kBatch];
 #pragma unroll
         for (int u = 0; u < kBatch; ++u) {
             const int i = base + u * kThreads;
@@ -46,96 +83,131 @@ __device__ __forceinline__ void rows_in_ct(V* buf, const V* __restrict__ cb, con
             const int i = base + u * kThreads;
             if (i < total) {
                 const int l = i / NN, z = i - l * NN;
-                buf[z * kLd + l] = val[u];
+                buf[z * kLdP + l] = val[u];
             }
         }
     }
 }
 
+// Global row accessors for line pairs (z0 even, rows of even length).
+struct CylRowsP {  // rows = the plane's sticks (via rowmap), -1 = absent row
+    float2* cb;
+    const int* rowmap;
+    int n3, z0;
+    __device__ __forceinline__ P2f operator()(int e, int slot) const {
+        const int s = rowmap[e];
+        return s >= 0 ? *reinterpret_cast<const P2f*>(cb + (long long)s * n3 + z0 + 2 * slot) : czero<P2f>();
+    }
+    __device__ __forceinline__ void operator()(int e, int slot, P2f v) const {
+        const int s = rowmap[e];
+        if (s >= 0) *reinterpret_cast<P2f*>(cb + (long long)s * n3 + z0 + 2 * slot) = v;
+    }
+};
+struct SlabRowsP {  // every y row of one plane's tile
+    float2* p;       // slab[b][plane][0][z0]
+    int n3;
+    __device__ __forceinline__ P2f operator()(int e, int slot) const {
+        return *reinterpret_cast<const P2f*>(p + (long long)e * n3 + 2 * slot);
+    }
+    __device__ __forceinline__ void operator()(int e, int slot, P2f v) const {
+        *reinterpret_cast<P2f*>(p + (long long)e * n3 + 2 * slot) = v;
+    }
+};
+struct XRowsP {  // x rows at fixed y: the occupied planes
+    float2* sb;      // slab[b][0][y][z0]
+    const int* xrow;
+    long long pstride;
+    __device__ __forceinline__ P2f operator()(int e, int slot) const {
+        const int p = xrow[e];
+        return p >= 0 ? *reinterpret_cast<const P2f*>(sb + p * pstride + 2 * slot) : czero<P2f>();
+    }
+    __device__ __forceinline__ void operator()(int e, int slot, P2f v) const {
+        const int p = xrow[e];
+        if (p >= 0) *reinterpret_cast<P2f*>(sb + p * pstride + 2 * slot) = v;
+    }
+};
+
 // ------------------------------------------------------------------ K1
-template <typename T, int N>
-__global__ void __launch_bounds__(kThreads) k1_ct(DevTables t, const V2<T>* __restrict__ tw3,
-                                                 const V2<T>* __restrict__ coeffs, V2<T>* __restrict__ cyl) {
-    using V = V2<T>;
+template <int N>
+__global__ void __launch_bounds__(kThreads) k1_ct(DevTables t, const float2* __restrict__ tw3,
+                                                 const float2* __restrict__ coeffs, float2* __restrict__ cyl) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    V* buf = reinterpret_cast<V*>(smem_raw);
-    V* stw = buf + N * kLd;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    float2* buf = reinterpret_cast<float2*>(smem_raw);
+    float2* stw = buf + N * kLdP;
     const int tile = blockIdx.x;
     const long long b = blockIdx.y;
-    load_tw<T>(stw, tw3, N);
+    load_tw<float>(stw, tw3, N);
     const int s0 = t.tile_ptr[tile], lines = t.tile_ptr[tile + 1] - s0;
-    for (int i = threadIdx.x; i < N * kLd; i += kThreads) buf[i] = czero<V>();
+    for (int i = threadIdx.x; i < N * kLdP; i += kThreads) buf[i] = make_float2(0.f, 0.f);
     __syncthreads();
-    scatter_entries(t.tile_pw, t.tile_pw_ptr[tile], t.tile_pw_ptr[tile + 1], coeffs + b * t.npw, buf);
+    scatter_entries_p(t.tile_pw, t.tile_pw_ptr[tile], t.tile_pw_ptr[tile + 1], coeffs + b * t.npw, buf);
     __syncthreads();
-    fft_ct<N, +1, kWarps, false, true, true>(stw, Smem<V>{buf}, Smem<V>{buf}, buf, lane, warp, lane < lines);
+    fft_ct<N, +1, kWarps, false, true, true>(stw, SmemP{buf}, SmemP{buf}, buf, slot_of(), sub_of(), warp_of(),
+                                             2 * slot_of() < lines);
     __syncthreads();
-    rows_out_ct<N>(buf, cyl + b * (long long)t.S * N, t.tile_sticks + s0, lines);
+    rows_out_p<N>(buf, cyl + b * (long long)t.S * N, t.tile_sticks + s0, lines);
 }
 
 // ------------------------------------------------------------------ K2
-template <typename T, int S, int N>
-__global__ void __launch_bounds__(kThreads) k2_ct(DevTables t, const V2<T>* __restrict__ tw2, V2<T>* cyl,
-                                                 V2<T>* slab) {
-    using V = V2<T>;
+template <int S, int N>
+__global__ void __launch_bounds__(kThreads) k2_ct(DevTables t, const float2* __restrict__ tw2, float2* cyl,
+                                                 float2* slab) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int n3 = t.n3;
-    V* buf = reinterpret_cast<V*>(smem_raw);
-    V* stw = buf + N * kLd;
+    float2* buf = reinterpret_cast<float2*>(smem_raw);
+    float2* stw = buf + N * kLdP;
     int* rowmap = reinterpret_cast<int*>(stw + N);
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int plane = blockIdx.x;
     const int z0 = blockIdx.y * kLines;
     const long long b = blockIdx.z;
     const int lines = min(kLines, n3 - z0);
-    load_tw<T>(stw, tw2, N);
+    load_tw<float>(stw, tw2, N);
     for (int e = threadIdx.x; e < N; e += kThreads) rowmap[e] = -1;
     __syncthreads();
     for (int s = t.plane_ptr[plane] + threadIdx.x; s < t.plane_ptr[plane + 1]; s += kThreads) rowmap[t.stick_row[s]] = s;
     __syncthreads();
-    CylRows<T> cr{cyl + b * (long long)t.S * n3, rowmap, n3, z0};
-    SlabRows<T> sr{slab + ((b * t.NP + plane) * (long long)N) * n3 + z0, n3};
-    if constexpr (S > 0) fft_ct<N, +1, kWarps, false, false, false>(stw, cr, sr, buf, lane, warp, lane < lines);
-    else fft_ct<N, -1, kWarps, false, false, false>(stw, sr, cr, buf, lane, warp, lane < lines);
+    CylRowsP cr{cyl + b * (long long)t.S * n3, rowmap, n3, z0};
+    SlabRowsP sr{slab + ((b * t.NP + plane) * (long long)N) * n3 + z0, n3};
+    const bool act = 2 * slot_of() < lines;
+    if constexpr (S > 0) fft_ct<N, +1, kWarps, false, false, false>(stw, cr, sr, buf, slot_of(), sub_of(), warp_of(), act);
+    else fft_ct<N, -1, kWarps, false, false, false>(stw, sr, cr, buf, slot_of(), sub_of(), warp_of(), act);
 }
 
 // ------------------------------------------------------------------ K3
-template <typename T, int N>
-__global__ void __launch_bounds__(kThreads) k3_ct(DevTables t, const V2<T>* __restrict__ tw1, const T* __restrict__ Vr,
-                                                 V2<T>* slab) {
-    using V = V2<T>;
+template <int N>
+__global__ void __launch_bounds__(kThreads) k3_ct(DevTables t, const float2* __restrict__ tw1,
+                                                 const float* __restrict__ Vr, float2* slab) {
     using SC = Sched<N>;
     constexpr int nst = SC::nst;
     static_assert(nst >= 2, "compile-time x-pass needs at least two stages");
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int n2 = t.n2, n3 = t.n3;
-    V* buf = reinterpret_cast<V*>(smem_raw);
-    V* stw = buf + N * kLd;
+    float2* buf = reinterpret_cast<float2*>(smem_raw);
+    float2* stw = buf + N * kLdP;
     int* xrow = reinterpret_cast<int*>(stw + N);
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int slot = slot_of(), sub = sub_of(), warp = warp_of();
     const int y = blockIdx.x;
     const int z0 = blockIdx.y * kLines;
     const long long b = blockIdx.z;
     const int lines = min(kLines, n3 - z0);
-    const bool act = lane < lines;
-    load_tw<T>(stw, tw1, N);
+    const bool act = 2 * slot < lines;
+    load_tw<float>(stw, tw1, N);
     for (int e = threadIdx.x; e < N; e += kThreads) xrow[e] = t.xrow_plane[e];
     __syncthreads();
     const long long pstride = (long long)n2 * n3;
-    XRows<T> xr{slab + b * t.NP * pstride + (long long)y * n3 + z0, xrow, pstride};
-    const T* vrow = Vr + (long long)y * n3 + z0;
-    Smem<V> sb{buf};
+    XRowsP xr{slab + b * t.NP * pstride + (long long)y * n3 + z0, xrow, pstride};
+    const float* vrow = Vr + (long long)y * n3 + z0 + 2 * slot;
+    SmemP sb{buf};
 
     // inverse x-FFT, stages 0 .. nst-2 (global rows -> buffer)
-    NatStage<N, +1, kWarps, 0>::template run<false>(stw, xr, sb, lane, warp, act);
+    NatStage<N, +1, kWarps, 0>::template run<false>(stw, xr, sb, slot, sub, warp, act);
     __syncthreads();
     if constexpr (nst >= 3) {
-        NatStage<N, +1, kWarps, 1>::template run<true>(stw, sb, sb, lane, warp, act);
+        NatStage<N, +1, kWarps, 1>::template run<true>(stw, sb, sb, slot, sub, warp, act);
         __syncthreads();
     }
     if constexpr (nst >= 4) {
-        NatStage<N, +1, kWarps, 2>::template run<true>(stw, sb, sb, lane, warp, act);
+        NatStage<N, +1, kWarps, 2>::template run<true>(stw, sb, sb, slot, sub, warp, act);
         __syncthreads();
     }
     // last inverse stage -> psi(x) * V(x, y, z) -> first forward stage of the
@@ -144,60 +216,60 @@ __global__ void __launch_bounds__(kThreads) k3_ct(DevTables t, const V2<T>* __re
     using F = RevStage<N, -1, kWarps, 0>;
     constexpr int R = SC::R(nst - 1);
     static_assert(F::NI == L::NI && SC::RR(0) == R, "chained stages must share units");
-    V h[L::U][R];
+    P2f h[L::U][R];
     if (act) {
-        L::compute(h, stw, sb, lane, warp);
+        L::compute(h, stw, sb, slot, sub, warp);
 #pragma unroll
         for (int u = 0; u < L::U; ++u) {
-            const int i = warp + u * kWarps;
-            if (L::NI % kWarps == 0 || i < L::NI) {
+            const int i = 2 * (warp + u * kWarps) + sub;
+            if (L::NI % (2 * kWarps) == 0 || i < L::NI) {
 #pragma unroll
                 for (int r = 0; r < R; ++r) {
-                    const T w = vrow[(long long)(i + r * L::NI) * pstride + lane];
-                    h[u][r] = cmk<V>(h[u][r].x * w, h[u][r].y * w);
+                    const float2 w = *reinterpret_cast<const float2*>(vrow + (long long)(i + r * L::NI) * pstride);
+                    h[u][r].a = cscale(h[u][r].a, w.x);
+                    h[u][r].b = cscale(h[u][r].b, w.y);
                 }
                 Dft<R, -1>::run(h[u]);
             }
         }
     }
     __syncthreads();
-    if (act) F::store(h, sb, lane, warp);
+    if (act) F::store(h, sb, slot, sub, warp);
     __syncthreads();
     // forward x-FFT, remaining stages (buffer -> occupied global rows)
     if constexpr (nst >= 3) {
-        RevStage<N, -1, kWarps, 1>::template run<true>(stw, sb, sb, lane, warp, act);
+        RevStage<N, -1, kWarps, 1>::template run<true>(stw, sb, sb, slot, sub, warp, act);
         __syncthreads();
     }
     if constexpr (nst >= 4) {
-        RevStage<N, -1, kWarps, 2>::template run<true>(stw, sb, sb, lane, warp, act);
+        RevStage<N, -1, kWarps, 2>::template run<true>(stw, sb, sb, slot, sub, warp, act);
         __syncthreads();
     }
-    RevStage<N, -1, kWarps, nst - 1>::template run<false>(stw, sb, xr, lane, warp, act);
+    RevStage<N, -1, kWarps, nst - 1>::template run<false>(stw, sb, xr, slot, sub, warp, act);
 }
 
 // ------------------------------------------------------------------ K4
-template <typename T, int N>
-__global__ void __launch_bounds__(kThreads) k4_ct(DevTables t, const V2<T>* __restrict__ tw3,
-                                                 const V2<T>* __restrict__ cyl, V2<T>* __restrict__ out, T scale) {
-    using V = V2<T>;
+template <int N>
+__global__ void __launch_bounds__(kThreads) k4_ct(DevTables t, const float2* __restrict__ tw3,
+                                                 const float2* __restrict__ cyl, float2* __restrict__ out, float scale) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    V* buf = reinterpret_cast<V*>(smem_raw);
-    V* stw = buf + N * kLd;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    float2* buf = reinterpret_cast<float2*>(smem_raw);
+    float2* stw = buf + N * kLdP;
     const int tile = blockIdx.x;
     const long long b = blockIdx.y;
-    load_tw<T>(stw, tw3, N);
+    load_tw<float>(stw, tw3, N);
     const int s0 = t.tile_ptr[tile], lines = t.tile_ptr[tile + 1] - s0;
-    rows_in_ct<N>(buf, cyl + b * (long long)t.S * N, t.tile_sticks + s0, lines);
+    rows_in_p<N>(buf, cyl + b * (long long)t.S * N, t.tile_sticks + s0, lines);
     __syncthreads();
-    fft_ct<N, -1, kWarps, false, true, true>(stw, Smem<V>{buf}, Smem<V>{buf}, buf, lane, warp, lane < lines);
+    fft_ct<N, -1, kWarps, false, true, true>(stw, SmemP{buf}, SmemP{buf}, buf, slot_of(), sub_of(), warp_of(),
+                                             2 * slot_of() < lines);
     __syncthreads();
-    gather_entries(t.tile_pw, t.tile_pw_ptr[tile], t.tile_pw_ptr[tile + 1], buf, out + b * t.npw, scale);
+    gather_entries_p(t.tile_pw, t.tile_pw_ptr[tile], t.tile_pw_ptr[tile + 1], buf, out + b * t.npw, scale);
 }
 
 // ------------------------------------------------------------ launchers
-template <typename T, int N> struct LaunchCTImpl {
-    static constexpr size_t sm = ct_smem<N>(sizeof(V2<T>));
+template <int N> struct CtSmem {
+    static constexpr size_t sm = ct_smem<N>();
     template <class K> static cudaError_t ensure(K kernel) {
         if (sm <= 48 * 1024) return cudaSuccess;
         return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
@@ -207,10 +279,11 @@ template <typename T, int N> struct LaunchCTImpl {
 template <typename T, int N>
 int LaunchCT<T, N>::k1(const DevTables& t, const void* tw3, const void* coeffs, long long nb, void* cyl,
                        cudaStream_t st) {
-    static const cudaError_t once = LaunchCTImpl<T, N>::ensure(k1_ct<T, N>);
+    static_assert(std::is_same<T, float>::value, "compile-time kernels are FP32");
+    static const cudaError_t once = CtSmem<N>::ensure(k1_ct<N>);
     if (once) return (int)once;
-    k1_ct<T, N><<<dim3(t.T, (unsigned)nb), kThreads, LaunchCTImpl<T, N>::sm, st>>>(
-        t, (const V2<T>*)tw3, (const V2<T>*)coeffs, (V2<T>*)cyl);
+    k1_ct<N><<<dim3(t.T, (unsigned)nb), kThreads, CtSmem<N>::sm, st>>>(t, (const float2*)tw3, (const float2*)coeffs,
+                                                                       (float2*)cyl);
     return (int)cudaGetLastError();
 }
 template <typename T, int N>
@@ -218,32 +291,32 @@ int LaunchCT<T, N>::k2(int sign, const DevTables& t, const void* tw2, long long 
                        cudaStream_t st) {
     const dim3 grid(t.NP, (t.n3 + kLines - 1) / kLines, (unsigned)nb);
     if (sign > 0) {
-        static const cudaError_t once = LaunchCTImpl<T, N>::ensure(k2_ct<T, +1, N>);
+        static const cudaError_t once = CtSmem<N>::ensure(k2_ct<+1, N>);
         if (once) return (int)once;
-        k2_ct<T, +1, N><<<grid, kThreads, LaunchCTImpl<T, N>::sm, st>>>(t, (const V2<T>*)tw2, (V2<T>*)cyl, (V2<T>*)slab);
+        k2_ct<+1, N><<<grid, kThreads, CtSmem<N>::sm, st>>>(t, (const float2*)tw2, (float2*)cyl, (float2*)slab);
     } else {
-        static const cudaError_t once = LaunchCTImpl<T, N>::ensure(k2_ct<T, -1, N>);
+        static const cudaError_t once = CtSmem<N>::ensure(k2_ct<-1, N>);
         if (once) return (int)once;
-        k2_ct<T, -1, N><<<grid, kThreads, LaunchCTImpl<T, N>::sm, st>>>(t, (const V2<T>*)tw2, (V2<T>*)cyl, (V2<T>*)slab);
+        k2_ct<-1, N><<<grid, kThreads, CtSmem<N>::sm, st>>>(t, (const float2*)tw2, (float2*)cyl, (float2*)slab);
     }
     return (int)cudaGetLastError();
 }
 template <typename T, int N>
 int LaunchCT<T, N>::k3(const DevTables& t, const void* tw1, const void* V, long long nb, void* slab, cudaStream_t st) {
-    static const cudaError_t once = LaunchCTImpl<T, N>::ensure(k3_ct<T, N>);
+    static const cudaError_t once = CtSmem<N>::ensure(k3_ct<N>);
     if (once) return (int)once;
     const dim3 grid(t.n2, (t.n3 + kLines - 1) / kLines, (unsigned)nb);
-    k3_ct<T, N><<<grid, kThreads, LaunchCTImpl<T, N>::sm, st>>>(t, (const V2<T>*)tw1, (const T*)V, (V2<T>*)slab);
+    k3_ct<N><<<grid, kThreads, CtSmem<N>::sm, st>>>(t, (const float2*)tw1, (const float*)V, (float2*)slab);
     return (int)cudaGetLastError();
 }
 template <typename T, int N>
 int LaunchCT<T, N>::k4(const DevTables& t, const void* tw3, const void* cyl, long long nb, void* out,
                        cudaStream_t st) {
-    static const cudaError_t once = LaunchCTImpl<T, N>::ensure(k4_ct<T, N>);
+    static const cudaError_t once = CtSmem<N>::ensure(k4_ct<N>);
     if (once) return (int)once;
-    const T scale = (T)(1.0 / ((double)t.n1 * t.n2 * t.n3));
-    k4_ct<T, N><<<dim3(t.T, (unsigned)nb), kThreads, LaunchCTImpl<T, N>::sm, st>>>(
-        t, (const V2<T>*)tw3, (const V2<T>*)cyl, (V2<T>*)out, scale);
+    const float scale = (float)(1.0 / ((double)t.n1 * t.n2 * t.n3));
+    k4_ct<N><<<dim3(t.T, (unsigned)nb), kThreads, CtSmem<N>::sm, st>>>(t, (const float2*)tw3, (const float2*)cyl,
+                                                                       (float2*)out, scale);
     return (int)cudaGetLastError();
 }
 

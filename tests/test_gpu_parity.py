@@ -75,7 +75,7 @@ def test_full_size_1024_bands_sampled(prec, n):
     g, c, V = make_case(n, R, nb, seed=2, prec=prec)
     plan, _, _, out = run(n, g, c, V, prec)
     chunk = plan.info()["chunk_bands"]
-    bands = sorted({0, chunk - 1, chunk, nb // 2, nb - 1})
+    bands = sorted({b for b in (0, chunk - 1, chunk, nb // 2, nb - 1) if b < nb})
     err = rel_l2_per_band(out.cpu().numpy()[bands], oracle_apply(n, g, c, V, bands))
     assert err.max() < TOL[prec], err.max()
 
