@@ -251,7 +251,13 @@ def run_ours(args, rank, world, local_rank):
         c_d = torch.from_numpy(synth.coefficients(g, NBANDS, seed=SEED)).to("cuda", cdt)
         V_d = torch.from_numpy(synth.potential(*GRID, "smooth", SEED + 1000)[0]).to("cuda", rdt)
         out_d = torch.empty_like(c_d)
-        plan = vloc.VlocPlan(GRID, g, cdt, chunk=args.chunk, generic=args.generic)
+        grid = tuple(int(x) for x in args.grid.split(","))
+        if grid != GRID:
+            g = synth.sphere_glist(*grid, min(grid) // 4)
+            c_d = torch.from_numpy(synth.coefficients(g, NBANDS, seed=SEED)).to("cuda", cdt)
+            V_d = torch.from_numpy(synth.potential(*grid, "smooth", SEED + 1000)[0]).to("cuda", rdt)
+            out_d = torch.empty_like(c_d)
+        plan = vloc.VlocPlan(grid, g, cdt, chunk=args.chunk, generic=args.generic)
         ms = time_steps(lambda: plan.apply(c_d, V_d, out=out_d), args.steps, args.warmup, stream, dist_on)
         plan.profile(True)
         for _ in range(args.steps):
@@ -260,6 +266,7 @@ def run_ours(args, rank, world, local_rank):
         plan.profile(False)
         if rank == 0:
             print(json.dumps({"only": "headline", "prec": args.prec, "bands": NBANDS, "steps": args.steps,
+                              "grid": list(grid),
                               "chunk": plan.info()["chunk_bands"], "generic": args.generic,
                               "ms_per_step": ms / args.steps, "bands_per_s": world * NBANDS * args.steps / ms * 1e3,
                               "kernel_ms_per_step": sum(t for _, t in prof.values()) / args.steps,
@@ -426,6 +433,7 @@ def main():
     ap.add_argument("--prec", choices=["f32", "f64"], default="f32", help="precision of --only headline")
     ap.add_argument("--chunk", type=int, default=0, help="bands per workspace chunk (0: the plan's default)")
     ap.add_argument("--generic", action="store_true", help="runtime-radix kernels only (--only headline)")
+    ap.add_argument("--grid", default="96,96,96", help="grid of --only headline (n1,n2,n3; R = n/4)")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3
