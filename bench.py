@@ -32,7 +32,8 @@ GRID, R, NBANDS, SEED = (96, 96, 96), 24, 1024, 2
 GRID2 = (96, 96, 120)
 FALLBACK_HBM_GBS = 6800.0
 FP64_NOMINAL_GFLOPS = 1250.0   # 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz ~ 1.26 TF/s
-KERNEL_SOURCES = ["paper_1601_07378_gb300/csrc/kernels_impl.cuh", "paper_1601_07378_gb300/csrc/fft_core.cuh"]
+KERNEL_SOURCES = ["paper_1601_07378_gb300/csrc/fft_core.cuh", "paper_1601_07378_gb300/csrc/fft_ct.cuh",
+                  "paper_1601_07378_gb300/csrc/kernels_impl.cuh", "paper_1601_07378_gb300/csrc/kernels_ct.cuh"]
 
 
 def env_int(name, default):
