@@ -176,12 +176,8 @@ def time_steps(fn, steps, warmup, stream, dist_on):
     torch.cuda.synchronize()
     if dist_on:
         dist.barrier()
-    ms = start.elapsed_time(stop)
-    if dist_on:
-        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    return ms
+    from paper_1601_07378_gb300.dist import max_over_ranks
+    return max_over_ranks(start.elapsed_time(stop), device="cuda")
 
 
 def cpu_oracle_rate(n, g, c, V, nbands_sample):
@@ -363,11 +359,8 @@ def run_ours(args, rank, world, local_rank):
     t0 = time.perf_counter()
     for _ in range(ke):
         plan.apply_host(c_h, V_h, o_h)
-    dt = time.perf_counter() - t0
-    if dist_on:
-        t = torch.tensor([dt], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        dt = float(t.item())
+    from paper_1601_07378_gb300.dist import max_over_ranks
+    dt = max_over_ranks(time.perf_counter() - t0, device="cuda")
     e2e = {"value": world * NBANDS * ke / dt, "unit": "bands/s", "steps": ke,
            "h2d_bytes_per_step": c_h.numel() * 8 + V_h.numel() * 4, "d2h_bytes_per_step": o_h.numel() * 8}
 
