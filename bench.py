@@ -347,6 +347,49 @@ def run_ours(args, rank, world, local_rank):
            "hbm_frac_of_B5": f64_value / world / (peak * 1e9 / (2 * B5))}
     del plan64, c128_d, o128_d, V64_d
 
+    # ---- uneven multi-instance batch, one graph launch per step: 8 grids
+    # 48^3 .. 144^3, R = n/4, 64 (i+1) bands each (FP32)
+    batched = None
+    if not args.no_extra:
+        insts = []
+        for i, m in enumerate(synth.BATCH_GRIDS):
+            nn = (m, m, m)
+            gi = synth.sphere_glist(*nn, m / 4)
+            nbi = 64 * (i + 1)
+            pi = vloc.VlocPlan(nn, gi, torch.complex64, graph=True, chunk=nbi)
+            ci = torch.from_numpy(synth.coefficients(gi, nbi, seed=3 + i, dtype=np.complex64)).cuda()
+            Vi = torch.from_numpy(synth.potential(*nn, "smooth", 1003 + i)[0].astype(np.float32)).cuda()
+            insts.append((pi, ci, Vi, torch.empty_like(ci)))
+        bplans, bcs, bVs, bouts = zip(*insts)
+        kb = max(3, args.steps // 4)
+        msb = time_steps(lambda: vloc.apply_batched(bplans, bcs, bVs, bouts), kb, 2, stream, dist_on)
+        nb_tot = sum(c.shape[0] for c in bcs)
+        batched = {"value": world * nb_tot / (msb / kb / 1e3), "unit": "bands/s", "ms_per_step": msb / kb,
+                   "bands_per_step": nb_tot, "launches_per_step": "1 graph launch",
+                   "what": "8 instances 48^3..144^3, R = n/4, 64..512 bands, FP32, one CUDA graph"}
+        del insts, bplans, bcs, bVs, bouts
+
+    # ---- differentiable apply: loss = sum_n <psi_n|V|psi_n> + ||V psi - t||^2,
+    # 512 bands at 96^3 FP32, forward + backward (dL/dc, dL/dV)
+    autograd = None
+    if not args.no_extra:
+        na = 512
+        ca = c_d[:na].clone().requires_grad_(True)
+        Va = V_d.clone().requires_grad_(True)
+        ta = (torch.randn(na, info["npw"], dtype=torch.complex64, device="cuda") * 0.01)
+
+        def fwd_bwd():
+            ca.grad = None
+            Va.grad = None
+            o = vloc.vloc_apply(ca, Va, plan)
+            L = (torch.conj(ca) * o).real.sum() + ((o - ta).abs() ** 2).sum()
+            L.backward()
+        ka = max(3, args.steps // 4)
+        msa = time_steps(fwd_bwd, ka, 2, stream, dist_on)
+        autograd = {"value": world * na / (msa / ka / 1e3), "unit": "bands/s (forward + backward)",
+                    "ms_per_step": msa / ka, "bands": na, "what": "96^3 FP32, loss <psi|V|psi> + ||V psi - t||^2"}
+        del ca, Va, ta
+
     # ---- end to end through the host-buffer entry point (pinned host memory)
     c_h = torch.from_numpy(c64).pin_memory()
     V_h = torch.from_numpy(V96.astype(np.float32)).pin_memory()
@@ -404,6 +447,7 @@ def run_ours(args, rank, world, local_rank):
             "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clocks,
             "fp64": f64, "adjoint": {"value": adj, "unit": "bands/s"},
             "grid_96x96x120": {"value": c2_value, "unit": "bands/s"},
+            "batched_uneven": batched, "autograd_512": autograd,
             "cufft_comparison": cufft,
         }
         print(json.dumps(line), flush=True)
@@ -421,6 +465,7 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-cufft", action="store_true", help="skip the torch.fft comparison")
+    ap.add_argument("--no-extra", action="store_true", help="skip the batched and autograd legs")
     ap.add_argument("--only", choices=["all", "headline"], default="all",
                     help="headline: only the FP32 forward steps (for profiler launch lists)")
     ap.add_argument("--bands", type=int, default=NBANDS, help="bands per GPU per step (default 1024)")

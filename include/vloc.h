@@ -62,7 +62,12 @@ extern "C" {
 #define VLOC_PARTITION_GREEDY   0x000  /* Sec. 3.2 sorted round-robin (default)     */
 #define VLOC_PARTITION_BASIC    0x010  /* Sec. 4.1 cyclic row/column groups         */
 #define VLOC_PARTITION_IMPROVED 0x020  /* Sec. 4.2 plane-sorted row/column groups   */
-#define VLOC_GRAPH              0x100  /* replay apply chains as CUDA graphs        */
+#define VLOC_GRAPH              0x100  /* replay apply chains as CUDA graphs: the    */
+                                       /* first call with a given set of pointers   */
+                                       /* and band count captures the launches into */
+                                       /* a graph (kept per plan, 8 most recent),   */
+                                       /* later calls replay it with one launch.    */
+                                       /* Buffers must stay valid while cached.     */
 #define VLOC_GENERIC_KERNELS    0x400  /* use the runtime-radix kernels for every   */
                                        /* axis (the compile-time-length kernels are */
                                        /* the default where one exists)             */

@@ -54,7 +54,7 @@ template <typename T> struct Launch {
     static int k4(const DevTables& t, const LaunchAxes& ax, const void* tw3, const void* cyl, long long nb, void* out,
                   cudaStream_t st);
     static int k3b(const DevTables& t, const LaunchAxes& ax, const void* tw1, const void* sc, const void* sg,
-                   long long nb, double* acc, cudaStream_t st);
+                   long long nb, int ngroups, double* partial, cudaStream_t st);
     static int finish_grad(const double* acc, void* g, long long N, cudaStream_t st);
 };
 extern template struct Launch<float>;
@@ -68,6 +68,8 @@ template <typename T, int N> struct LaunchCT {
     static int k2(int sign, const DevTables& t, const void* tw2, long long nb, void* cyl, void* slab, cudaStream_t st);
     static int k3(const DevTables& t, const void* tw1, const void* V, long long nb, void* slab, cudaStream_t st);
     static int k4(const DevTables& t, const void* tw3, const void* cyl, long long nb, void* out, cudaStream_t st);
+    static int k3b(const DevTables& t, const void* tw1, const void* sc, const void* sg, long long nb, int bpg,
+                   double* partial, cudaStream_t st);
 };
 
 // Precision dispatch (kernels.cu): dbl = 0 for float, 1 for double; `fast`
@@ -81,8 +83,12 @@ int launch_k3_xpass_v(int dbl, int fast, const DevTables& t, const LaunchAxes& a
                       long long nb, void* slab, cudaStream_t st);
 int launch_k4_zpass_gather(int dbl, int fast, const DevTables& t, const LaunchAxes& ax, const void* tw3, const void* cyl,
                            long long nb, void* out, cudaStream_t st);
-int launch_k3b_grad_v(int dbl, const DevTables& t, const LaunchAxes& ax, const void* tw1, const void* slab_c,
-                      const void* slab_g, long long nb, double* acc, cudaStream_t st);
+// dL/dV x-pass over nb bands in groups of at most `bpg` bands; each group's
+// partial sum goes to partial[group][N]; launch_reduce_partials then adds the
+// groups (in order) into acc.  Returns the groups used via *used.
+int launch_k3b_grad_v(int dbl, int fast, const DevTables& t, const LaunchAxes& ax, const void* tw1, const void* slab_c,
+                      const void* slab_g, long long nb, int bpg, double* partial, int* used, cudaStream_t st);
+int launch_reduce_partials(const double* partial, int ngroups, long long N, double* acc, cudaStream_t st);
 int launch_finish_grad_v(int dbl, const double* acc, void* gradV, long long N, cudaStream_t st);
 int launch_zero_f64(double* p, long long n, cudaStream_t st);
 size_t smem_bytes_for(int dbl, int n);

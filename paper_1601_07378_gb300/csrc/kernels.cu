@@ -89,11 +89,32 @@ int launch_k4_zpass_gather(int dbl, int fast, const DevTables& t, const LaunchAx
     }
     return dbl ? Launch<double>::k4(t, ax, tw3, cyl, nb, out, st) : Launch<float>::k4(t, ax, tw3, cyl, nb, out, st);
 }
-int launch_k3b_grad_v(int dbl, const DevTables& t, const LaunchAxes& ax, const void* tw1, const void* slab_c,
-                      const void* slab_g, long long nb, double* acc, cudaStream_t st) {
-    return dbl ? Launch<double>::k3b(t, ax, tw1, slab_c, slab_g, nb, acc, st)
-               : Launch<float>::k3b(t, ax, tw1, slab_c, slab_g, nb, acc, st);
+int launch_k3b_grad_v(int dbl, int fast, const DevTables& t, const LaunchAxes& ax, const void* tw1, const void* slab_c,
+                      const void* slab_g, long long nb, int bpg, double* partial, int* used, cudaStream_t st) {
+    const int ng = (int)((nb + bpg - 1) / bpg);
+    *used = ng;
+    if (!dbl && fast) switch (t.n1) {
+#define VLOC_CASE(N) case N: return LaunchCT<float, N>::k3b(t, tw1, slab_c, slab_g, nb, bpg, partial, st);
+        VLOC_CT_SIZES(VLOC_CASE)
+#undef VLOC_CASE
+        default: break;
+    }
+    return dbl ? Launch<double>::k3b(t, ax, tw1, slab_c, slab_g, nb, ng, partial, st)
+               : Launch<float>::k3b(t, ax, tw1, slab_c, slab_g, nb, ng, partial, st);
 }
+
+__global__ void k_reduce_partials(const double* __restrict__ partial, int ng, long long N, double* __restrict__ acc) {
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    double s = acc[i];
+    for (int g = 0; g < ng; ++g) s += partial[(long long)g * N + i];
+    acc[i] = s;
+}
+int launch_reduce_partials(const double* partial, int ngroups, long long N, double* acc, cudaStream_t st) {
+    k_reduce_partials<<<(unsigned)((N + 255) / 256), 256, 0, st>>>(partial, ngroups, N, acc);
+    return (int)cudaGetLastError();
+}
+
 int launch_finish_grad_v(int dbl, const double* acc, void* gradV, long long N, cudaStream_t st) {
     return dbl ? Launch<double>::finish_grad(acc, gradV, N, st) : Launch<float>::finish_grad(acc, gradV, N, st);
 }

@@ -267,6 +267,93 @@ __global__ void __launch_bounds__(kThreads) k4_ct(DevTables t, const float2* __r
     gather_entries_p(t.tile_pw, t.tile_pw_ptr[tile], t.tile_pw_ptr[tile + 1], buf, out + b * t.npw, scale);
 }
 
+// ----------------------------------------------------------------- K3b
+// dL/dV x-pass for one (y, z tile, band group): psi = inverse x-FFT of the
+// c-slab tile (kept in buffer A), g = inverse x-FFT of the grad-slab tile
+// (its last stage stays in registers), acc += Re(conj(g) psi) per element in
+// FP32 over the group's bands (at most 16), then the group's partial sum,
+// times 1/N, is written in FP64; groups are added later in a fixed order.
+template <int N>
+__global__ void __launch_bounds__(kThreads) k3b_ct(DevTables t, const float2* __restrict__ tw1,
+                                                  const float2* slab_c, const float2* slab_g, int nb, int bpg,
+                                                  double* __restrict__ partial, double invN) {
+    using SC = Sched<N>;
+    constexpr int nst = SC::nst;
+    static_assert(nst >= 2, "compile-time x-pass needs at least two stages");
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int n2 = t.n2, n3 = t.n3;
+    float2* bufA = reinterpret_cast<float2*>(smem_raw);
+    float2* bufB = bufA + N * kLdP;
+    float2* stw = bufB + N * kLdP;
+    int* xrow = reinterpret_cast<int*>(stw + N);
+    const int slot = slot_of(), sub = sub_of(), warp = warp_of();
+    const int y = blockIdx.x;
+    const int z0 = blockIdx.y * kLines;
+    const int grp = blockIdx.z;
+    const int lines = min(kLines, n3 - z0);
+    const bool act = 2 * slot < lines;
+    load_tw<float>(stw, tw1, N);
+    for (int e = threadIdx.x; e < N; e += kThreads) xrow[e] = t.xrow_plane[e];
+    __syncthreads();
+    const long long pstride = (long long)n2 * n3;
+    using L = NatStage<N, +1, kWarps, nst - 1>;
+    constexpr int R = SC::R(nst - 1);
+    float2 acc[L::U][R];
+#pragma unroll
+    for (int u = 0; u < L::U; ++u)
+#pragma unroll
+        for (int r = 0; r < R; ++r) acc[u][r] = make_float2(0.f, 0.f);
+    SmemP sa{bufA}, sb{bufB};
+    const int b1 = min(nb, (grp + 1) * bpg);
+    for (int b = grp * bpg; b < b1; ++b) {
+        XRowsP xc{const_cast<float2*>(slab_c) + (long long)b * t.NP * pstride + (long long)y * n3 + z0, xrow, pstride};
+        XRowsP xg{const_cast<float2*>(slab_g) + (long long)b * t.NP * pstride + (long long)y * n3 + z0, xrow, pstride};
+        fft_ct<N, +1, kWarps, false, false, true>(stw, xc, sa, bufA, slot, sub, warp, act);  // psi -> A
+        NatStage<N, +1, kWarps, 0>::template run<false>(stw, xg, sb, slot, sub, warp, act);
+        __syncthreads();
+        if constexpr (nst >= 3) {
+            NatStage<N, +1, kWarps, 1>::template run<true>(stw, sb, sb, slot, sub, warp, act);
+            __syncthreads();
+        }
+        if constexpr (nst >= 4) {
+            NatStage<N, +1, kWarps, 2>::template run<true>(stw, sb, sb, slot, sub, warp, act);
+            __syncthreads();
+        }
+        if (act) {
+            P2f h[L::U][R];
+            L::compute(h, stw, sb, slot, sub, warp);
+#pragma unroll
+            for (int u = 0; u < L::U; ++u) {
+                const int i = 2 * (warp + u * kWarps) + sub;
+                if (L::NI % (2 * kWarps) == 0 || i < L::NI) {
+#pragma unroll
+                    for (int r = 0; r < R; ++r) {
+                        const P2f p = sa(i + r * L::NI, slot);
+                        acc[u][r].x += h[u][r].a.x * p.a.x + h[u][r].a.y * p.a.y;
+                        acc[u][r].y += h[u][r].b.x * p.b.x + h[u][r].b.y * p.b.y;
+                    }
+                }
+            }
+        }
+        __syncthreads();
+    }
+    if (act) {
+        double* part = partial + (long long)grp * t.n1 * pstride + (long long)y * n3 + z0 + 2 * slot;
+#pragma unroll
+        for (int u = 0; u < L::U; ++u) {
+            const int i = 2 * (warp + u * kWarps) + sub;
+            if (L::NI % (2 * kWarps) == 0 || i < L::NI) {
+#pragma unroll
+                for (int r = 0; r < R; ++r) {
+                    double* q = part + (long long)(i + r * L::NI) * pstride;
+                    q[0] = (double)acc[u][r].x * invN;
+                    q[1] = (double)acc[u][r].y * invN;
+                }
+            }
+        }
+    }
+}
+
 // ------------------------------------------------------------ launchers
 template <int N> struct CtSmem {
     static constexpr size_t sm = ct_smem<N>();
@@ -307,6 +394,20 @@ int LaunchCT<T, N>::k3(const DevTables& t, const void* tw1, const void* V, long 
     if (once) return (int)once;
     const dim3 grid(t.n2, (t.n3 + kLines - 1) / kLines, (unsigned)nb);
     k3_ct<N><<<grid, kThreads, CtSmem<N>::sm, st>>>(t, (const float2*)tw1, (const float*)V, (float2*)slab);
+    return (int)cudaGetLastError();
+}
+template <typename T, int N>
+int LaunchCT<T, N>::k3b(const DevTables& t, const void* tw1, const void* sc, const void* sg, long long nb, int bpg,
+                        double* partial, cudaStream_t st) {
+    constexpr size_t sm = 2 * (size_t)N * kLdP * sizeof(float2) + (size_t)N * sizeof(float2) + (size_t)N * sizeof(int) + 16;
+    static const cudaError_t once =
+        sm <= 48 * 1024 ? cudaSuccess : cudaFuncSetAttribute(k3b_ct<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (once) return (int)once;
+    const int ng = (int)((nb + bpg - 1) / bpg);
+    const dim3 grid(t.n2, (t.n3 + kLines - 1) / kLines, ng);
+    const double invN = 1.0 / ((double)t.n1 * t.n2 * t.n3);
+    k3b_ct<N><<<grid, kThreads, sm, st>>>(t, (const float2*)tw1, (const float2*)sc, (const float2*)sg, (int)nb, bpg,
+                                          partial, invN);
     return (int)cudaGetLastError();
 }
 template <typename T, int N>

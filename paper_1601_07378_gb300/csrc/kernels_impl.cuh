@@ -265,8 +265,8 @@ template <typename T> struct AccumProduct {
 
 template <typename T>
 __global__ void __launch_bounds__(kThreads) k3b_grad_v(DevTables t, AxisPlan ax, const V2<T>* __restrict__ tw1,
-                                                      const V2<T>* slab_c, const V2<T>* slab_g, int nb,
-                                                      double* __restrict__ accg, double invN) {
+                                                      const V2<T>* slab_c, const V2<T>* slab_g, int nb, int bpg,
+                                                      double* __restrict__ partial, double invN) {
     using V = V2<T>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int n1 = t.n1, n2 = t.n2, n3 = t.n3;
@@ -278,6 +278,7 @@ __global__ void __launch_bounds__(kThreads) k3b_grad_v(DevTables t, AxisPlan ax,
     int* xrow = reinterpret_cast<int*>(acc + n1 * kLd);
     const int y = blockIdx.x;
     const int z0 = blockIdx.y * kLines;
+    const int grp = blockIdx.z;
     const int lines = min(kLines, n3 - z0);
     load_tw<T>(stw, tw1, n1);
     for (int e = threadIdx.x; e < n1; e += kThreads) xrow[e] = t.xrow_plane[e];
@@ -288,7 +289,8 @@ __global__ void __launch_bounds__(kThreads) k3b_grad_v(DevTables t, AxisPlan ax,
     // two buffers that are not D1.
     V* D1 = final_buf(ax.nst, P, Q);
     V* G1 = (D1 == P) ? Q : P;
-    for (int b = 0; b < nb; ++b) {
+    const int b1 = min(nb, (grp + 1) * bpg);
+    for (int b = grp * bpg; b < b1; ++b) {
         XRows<T> xc{const_cast<V*>(slab_c) + (long long)b * t.NP * pstride + (long long)y * n3 + z0, xrow, pstride};
         XRows<T> xg{const_cast<V*>(slab_g) + (long long)b * t.NP * pstride + (long long)y * n3 + z0, xrow, pstride};
         fft_lines<+1>(ax, stw, xc, Smem<V>{D1}, P, Q, lines);
@@ -296,12 +298,12 @@ __global__ void __launch_bounds__(kThreads) k3b_grad_v(DevTables t, AxisPlan ax,
         fft_lines<+1>(ax, stw, xg, AccumProduct<T>{D1, acc}, G1, R3, lines);
         __syncthreads();
     }
+    // this band group's partial sum (overwritten; summed over groups later
+    // in a fixed order, so the result is deterministic)
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    double* part = partial + (long long)grp * n1 * pstride;
     if (lane < lines) {
-        for (int e = warp; e < n1; e += kWarps) {
-            double* dst = accg + ((long long)e * n2 + y) * n3 + z0 + lane;
-            *dst += acc[e * kLd + lane] * invN;
-        }
+        for (int e = warp; e < n1; e += kWarps) part[((long long)e * n2 + y) * n3 + z0 + lane] = acc[e * kLd + lane] * invN;
     }
 }
 
@@ -378,11 +380,13 @@ int Launch<T>::k4(const DevTables& t, const LaunchAxes& ax, const void* tw3, con
 }
 template <typename T>
 int Launch<T>::k3b(const DevTables& t, const LaunchAxes& ax, const void* tw1, const void* sc, const void* sg,
-                   long long nb, double* acc, cudaStream_t st) {
-    const dim3 grid(t.n2, (t.n3 + kLines - 1) / kLines);
+                   long long nb, int ngroups, double* partial, cudaStream_t st) {
+    const int bpg = (int)((nb + ngroups - 1) / ngroups);
+    const int ng = (int)((nb + bpg - 1) / bpg);
+    const dim3 grid(t.n2, (t.n3 + kLines - 1) / kLines, ng);
     const double invN = 1.0 / ((double)t.n1 * t.n2 * t.n3);
     k3b_grad_v<T><<<grid, kThreads, smem_grad(t.n1), st>>>(t, axis_of(ax, 0), (const V2<T>*)tw1, (const V2<T>*)sc,
-                                                           (const V2<T>*)sg, (int)nb, acc, invN);
+                                                           (const V2<T>*)sg, (int)nb, bpg, partial, invN);
     return (int)cudaGetLastError();
 }
 template <typename T> int Launch<T>::finish_grad(const double* acc, void* g, long long N, cudaStream_t st) {

@@ -40,6 +40,7 @@ int cuda_fail(cudaError_t e, const char* what) {
     } while (0)
 
 const int kRadices[] = {16, 15, 12, 10, 9, 8, 6, 5, 4, 3, 2};
+constexpr long long kGradBandsPerGroup = 16;  // bands per group of the dL/dV x-pass (FP32 sums)
 constexpr int kLinesPerTile = 32;
 
 bool smooth235(int n) {
@@ -101,6 +102,7 @@ struct vloc_plan_s {
     long long npw = 0, N = 0;
     int S = 0, NP = 0, P = 0, T = 0;
     int fast = 1;  // compile-time-length kernels where available
+    int ngroups = 1;  // band groups of the dL/dV x-pass
     long long chunk = 1, ws_bands = 2;
     size_t elem = 8;
     LaunchAxes ax{};
@@ -120,11 +122,22 @@ struct vloc_plan_s {
     void* d_stage = nullptr;
     size_t stage_bytes = 0;
     long long stage_bands = 0;
-    cudaStream_t copy_stream = nullptr;
+    cudaStream_t copy_stream = nullptr;  // host-to-device copies
+    cudaStream_t d2h_stream = nullptr;   // device-to-host copies
     cudaEvent_t ev[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
     int device = 0;
     int smem_optin = 0;
     std::mutex mu;
+    // CUDA graphs of apply chains (VLOC_GRAPH), keyed by the call's pointers
+    struct GraphEntry {
+        std::vector<uintptr_t> key;
+        cudaGraphExec_t exec = nullptr;
+        std::vector<std::pair<vloc_plan_s*, long long>> kernels;  // kernels per plan in the graph
+        unsigned long long last_use = 0;
+    };
+    std::vector<GraphEntry> graphs;
+    cudaStream_t cap_stream = nullptr;
+    unsigned long long use_clock = 0;
     // launch accounting and optional per-launch event timing
     long long launches = 0;
     bool prof_on = false;
@@ -161,9 +174,13 @@ static void free_plan(vloc_plan p) {
     cudaFree(p->d_acc);
     cudaFree(p->d_stage);
     for (cudaEvent_t e : p->prof_pool) cudaEventDestroy(e);
+    for (auto& g : p->graphs)
+        if (g.exec) cudaGraphExecDestroy(g.exec);
+    if (p->cap_stream) cudaStreamDestroy(p->cap_stream);
     for (cudaEvent_t e : p->ev)
         if (e) cudaEventDestroy(e);
     if (p->copy_stream) cudaStreamDestroy(p->copy_stream);
+    if (p->d2h_stream) cudaStreamDestroy(p->d2h_stream);
     delete p;
 }
 
@@ -382,10 +399,12 @@ int vloc_plan_create(vloc_plan* out, int n1, int n2, int n3, const int32_t* g, i
     chunk = std::min<long long>(chunk, 65535);
     p->chunk = chunk;
     p->ws_bands = std::max<long long>(chunk, 2);
-    p->ws_bytes = per_band * (size_t)p->ws_bands + (size_t)N * sizeof(double);
+    p->ngroups = (int)((std::max<long long>(1, p->ws_bands / 2) + kGradBandsPerGroup - 1) / kGradBandsPerGroup);
+    p->ws_bytes = per_band * (size_t)p->ws_bands + (size_t)N * sizeof(double) * (1 + p->ngroups);
     if ((e = cudaMalloc(&p->d_cyl, (size_t)S * n3 * elem * p->ws_bands))) { free_plan(p); return cuda_fail(e, "cudaMalloc(cylinder)"); }
     if ((e = cudaMalloc(&p->d_slab, (size_t)NP * n2 * n3 * elem * p->ws_bands))) { free_plan(p); return cuda_fail(e, "cudaMalloc(slab)"); }
-    if ((e = cudaMalloc(&p->d_acc, (size_t)N * sizeof(double)))) { free_plan(p); return cuda_fail(e, "cudaMalloc(acc)"); }
+    // dL/dV accumulator [N] followed by the band groups' partial sums [ngroups][N]
+    if ((e = cudaMalloc(&p->d_acc, (size_t)N * sizeof(double) * (1 + p->ngroups)))) { free_plan(p); return cuda_fail(e, "cudaMalloc(acc)"); }
     if ((e = cudaStreamSynchronize(st))) { free_plan(p); return cuda_fail(e, "plan create sync"); }
     *out = p;
     return VLOC_OK;
@@ -466,9 +485,78 @@ static int apply_impl(vloc_plan p, const void* c, const void* V, int64_t nb, voi
     return VLOC_OK;
 }
 
+}  // extern "C"
+
+// Replay (or capture, then replay) the work `enqueue` puts on a stream as one
+// CUDA graph, cached in `owner` under `key`; `plans` are the plans whose
+// kernels the work launches.  Captured on the owner's private stream, then
+// launched on `st`, so it stays ordered with the caller's work.
+template <class F>
+static int graph_run(vloc_plan owner, const std::vector<vloc_plan>& plans, std::vector<uintptr_t> key,
+                     cudaStream_t st, F&& enqueue) {
+    cudaError_t e;
+    for (auto& g : owner->graphs)
+        if (g.key == key) {
+            g.last_use = ++owner->use_clock;
+            if ((e = cudaGraphLaunch(g.exec, st))) return cuda_fail(e, "cudaGraphLaunch");
+            for (auto& k : g.kernels) k.first->launches += k.second;
+            return VLOC_OK;
+        }
+    if (!owner->cap_stream && (e = cudaStreamCreateWithFlags(&owner->cap_stream, cudaStreamNonBlocking)))
+        return cuda_fail(e, "capture stream");
+    std::vector<long long> l0;
+    std::vector<bool> prof;
+    for (vloc_plan q : plans) {
+        l0.push_back(q->launches);
+        prof.push_back(q->prof_on);
+        q->prof_on = false;  // no timing events inside a graph
+    }
+    auto restore = [&] {
+        for (size_t i = 0; i < plans.size(); ++i) plans[i]->prof_on = prof[i];
+    };
+    if ((e = cudaStreamBeginCapture(owner->cap_stream, cudaStreamCaptureModeThreadLocal))) {
+        restore();
+        return cuda_fail(e, "cudaStreamBeginCapture");
+    }
+    const int rc = enqueue(owner->cap_stream);
+    cudaGraph_t graph = nullptr;
+    e = cudaStreamEndCapture(owner->cap_stream, &graph);
+    restore();
+    vloc_plan_s::GraphEntry ent;
+    for (size_t i = 0; i < plans.size(); ++i) {
+        ent.kernels.push_back({plans[i], plans[i]->launches - l0[i]});
+        plans[i]->launches = l0[i];
+    }
+    if (rc || e) {
+        if (graph) cudaGraphDestroy(graph);
+        return rc ? rc : cuda_fail(e, "cudaStreamEndCapture");
+    }
+    e = cudaGraphInstantiate(&ent.exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e) return cuda_fail(e, "cudaGraphInstantiate");
+    if (owner->graphs.size() >= 8) {  // least recently used out
+        auto it = std::min_element(owner->graphs.begin(), owner->graphs.end(),
+                                   [](const auto& a, const auto& b) { return a.last_use < b.last_use; });
+        cudaGraphExecDestroy(it->exec);
+        owner->graphs.erase(it);
+    }
+    ent.key = std::move(key);
+    ent.last_use = ++owner->use_clock;
+    owner->graphs.push_back(std::move(ent));
+    auto& g = owner->graphs.back();
+    if ((e = cudaGraphLaunch(g.exec, st))) return cuda_fail(e, "cudaGraphLaunch");
+    for (auto& k : g.kernels) k.first->launches += k.second;
+    return VLOC_OK;
+}
+
+extern "C" {
+
 int vloc_apply(vloc_plan p, const void* c, const void* V, int64_t nb, void* out, void* stream) {
     int rc = check_io(p, c, V, nb, out);
     if (rc || nb == 0) return rc;
+    if (p->flags & VLOC_GRAPH)
+        return graph_run(p, {p}, {(uintptr_t)c, (uintptr_t)V, (uintptr_t)nb, (uintptr_t)out}, (cudaStream_t)stream,
+                         [&](cudaStream_t cs) { return apply_impl(p, c, V, nb, out, cs); });
     return apply_impl(p, c, V, nb, out, (cudaStream_t)stream);
 }
 
@@ -518,7 +606,10 @@ int vloc_backward(vloc_plan p, const void* c, const void* gout, const void* V, i
             if ((rc = launch(p, KK_Y_INV, st, [&] { return launch_k2_ypass(dbl, p->fast, +1, t, ax, p->d_tw[1], cb, cylC, slabC, st); }))) return rc;
             if ((rc = launch(p, KK_SCATTER_Z, st, [&] { return launch_k1_scatter_zpass(dbl, p->fast, t, ax, p->d_tw[2], gg, cb, cylG, st); }))) return rc;
             if ((rc = launch(p, KK_Y_INV, st, [&] { return launch_k2_ypass(dbl, p->fast, +1, t, ax, p->d_tw[1], cb, cylG, slabG, st); }))) return rc;
-            if ((rc = launch(p, KK_GRAD_V, st, [&] { return launch_k3b_grad_v(dbl, t, ax, p->d_tw[0], slabC, slabG, cb, p->d_acc, st); }))) return rc;
+            int used = 1;
+            double* partial = p->d_acc + p->N;
+            if ((rc = launch(p, KK_GRAD_V, st, [&] { return launch_k3b_grad_v(dbl, p->fast, t, ax, p->d_tw[0], slabC, slabG, cb, (int)kGradBandsPerGroup, partial, &used, st); }))) return rc;
+            if ((rc = launch(p, KK_AUX, st, [&] { return launch_reduce_partials(partial, used, p->N, p->d_acc, st); }))) return rc;
         }
         if ((rc = launch(p, KK_AUX, st, [&] { return launch_finish_grad_v(dbl, p->d_acc, gV, p->N, st); }))) return rc;
     }
@@ -537,12 +628,25 @@ int vloc_apply_batched(int ninst, const vloc_plan* plans, const void* const* c, 
         int rc = check_io(plans[i], c[i], V[i], nb[i], out[i]);
         if (rc) return rc;
     }
+    auto enqueue = [&](cudaStream_t cs) {
+        for (int i = 0; i < ninst; ++i) {
+            if (nb[i] == 0) continue;
+            int rc = apply_impl(plans[i], c[i], V[i], nb[i], out[i], cs);
+            if (rc) return rc;
+        }
+        return (int)VLOC_OK;
+    };
+    bool all_graph = ninst > 0;
+    for (int i = 0; i < ninst; ++i) all_graph = all_graph && (plans[i]->flags & VLOC_GRAPH);
+    if (!all_graph) return enqueue((cudaStream_t)stream);
+    // the whole batch as one graph launch, cached on the first plan
+    std::vector<uintptr_t> key{(uintptr_t)ninst};
+    std::vector<vloc_plan> ps;
     for (int i = 0; i < ninst; ++i) {
-        if (nb[i] == 0) continue;
-        int rc = apply_impl(plans[i], c[i], V[i], nb[i], out[i], (cudaStream_t)stream);
-        if (rc) return rc;
+        key.insert(key.end(), {(uintptr_t)plans[i], (uintptr_t)c[i], (uintptr_t)V[i], (uintptr_t)nb[i], (uintptr_t)out[i]});
+        if (std::find(ps.begin(), ps.end(), plans[i]) == ps.end()) ps.push_back(plans[i]);
     }
-    return VLOC_OK;
+    return graph_run(plans[0], ps, std::move(key), (cudaStream_t)stream, enqueue);
 }
 
 int vloc_apply_host(vloc_plan p, const void* ch, const void* Vh, int64_t nb, void* oh, void* stream) {
@@ -554,10 +658,12 @@ int vloc_apply_host(vloc_plan p, const void* ch, const void* Vh, int64_t nb, voi
     std::lock_guard<std::mutex> lock(p->mu);
     const size_t re = p->dbl ? 8 : 4;
     const size_t bstride = (size_t)p->npw * p->elem;
-    const long long sb = p->chunk;
+    // staging chunks: at most 256 bands, so copies in, compute and copies
+    // out of neighbouring chunks overlap (H2D and D2H on separate streams)
+    const long long sb = std::min<long long>(p->chunk, 256);
     const size_t vbytes = (size_t)p->N * re;
-    // staging: V + 2 slots of (in, out) for `sb` bands
-    const size_t need = vbytes + 4 * (size_t)sb * bstride + 256 * 5;
+    auto align = [](size_t x) { return (x + 255) & ~(size_t)255; };
+    const size_t need = align(vbytes) + 4 * align((size_t)sb * bstride);
     cudaError_t e;
     if (p->stage_bytes < need) {
         cudaFree(p->d_stage);
@@ -567,10 +673,11 @@ int vloc_apply_host(vloc_plan p, const void* ch, const void* Vh, int64_t nb, voi
         p->stage_bytes = need;
         if (!p->copy_stream && (e = cudaStreamCreateWithFlags(&p->copy_stream, cudaStreamNonBlocking)))
             return cuda_fail(e, "copy stream");
+        if (!p->d2h_stream && (e = cudaStreamCreateWithFlags(&p->d2h_stream, cudaStreamNonBlocking)))
+            return cuda_fail(e, "copy stream");
         for (auto& ev : p->ev)
             if (!ev && (e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming))) return cuda_fail(e, "events");
     }
-    auto align = [](size_t x) { return (x + 255) & ~(size_t)255; };
     char* base = (char*)p->d_stage;
     char* dV = base;
     char* slot_in[2];
@@ -581,31 +688,30 @@ int vloc_apply_host(vloc_plan p, const void* ch, const void* Vh, int64_t nb, voi
         slot_out[s] = base + off; off += align((size_t)sb * bstride);
     }
     if ((e = cudaMemcpyAsync(dV, Vh, vbytes, cudaMemcpyHostToDevice, st))) return cuda_fail(e, "H2D V");
-    // ev[s]: slot s input on device; ev[2+s]: slot s result computed;
-    // ev[4+s]: slot s result copied back to the host.
+    // per slot s: ev[s] input copied in, ev[2+s] result computed, ev[4+s]
+    // result copied out.  A slot's input is overwritten only after the chunk
+    // two back has been computed, its output only after that chunk's result
+    // has been copied out.
     const int64_t nchunks = (nb + sb - 1) / sb;
     for (int64_t i = 0; i < nchunks; ++i) {
         const int s = (int)(i & 1);
         const int64_t b0 = i * sb;
         const long long cb = std::min<long long>(sb, nb - b0);
-        // copy stream: slot s input may be overwritten once chunk i-2 was
-        // consumed (its compute-done event was waited on before its copy-out,
-        // which precedes this copy on the same stream)
+        if (i >= 2 && (e = cudaStreamWaitEvent(p->copy_stream, p->ev[2 + s], 0))) return cuda_fail(e, "wait");
         if ((e = cudaMemcpyAsync(slot_in[s], (const char*)ch + b0 * bstride, cb * bstride, cudaMemcpyHostToDevice, p->copy_stream)))
             return cuda_fail(e, "H2D coeffs");
         if ((e = cudaEventRecord(p->ev[s], p->copy_stream))) return cuda_fail(e, "record");
         if ((e = cudaStreamWaitEvent(st, p->ev[s], 0))) return cuda_fail(e, "wait");
-        // compute stream: slot s output may be overwritten once chunk i-2's
-        // result has been copied back
         if (i >= 2 && (e = cudaStreamWaitEvent(st, p->ev[4 + s], 0))) return cuda_fail(e, "wait");
         int rc = apply_impl(p, slot_in[s], dV, cb, slot_out[s], st);
         if (rc) return rc;
         if ((e = cudaEventRecord(p->ev[2 + s], st))) return cuda_fail(e, "record");
-        if ((e = cudaStreamWaitEvent(p->copy_stream, p->ev[2 + s], 0))) return cuda_fail(e, "wait");
-        if ((e = cudaMemcpyAsync((char*)oh + b0 * bstride, slot_out[s], cb * bstride, cudaMemcpyDeviceToHost, p->copy_stream)))
+        if ((e = cudaStreamWaitEvent(p->d2h_stream, p->ev[2 + s], 0))) return cuda_fail(e, "wait");
+        if ((e = cudaMemcpyAsync((char*)oh + b0 * bstride, slot_out[s], cb * bstride, cudaMemcpyDeviceToHost, p->d2h_stream)))
             return cuda_fail(e, "D2H out");
-        if ((e = cudaEventRecord(p->ev[4 + s], p->copy_stream))) return cuda_fail(e, "record");
+        if ((e = cudaEventRecord(p->ev[4 + s], p->d2h_stream))) return cuda_fail(e, "record");
     }
+    if ((e = cudaStreamSynchronize(p->d2h_stream))) return cuda_fail(e, "sync copy");
     if ((e = cudaStreamSynchronize(p->copy_stream))) return cuda_fail(e, "sync copy");
     if ((e = cudaStreamSynchronize(st))) return cuda_fail(e, "sync");
     return VLOC_OK;
