@@ -90,6 +90,7 @@ typedef struct vloc_info {
     int64_t workspace_bytes;     /* device workspace owned by the plan            */
     int32_t radix[3][4];         /* per-axis radix schedule (0 = unused)          */
     int32_t nstages[3];
+    int32_t path;                /* bit 0: compile-time-length kernels in use     */
 } vloc_info;
 
 /*
@@ -117,6 +118,16 @@ typedef struct vloc_info {
  */
 int vloc_plan_create(vloc_plan* out, int n1, int n2, int n3, const int32_t* g_hkl, int64_t npw,
                      int flags, int64_t max_bands_per_chunk, void* stream);
+
+/*
+ * vloc_plan_set_schedule -- replace the radix schedule of one axis (0: n1,
+ * 1: n2, 2: n3) of a plan: nst stages (1..4) with radices from
+ * {2,3,4,5,6,8,9,10,12,15,16} whose product is that axis's length.  The
+ * plan then runs the runtime-radix kernels (the compile-time-length kernels
+ * have their schedule built in).  Used by the autotuner.  Not while the plan
+ * has work in flight.  Errors: VLOC_ERR_ARG (bad axis, radix or product).
+ */
+int vloc_plan_set_schedule(vloc_plan plan, int axis, int nst, const int32_t* radix);
 
 /* vloc_plan_destroy -- free the plan's device and host memory (synchronises
  * the device first).  NULL is accepted.  Returns VLOC_OK or VLOC_ERR_CUDA. */
@@ -156,9 +167,12 @@ int vloc_backward(vloc_plan plan, const void* coeffs, const void* grad_out, cons
 
 /*
  * vloc_apply_batched -- ninst independent applies (plans of different grids
- * and spheres) enqueued back to back on one stream; with VLOC_GRAPH plans the
- * whole batch is one graph launch.  Arrays have ninst entries each; plans
- * must share a precision.  Errors as vloc_apply, per instance.
+ * and spheres).  Without VLOC_GRAPH they are enqueued back to back on the
+ * stream.  When every plan has VLOC_GRAPH the whole batch is captured once
+ * (per pointer set) into one CUDA graph whose instances run as up to four
+ * parallel branches (instances sharing a plan share a branch), and each
+ * call is one graph launch.  Arrays have ninst entries each; plans must
+ * share a precision.  Errors as vloc_apply, per instance.
  */
 int vloc_apply_batched(int ninst, const vloc_plan* plans, const void* const* coeffs,
                        const void* const* V, const int64_t* nbands, void* const* out,

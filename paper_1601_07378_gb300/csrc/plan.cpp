@@ -40,7 +40,8 @@ int cuda_fail(cudaError_t e, const char* what) {
     } while (0)
 
 const int kRadices[] = {16, 15, 12, 10, 9, 8, 6, 5, 4, 3, 2};
-constexpr long long kGradBandsPerGroup = 16;  // bands per group of the dL/dV x-pass (FP32 sums)
+constexpr long long kGradBandsPerGroup = 16;
+constexpr long long kBatchBranches = 4;  // parallel branches of a batched graph  // bands per group of the dL/dV x-pass (FP32 sums)
 constexpr int kLinesPerTile = 32;
 
 bool smooth235(int n) {
@@ -138,6 +139,9 @@ struct vloc_plan_s {
     std::vector<GraphEntry> graphs;
     cudaStream_t cap_stream = nullptr;
     unsigned long long use_clock = 0;
+    std::vector<cudaStream_t> branch_streams;  // parallel branches of batched graphs
+    std::vector<cudaEvent_t> branch_events;
+    cudaEvent_t fork_event = nullptr;
     // launch accounting and optional per-launch event timing
     long long launches = 0;
     bool prof_on = false;
@@ -177,6 +181,9 @@ static void free_plan(vloc_plan p) {
     for (auto& g : p->graphs)
         if (g.exec) cudaGraphExecDestroy(g.exec);
     if (p->cap_stream) cudaStreamDestroy(p->cap_stream);
+    for (cudaStream_t b : p->branch_streams) cudaStreamDestroy(b);
+    for (cudaEvent_t b : p->branch_events) cudaEventDestroy(b);
+    if (p->fork_event) cudaEventDestroy(p->fork_event);
     for (cudaEvent_t e : p->ev)
         if (e) cudaEventDestroy(e);
     if (p->copy_stream) cudaStreamDestroy(p->copy_stream);
@@ -410,6 +417,25 @@ int vloc_plan_create(vloc_plan* out, int n1, int n2, int n3, const int32_t* g, i
     return VLOC_OK;
 }
 
+int vloc_plan_set_schedule(vloc_plan p, int axis, int nst, const int32_t* radix) {
+    if (!p || axis < 0 || axis > 2 || nst < 1 || nst > 4 || !radix) return VLOC_ERR_ARG;
+    long long prod = 1;
+    for (int i = 0; i < nst; ++i) {
+        bool ok = false;
+        for (int r : kRadices) ok = ok || r == radix[i];
+        if (!ok) return VLOC_ERR_ARG;
+        prod *= radix[i];
+    }
+    if (prod != p->ax.n[axis]) return VLOC_ERR_ARG;
+    p->ax.nst[axis] = nst;
+    for (int i = 0; i < 4; ++i) p->ax.radix[axis][i] = i < nst ? radix[i] : 0;
+    p->fast = 0;
+    for (auto& g : p->graphs)
+        if (g.exec) cudaGraphExecDestroy(g.exec);
+    p->graphs.clear();
+    return VLOC_OK;
+}
+
 int vloc_plan_destroy(vloc_plan p) {
     if (!p) return VLOC_OK;
     if (p->flags & VLOC_HOST_ONLY) { delete p; return VLOC_OK; }
@@ -639,6 +665,44 @@ int vloc_apply_batched(int ninst, const vloc_plan* plans, const void* const* c, 
     bool all_graph = ninst > 0;
     for (int i = 0; i < ninst; ++i) all_graph = all_graph && (plans[i]->flags & VLOC_GRAPH);
     if (!all_graph) return enqueue((cudaStream_t)stream);
+    // Captured as parallel branches: instance i runs on branch (i mod K) so
+    // independent instances (each with its own workspace) overlap and fill
+    // one another's kernel tails; instances sharing a plan share a branch.
+    vloc_plan owner = plans[0];
+    const int K = std::min(ninst, (int)kBatchBranches);
+    cudaError_t e;
+    while ((int)owner->branch_streams.size() < K) {
+        cudaStream_t s;
+        if ((e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking))) return cuda_fail(e, "branch stream");
+        owner->branch_streams.push_back(s);
+        cudaEvent_t ev;
+        if ((e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming))) return cuda_fail(e, "branch event");
+        owner->branch_events.push_back(ev);
+    }
+    if (!owner->fork_event && (e = cudaEventCreateWithFlags(&owner->fork_event, cudaEventDisableTiming)))
+        return cuda_fail(e, "fork event");
+    auto branched = [&](cudaStream_t cs) {
+        cudaError_t er;
+        if ((er = cudaEventRecord(owner->fork_event, cs))) return cuda_fail(er, "fork");
+        std::vector<int> branch_of(ninst);
+        for (int i = 0; i < ninst; ++i) {
+            branch_of[i] = i % K;
+            for (int j = 0; j < i; ++j)
+                if (plans[j] == plans[i]) { branch_of[i] = branch_of[j]; break; }
+        }
+        for (int b = 0; b < K; ++b)
+            if ((er = cudaStreamWaitEvent(owner->branch_streams[b], owner->fork_event, 0))) return cuda_fail(er, "fork wait");
+        for (int i = 0; i < ninst; ++i) {
+            if (nb[i] == 0) continue;
+            int rc = apply_impl(plans[i], c[i], V[i], nb[i], out[i], owner->branch_streams[branch_of[i]]);
+            if (rc) return rc;
+        }
+        for (int b = 0; b < K; ++b) {
+            if ((er = cudaEventRecord(owner->branch_events[b], owner->branch_streams[b]))) return cuda_fail(er, "join");
+            if ((er = cudaStreamWaitEvent(cs, owner->branch_events[b], 0))) return cuda_fail(er, "join wait");
+        }
+        return (int)VLOC_OK;
+    };
     // the whole batch as one graph launch, cached on the first plan
     std::vector<uintptr_t> key{(uintptr_t)ninst};
     std::vector<vloc_plan> ps;
@@ -646,7 +710,7 @@ int vloc_apply_batched(int ninst, const vloc_plan* plans, const void* const* c, 
         key.insert(key.end(), {(uintptr_t)plans[i], (uintptr_t)c[i], (uintptr_t)V[i], (uintptr_t)nb[i], (uintptr_t)out[i]});
         if (std::find(ps.begin(), ps.end(), plans[i]) == ps.end()) ps.push_back(plans[i]);
     }
-    return graph_run(plans[0], ps, std::move(key), (cudaStream_t)stream, enqueue);
+    return graph_run(plans[0], ps, std::move(key), (cudaStream_t)stream, branched);
 }
 
 int vloc_apply_host(vloc_plan p, const void* ch, const void* Vh, int64_t nb, void* oh, void* stream) {
@@ -767,6 +831,7 @@ int vloc_get_info(vloc_plan p, vloc_info* info) {
     info->npw = p->npw;
     info->nsticks = p->S; info->nplanes = p->NP; info->nparts = p->P;
     info->lines_per_tile = kLinesPerTile;
+    info->path = p->fast ? 1 : 0;
     info->chunk_bands = p->chunk;
     info->workspace_bytes = (int64_t)p->ws_bytes;
     for (int a = 0; a < 3; ++a) {

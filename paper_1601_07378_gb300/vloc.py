@@ -41,6 +41,7 @@ EXPORTS = [
     "vloc_apply_batched", "vloc_apply_host", "vloc_get_index_map", "vloc_get_partition",
     "vloc_get_info", "vloc_strerror", "vloc_version", "vloc_last_cuda_error",
     "vloc_profile", "vloc_get_profile", "vloc_get_launch_count", "vloc_apply_noalloc",
+    "vloc_plan_set_schedule",
 ]
 
 KERNEL_NAMES = ["k1_scatter_zpass", "k2_ypass_inv", "k3_xpass_v", "k2_ypass_fwd", "k4_zpass_gather",
@@ -58,7 +59,7 @@ class VlocInfo(ctypes.Structure):
         ("nsticks", ctypes.c_int32), ("nplanes", ctypes.c_int32), ("nparts", ctypes.c_int32),
         ("lines_per_tile", ctypes.c_int32), ("chunk_bands", ctypes.c_int64),
         ("workspace_bytes", ctypes.c_int64), ("radix", (ctypes.c_int32 * 4) * 3),
-        ("nstages", ctypes.c_int32 * 3),
+        ("nstages", ctypes.c_int32 * 3), ("path", ctypes.c_int32),
     ]
 
 
@@ -103,6 +104,7 @@ def load(path: str | None = None) -> ctypes.CDLL:
         lib.vloc_last_cuda_error.restype = ctypes.c_char_p
         lib.vloc_version.argtypes = []
         lib.vloc_profile.argtypes = [vp, c_int]
+        lib.vloc_plan_set_schedule.argtypes = [vp, c_int, c_int, ctypes.POINTER(i32)]
         lib.vloc_get_profile.argtypes = [vp, ctypes.POINTER(VlocKernelStat)]
         lib.vloc_get_launch_count.argtypes = [vp, ctypes.POINTER(i64)]
         for name in EXPORTS:
@@ -202,7 +204,14 @@ class VlocPlan:
             "lines_per_tile": inf.lines_per_tile, "chunk_bands": inf.chunk_bands,
             "workspace_bytes": inf.workspace_bytes,
             "radix": [[inf.radix[a][i] for i in range(inf.nstages[a])] for a in range(3)],
+            "compile_time_kernels": bool(inf.path & 1),
         }
+
+    def set_schedule(self, axis: int, radices):
+        """Replace one axis's radix schedule (switches the plan to the
+        runtime-radix kernels)."""
+        arr = (ctypes.c_int32 * len(radices))(*[int(r) for r in radices])
+        _check(self.lib.vloc_plan_set_schedule(self.handle, int(axis), len(radices), arr), "vloc_plan_set_schedule")
 
     def profile(self, enable: bool = True):
         _check(self.lib.vloc_profile(self.handle, int(enable)), "vloc_profile")
