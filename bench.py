@@ -347,6 +347,25 @@ def run_ours(args, rank, world, local_rank):
            "hbm_frac_of_B5": f64_value / world / (peak * 1e9 / (2 * B5))}
     del plan64, c128_d, o128_d, V64_d
 
+    # ---- Gamma-point real mode (Sec. 4.3): 1024 real bands on the half
+    # sphere (28889 PWs), two per complex transform, FP32
+    gamma = None
+    if not args.no_extra:
+        gh = synth.half_sphere(g)
+        pg = vloc.VlocPlan(GRID, gh, torch.complex64, gamma=True)
+        cg = torch.from_numpy(synth.coefficients(gh, NBANDS, seed=SEED + 5, dtype=np.complex64)).cuda()
+        og = torch.empty_like(cg)
+        kg = max(3, args.steps // 2)
+        msg = time_steps(lambda: pg.apply(cg, V_d, out=og), kg, 2, stream, dist_on)
+        pg.profile(True)
+        pg.apply(cg, V_d, out=og)
+        profg = pg.get_profile()
+        pg.profile(False)
+        gamma = {"value": world * NBANDS / (msg / kg / 1e3), "unit": "bands/s", "ms_per_step": msg / kg,
+                 "npw_half": len(gh), "what": "1024 real bands, 96^3, half sphere, two bands per complex transform",
+                 "kernel_share": {k: round(v[1] / sum(t for _, t in profg.values()), 4) for k, v in profg.items()}}
+        del pg, cg, og
+
     # ---- uneven multi-instance batch, one graph launch per step: 8 grids
     # 48^3 .. 144^3, R = n/4, 64 (i+1) bands each (FP32)
     batched = None
@@ -447,7 +466,7 @@ def run_ours(args, rank, world, local_rank):
             "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clocks,
             "fp64": f64, "adjoint": {"value": adj, "unit": "bands/s"},
             "grid_96x96x120": {"value": c2_value, "unit": "bands/s"},
-            "batched_uneven": batched, "autograd_512": autograd,
+            "batched_uneven": batched, "autograd_512": autograd, "gamma_real": gamma,
             "cufft_comparison": cufft,
         }
         print(json.dumps(line), flush=True)

@@ -71,6 +71,13 @@ extern "C" {
 #define VLOC_GENERIC_KERNELS    0x400  /* use the runtime-radix kernels for every   */
                                        /* axis (the compile-time-length kernels are */
                                        /* the default where one exists)             */
+#define VLOC_GAMMA              0x1000 /* Gamma-point real mode (Sec. 4.3): g_hkl is */
+                                       /* half of a G -> -G symmetric list (never    */
+                                       /* both G and -G); coefficients c(-G) =      */
+                                       /* conj c(G) are implied, c(0) is taken real; */
+                                       /* bands are real in r-space and travel two  */
+                                       /* per complex transform.  Apply / adjoint / */
+                                       /* batched only.                             */
 #define VLOC_HOST_ONLY          0x200  /* build host tables only (no device memory, */
                                        /* no CUDA call); for introspection: the     */
                                        /* device calls then return VLOC_ERR_STATE   */
@@ -90,7 +97,8 @@ typedef struct vloc_info {
     int64_t workspace_bytes;     /* device workspace owned by the plan            */
     int32_t radix[3][4];         /* per-axis radix schedule (0 = unused)          */
     int32_t nstages[3];
-    int32_t path;                /* bit 0: compile-time-length kernels in use     */
+    int32_t path;                /* bit 0: compile-time-length kernels enabled;   */
+                                 /* bit 2: Gamma-point real mode                  */
 } vloc_info;
 
 /*
@@ -106,8 +114,10 @@ typedef struct vloc_info {
  *                may free it after the call.
  *   npw        : number of plane waves, >= 1.
  *   flags      : exactly one of VLOC_F32 / VLOC_F64, optionally one
- *                partition flag, VLOC_GRAPH, VLOC_HOST_ONLY and
- *                VLOC_GENERIC_KERNELS.
+ *                partition flag, VLOC_GRAPH, VLOC_HOST_ONLY,
+ *                VLOC_GENERIC_KERNELS and VLOC_GAMMA.  With VLOC_GAMMA every
+ *                -G must be a valid index too (else VLOC_ERR_GLIST), and
+ *                npw counts the half list (the caller's arrays).
  *   max_bands_per_chunk : bands per workspace chunk (<= 0: automatic, a
  *                2 GiB workspace capped at 1/8 of the free device memory;
  *                large chunks keep every kernel many waves deep).
@@ -237,7 +247,7 @@ int vloc_apply_noalloc(vloc_plan plan, const void* coeffs, const void* V, int64_
  * every kernel of a plan's calls, for the roofline and profile reports.
  * Kernel slots: 0 scatter + inverse z-pass, 1 inverse y-pass, 2 x-pass with
  * V(r), 3 forward y-pass, 4 forward z-pass + gather, 5 dL/dV x-pass,
- * 6 auxiliary (zero / convert). */
+ * 6 auxiliary (zero / convert), 7 Gamma-point pack / unpack. */
 #define VLOC_NKERNELS 8
 typedef struct vloc_kernel_stat {
     int64_t launches;

@@ -18,6 +18,11 @@ it follows:
 * ``closed_form_apply``: for a potential with few Fourier modes the action is
   the convolution out(G) = sum_q v_q c(G - q) (no FFT at all), valid while
   every n_a > 2R + K (no wrap-around, Fig. 1).
+* ``gamma_complete`` / ``gamma_apply``: the Gamma-point real mode (Sec. 4.3,
+  last paragraph): a band stored on half of the sphere is completed with
+  c(-G) = conj c(G) (c(0) real), acted on by ``apply`` and read back on the
+  half; ``bf_real_apply`` writes the same action with real plane-wave sums
+  (cosines and sines, brute force, tiny grids).
 * ``sticks`` / ``greedy_partition`` (Sec. 3.2, Fig. 2), ``basic_partition``
   (Sec. 4.1, Fig. 3-4) and ``improved_partition`` (Sec. 4.2).
 
@@ -257,6 +262,49 @@ def closed_form_apply(g, c, modes) -> np.ndarray:
 # --------------------------------------------------------------------------
 # sticks and the three partitions (Sec. 3.2, 4.1, 4.2)
 # --------------------------------------------------------------------------
+def gamma_complete(g_half, c_half):
+    """Sec. 4.3: Psi(G) = conj Psi(-G).  Full list = the half list followed by
+    -G for each G != 0 of it; coefficients completed the same way, with the
+    G = 0 coefficient taken real.  Returns (g_full, c_full)."""
+    g_half = np.asarray(g_half, dtype=np.int64).reshape(-1, 3)
+    c_half = np.asarray(c_half, dtype=np.complex128).reshape(-1, len(g_half))
+    nz = np.any(g_half != 0, axis=1)
+    g_full = np.concatenate([g_half, -g_half[nz]])
+    c0 = c_half.copy()
+    c0[:, ~nz] = c0[:, ~nz].real
+    c_full = np.concatenate([c0, np.conj(c0[:, nz])], axis=1)
+    return g_full.astype(np.int32), c_full
+
+
+def gamma_apply(n, g_half, c_half, V, nthreads: int = 0) -> np.ndarray:
+    """A applied to real bands given on half of the sphere (Sec. 4.3):
+    complete, apply (Sec. 2), keep the half list's entries."""
+    g_full, c_full = gamma_complete(g_half, c_half)
+    return apply(n, g_full, c_full, V, nthreads)[:, :len(g_half)]
+
+
+def bf_real_apply(n, g_half, c_half, V) -> np.ndarray:
+    """Real-arithmetic brute force of the Gamma-point action (tiny grids):
+    psi(r) = Re c(0) + 2 sum_{G != 0 in half} [Re c(G) cos(th) - Im c(G) sin(th)],
+    th = 2 pi G.r / n; then out(G) = (1/N) sum_r V(r) psi(r) (cos(th) - i sin(th))."""
+    n1, n2, n3 = n
+    N = n1 * n2 * n3
+    g_half = np.asarray(g_half, dtype=np.float64).reshape(-1, 3)
+    c_half = np.asarray(c_half, dtype=np.complex128).reshape(-1, len(g_half))
+    r = np.stack(np.meshgrid(np.arange(n1) / n1, np.arange(n2) / n2, np.arange(n3) / n3,
+                             indexing="ij"), axis=-1).reshape(-1, 3)
+    th = 2.0 * np.pi * (r @ g_half.T)                     # [N, nh]
+    cos, sin = np.cos(th), np.sin(th)
+    w = np.where(np.any(g_half != 0, axis=1), 2.0, 1.0)   # G = 0 counted once
+    Vr = np.asarray(V, dtype=np.float64).reshape(-1)
+    out = np.empty_like(c_half)
+    for b in range(len(c_half)):
+        psi = cos @ (w * c_half[b].real) - sin @ (np.where(w == 2.0, 2.0, 0.0) * c_half[b].imag)
+        f = Vr * psi
+        out[b] = (f @ cos - 1j * (f @ sin)) / N
+    return out
+
+
 def sticks(n, g):
     """Occupied z-sticks: sorted linear ids (h mod n1)*n2 + (k mod n2) and #PW each."""
     g = _glist(g)

@@ -34,7 +34,7 @@ struct LaunchAxes {
 };
 
 // Kernel kinds (profiling slots).
-enum KernelKind { KK_SCATTER_Z = 0, KK_Y_INV = 1, KK_X_V = 2, KK_Y_FWD = 3, KK_Z_GATHER = 4, KK_GRAD_V = 5, KK_AUX = 6 };
+enum KernelKind { KK_SCATTER_Z = 0, KK_Y_INV = 1, KK_X_V = 2, KK_Y_FWD = 3, KK_Z_GATHER = 4, KK_GRAD_V = 5, KK_AUX = 6, KK_GAMMA = 7 };
 
 // Typed launchers (defined in kernels_impl.cuh, instantiated per precision
 // in kernels_f32.cu / kernels_f64.cu).  Every pointer is a device pointer;
@@ -90,6 +90,13 @@ int launch_k3b_grad_v(int dbl, int fast, const DevTables& t, const LaunchAxes& a
                       const void* slab_g, long long nb, int bpg, double* partial, int* used, cudaStream_t st);
 int launch_reduce_partials(const double* partial, int ngroups, long long N, double* acc, cudaStream_t st);
 int launch_finish_grad_v(int dbl, const double* acc, void* gradV, long long N, cudaStream_t st);
+// Gamma-point real mode: pack bands (2p, 2p+1) of c [nb][nh] into complex
+// band p of C [np][nfull] over the full list (G, then -G at neg[q]), and
+// separate the results U [np][nfull] back into out [nb][nh].
+int launch_gamma_pack(int dbl, const void* c, long long nb, long long nh, const int* neg, long long nfull, void* C,
+                      long long np, cudaStream_t st);
+int launch_gamma_unpack(int dbl, const void* U, long long np, long long nfull, const int* neg, long long nh,
+                        void* out, long long nb, cudaStream_t st);
 int launch_zero_f64(double* p, long long n, cudaStream_t st);
 size_t smem_bytes_for(int dbl, int n);
 size_t grad_smem_bytes(int dbl, int n);

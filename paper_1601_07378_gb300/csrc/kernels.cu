@@ -16,6 +16,59 @@ __global__ void k_zero_f64(double* p, long long n) {
     if (i < n) p[i] = 0.0;
 }
 
+// ---- Gamma-point real mode: two real bands per complex band
+template <typename V>
+__global__ void k_gamma_pack(const V* __restrict__ c, long long nb, long long nh, const int* __restrict__ neg,
+                             long long nfull, V* __restrict__ C) {
+    const long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    const long long p = blockIdx.y;
+    if (q >= nh) return;
+    const V a = c[(2 * p) * nh + q];
+    V b;
+    b.x = 0; b.y = 0;
+    if (2 * p + 1 < nb) b = c[(2 * p + 1) * nh + q];
+    V* row = C + p * nfull;
+    const int n = neg[q];
+    V u, w;
+    if (n == q) {  // G = 0 is its own partner: the real parts
+        u.x = a.x; u.y = b.x;
+        row[q] = u;
+        return;
+    }
+    u.x = a.x - b.y; u.y = a.y + b.x;   // a + i b at G
+    w.x = a.x + b.y; w.y = b.x - a.y;   // conj(a) + i conj(b) at -G
+    row[q] = u;
+    row[n] = w;
+}
+template <typename V>
+__global__ void k_gamma_unpack(const V* __restrict__ U, long long nfull, const int* __restrict__ neg, long long nh,
+                               V* __restrict__ out, long long nb) {
+    const long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    const long long p = blockIdx.y;
+    if (q >= nh) return;
+    const V* row = U + p * nfull;
+    const V x = row[q], y = row[neg[q]];  // U(G) and U(-G)
+    V a, b;
+    a.x = (x.x + y.x) * 0.5f; a.y = (x.y - y.y) * 0.5f;   // (U(G) + conj U(-G)) / 2
+    b.x = (x.y + y.y) * 0.5f; b.y = (y.x - x.x) * 0.5f;   // (U(G) - conj U(-G)) / 2i
+    out[(2 * p) * nh + q] = a;
+    if (2 * p + 1 < nb) out[(2 * p + 1) * nh + q] = b;
+}
+int launch_gamma_pack(int dbl, const void* c, long long nb, long long nh, const int* neg, long long nfull, void* C,
+                      long long np, cudaStream_t st) {
+    const dim3 grid((unsigned)((nh + 255) / 256), (unsigned)np);
+    if (dbl) k_gamma_pack<double2><<<grid, 256, 0, st>>>((const double2*)c, nb, nh, neg, nfull, (double2*)C);
+    else k_gamma_pack<float2><<<grid, 256, 0, st>>>((const float2*)c, nb, nh, neg, nfull, (float2*)C);
+    return (int)cudaGetLastError();
+}
+int launch_gamma_unpack(int dbl, const void* U, long long np, long long nfull, const int* neg, long long nh,
+                        void* out, long long nb, cudaStream_t st) {
+    const dim3 grid((unsigned)((nh + 255) / 256), (unsigned)np);
+    if (dbl) k_gamma_unpack<double2><<<grid, 256, 0, st>>>((const double2*)U, nfull, neg, nh, (double2*)out, nb);
+    else k_gamma_unpack<float2><<<grid, 256, 0, st>>>((const float2*)U, nfull, neg, nh, (float2*)out, nb);
+    return (int)cudaGetLastError();
+}
+
 int launch_zero_f64(double* p, long long n, cudaStream_t st) {
     k_zero_f64<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(p, n);
     return (int)cudaGetLastError();

@@ -103,6 +103,10 @@ struct vloc_plan_s {
     long long npw = 0, N = 0;
     int S = 0, NP = 0, P = 0, T = 0;
     int fast = 1;  // compile-time-length kernels where available
+    bool gamma = false;       // Gamma-point real mode (half-sphere coefficients)
+    long long npw_user = 0;   // plane waves per band in the caller's arrays
+    int* d_gamma_neg = nullptr;  // full-list index of -G for each caller G
+    void* d_gamma_buf = nullptr; // packed pairs and their results, [2][chunk][npw]
     int ngroups = 1;  // band groups of the dL/dV x-pass
     long long chunk = 1, ws_bands = 2;
     size_t elem = 8;
@@ -176,6 +180,8 @@ static void free_plan(vloc_plan p) {
     cudaFree(p->d_cyl);
     cudaFree(p->d_slab);
     cudaFree(p->d_acc);
+    cudaFree(p->d_gamma_neg);
+    cudaFree(p->d_gamma_buf);
     cudaFree(p->d_stage);
     for (cudaEvent_t e : p->prof_pool) cudaEventDestroy(e);
     for (auto& g : p->graphs)
@@ -201,11 +207,31 @@ int vloc_plan_create(vloc_plan* out, int n1, int n2, int n3, const int32_t* g, i
     const int part_flag = flags & 0x0F0;
     if (part_flag != VLOC_PARTITION_GREEDY && part_flag != VLOC_PARTITION_BASIC && part_flag != VLOC_PARTITION_IMPROVED)
         return VLOC_ERR_ARG;
-    if (flags & ~(0x003 | 0x0F0 | VLOC_GRAPH | VLOC_HOST_ONLY | VLOC_GENERIC_KERNELS)) return VLOC_ERR_ARG;
+    if (flags & ~(0x003 | 0x0F0 | VLOC_GRAPH | VLOC_HOST_ONLY | VLOC_GENERIC_KERNELS | VLOC_GAMMA)) return VLOC_ERR_ARG;
     const bool host_only = (flags & VLOC_HOST_ONLY) != 0;
     const int ns[3] = {n1, n2, n3};
     for (int a = 0; a < 3; ++a)
         if (ns[a] < 2 || ns[a] > 256 || !smooth235(ns[a])) return VLOC_ERR_SIZE;
+    // Gamma-point real mode (Sec. 4.3, last paragraph): the caller gives half
+    // of a sphere symmetric under G -> -G; the plan runs on the full list
+    // (the half, then -G for every G != 0 in the half's order).
+    const int64_t npw_user = npw;
+    std::vector<int32_t> gfull;
+    std::vector<int32_t> gamma_neg;
+    if (flags & VLOC_GAMMA) {
+        gfull.assign(g, g + 3 * npw);
+        gamma_neg.resize(npw);
+        int64_t next = npw;
+        for (int64_t q = 0; q < npw; ++q) {
+            const int h = g[3 * q], k = g[3 * q + 1], l = g[3 * q + 2];
+            if (h == 0 && k == 0 && l == 0) { gamma_neg[q] = (int32_t)q; continue; }
+            if (!valid_miller(-h, n1) || !valid_miller(-k, n2) || !valid_miller(-l, n3)) return VLOC_ERR_GLIST;
+            gfull.insert(gfull.end(), {-h, -k, -l});
+            gamma_neg[q] = (int32_t)next++;
+        }
+        g = gfull.data();
+        npw = next;  // duplicates (G and -G both in the half) are caught below
+    }
     const long long N = (long long)n1 * n2 * n3;
     if (npw > N) return VLOC_ERR_GLIST;
     const int dbl = prec == VLOC_F64;
@@ -215,6 +241,8 @@ int vloc_plan_create(vloc_plan* out, int n1, int n2, int n3, const int32_t* g, i
     vloc_plan p = new (std::nothrow) vloc_plan_s();
     if (!p) return VLOC_ERR_ALLOC;
     p->n1 = n1; p->n2 = n2; p->n3 = n3; p->dbl = dbl; p->flags = flags; p->npw = npw; p->N = N;
+    p->npw_user = npw_user;
+    p->gamma = (flags & VLOC_GAMMA) != 0;
     p->elem = elem;
     p->fast = (flags & VLOC_GENERIC_KERNELS) ? 0 : 1;
     for (int a = 0; a < 3; ++a) {
@@ -410,6 +438,14 @@ int vloc_plan_create(vloc_plan* out, int n1, int n2, int n3, const int32_t* g, i
     p->ws_bytes = per_band * (size_t)p->ws_bands + (size_t)N * sizeof(double) * (1 + p->ngroups);
     if ((e = cudaMalloc(&p->d_cyl, (size_t)S * n3 * elem * p->ws_bands))) { free_plan(p); return cuda_fail(e, "cudaMalloc(cylinder)"); }
     if ((e = cudaMalloc(&p->d_slab, (size_t)NP * n2 * n3 * elem * p->ws_bands))) { free_plan(p); return cuda_fail(e, "cudaMalloc(slab)"); }
+    if (p->gamma) {
+        if ((e = cudaMalloc(&p->d_gamma_neg, sizeof(int) * (size_t)npw_user))) { free_plan(p); return cuda_fail(e, "cudaMalloc(gamma map)"); }
+        if ((e = cudaMemcpyAsync(p->d_gamma_neg, gamma_neg.data(), sizeof(int) * (size_t)npw_user, cudaMemcpyHostToDevice, st))) {
+            free_plan(p); return cuda_fail(e, "upload gamma map");
+        }
+        if ((e = cudaMalloc(&p->d_gamma_buf, 2 * (size_t)p->chunk * npw * elem))) { free_plan(p); return cuda_fail(e, "cudaMalloc(gamma buffers)"); }
+        p->ws_bytes += 2 * (size_t)p->chunk * npw * elem;
+    }
     // dL/dV accumulator [N] followed by the band groups' partial sums [ngroups][N]
     if ((e = cudaMalloc(&p->d_acc, (size_t)N * sizeof(double) * (1 + p->ngroups)))) { free_plan(p); return cuda_fail(e, "cudaMalloc(acc)"); }
     if ((e = cudaStreamSynchronize(st))) { free_plan(p); return cuda_fail(e, "plan create sync"); }
@@ -457,7 +493,7 @@ static int check_io(vloc_plan p, const void* c, const void* V, int64_t nb, const
     if (!c || !V || !out) return VLOC_ERR_ARG;
     const size_t re = p->dbl ? 8 : 4;
     if (!aligned(c, p->elem) || !aligned(out, p->elem) || !aligned(V, re)) return VLOC_ERR_ARG;
-    const size_t bytes = (size_t)nb * p->npw * p->elem;
+    const size_t bytes = (size_t)nb * p->npw_user * p->elem;
     if (c != out && overlap(c, bytes, out, bytes)) return VLOC_ERR_ARG;
     if (overlap(V, (size_t)p->N * re, out, bytes)) return VLOC_ERR_ARG;
     return VLOC_OK;
@@ -512,6 +548,38 @@ static int apply_impl(vloc_plan p, const void* c, const void* V, int64_t nb, voi
 }
 
 }  // extern "C"
+
+// Gamma-point real mode: bands 2p and 2p+1 (real in r-space) travel as one
+// complex band a + i b through the chain; each result pair is separated with
+// U(G) and conj U(-G).
+static int gamma_apply(vloc_plan p, const void* c, const void* V, int64_t nb, void* out, cudaStream_t st) {
+    const long long npairs = (nb + 1) / 2;
+    const size_t full = (size_t)p->npw * p->elem;
+    char* C = (char*)p->d_gamma_buf;
+    char* U = C + (size_t)p->chunk * full;
+    for (long long p0 = 0; p0 < npairs; p0 += p->chunk) {
+        const long long cp = std::min<long long>(p->chunk, npairs - p0);
+        const long long b0 = 2 * p0, bn = std::min<long long>(nb - b0, 2 * cp);
+        const size_t ustride = (size_t)p->npw_user * p->elem;
+        int rc;
+        if ((rc = launch(p, KK_GAMMA, st, [&] {
+                 return launch_gamma_pack(p->dbl, (const char*)c + b0 * ustride, bn, p->npw_user, p->d_gamma_neg,
+                                          p->npw, C, cp, st);
+             })))
+            return rc;
+        if ((rc = apply_impl(p, C, V, cp, U, st))) return rc;
+        if ((rc = launch(p, KK_GAMMA, st, [&] {
+                 return launch_gamma_unpack(p->dbl, U, cp, p->npw, p->d_gamma_neg, p->npw_user, (char*)out + b0 * ustride,
+                                            bn, st);
+             })))
+            return rc;
+    }
+    return VLOC_OK;
+}
+
+static int apply_any(vloc_plan p, const void* c, const void* V, int64_t nb, void* out, cudaStream_t st) {
+    return p->gamma ? gamma_apply(p, c, V, nb, out, st) : apply_impl(p, c, V, nb, out, st);
+}
 
 // Replay (or capture, then replay) the work `enqueue` puts on a stream as one
 // CUDA graph, cached in `owner` under `key`; `plans` are the plans whose
@@ -582,8 +650,8 @@ int vloc_apply(vloc_plan p, const void* c, const void* V, int64_t nb, void* out,
     if (rc || nb == 0) return rc;
     if (p->flags & VLOC_GRAPH)
         return graph_run(p, {p}, {(uintptr_t)c, (uintptr_t)V, (uintptr_t)nb, (uintptr_t)out}, (cudaStream_t)stream,
-                         [&](cudaStream_t cs) { return apply_impl(p, c, V, nb, out, cs); });
-    return apply_impl(p, c, V, nb, out, (cudaStream_t)stream);
+                         [&](cudaStream_t cs) { return apply_any(p, c, V, nb, out, cs); });
+    return apply_any(p, c, V, nb, out, (cudaStream_t)stream);
 }
 
 int vloc_apply_adjoint(vloc_plan p, const void* c, const void* V, int64_t nb, void* out, void* stream) {
@@ -594,7 +662,7 @@ int vloc_apply_adjoint(vloc_plan p, const void* c, const void* V, int64_t nb, vo
 int vloc_backward(vloc_plan p, const void* c, const void* gout, const void* V, int64_t nb, void* gc, void* gV,
                   void* stream) {
     if (!p || nb < 0) return VLOC_ERR_ARG;
-    if (p->flags & VLOC_HOST_ONLY) return VLOC_ERR_STATE;
+    if ((p->flags & VLOC_HOST_ONLY) || p->gamma) return VLOC_ERR_STATE;
     if (!gc && !gV) return VLOC_OK;
     cudaStream_t st = (cudaStream_t)stream;
     const size_t re = p->dbl ? 8 : 4;
@@ -657,7 +725,7 @@ int vloc_apply_batched(int ninst, const vloc_plan* plans, const void* const* c, 
     auto enqueue = [&](cudaStream_t cs) {
         for (int i = 0; i < ninst; ++i) {
             if (nb[i] == 0) continue;
-            int rc = apply_impl(plans[i], c[i], V[i], nb[i], out[i], cs);
+            int rc = apply_any(plans[i], c[i], V[i], nb[i], out[i], cs);
             if (rc) return rc;
         }
         return (int)VLOC_OK;
@@ -694,7 +762,7 @@ int vloc_apply_batched(int ninst, const vloc_plan* plans, const void* const* c, 
             if ((er = cudaStreamWaitEvent(owner->branch_streams[b], owner->fork_event, 0))) return cuda_fail(er, "fork wait");
         for (int i = 0; i < ninst; ++i) {
             if (nb[i] == 0) continue;
-            int rc = apply_impl(plans[i], c[i], V[i], nb[i], out[i], owner->branch_streams[branch_of[i]]);
+            int rc = apply_any(plans[i], c[i], V[i], nb[i], out[i], owner->branch_streams[branch_of[i]]);
             if (rc) return rc;
         }
         for (int b = 0; b < K; ++b) {
@@ -715,7 +783,7 @@ int vloc_apply_batched(int ninst, const vloc_plan* plans, const void* const* c, 
 
 int vloc_apply_host(vloc_plan p, const void* ch, const void* Vh, int64_t nb, void* oh, void* stream) {
     if (!p || nb < 0) return VLOC_ERR_ARG;
-    if (p->flags & VLOC_HOST_ONLY) return VLOC_ERR_STATE;
+    if ((p->flags & VLOC_HOST_ONLY) || p->gamma) return VLOC_ERR_STATE;
     if (nb == 0) return VLOC_OK;
     if (!ch || !Vh || !oh) return VLOC_ERR_ARG;
     cudaStream_t st = (cudaStream_t)stream;
@@ -812,7 +880,7 @@ int vloc_get_launch_count(vloc_plan p, int64_t* count) {
 
 int vloc_get_index_map(vloc_plan p, int64_t* gi) {
     if (!p || !gi) return VLOC_ERR_ARG;
-    std::memcpy(gi, p->grid_index.data(), p->grid_index.size() * sizeof(int64_t));
+    std::memcpy(gi, p->grid_index.data(), (size_t)p->npw_user * sizeof(int64_t));
     return VLOC_OK;
 }
 
@@ -828,10 +896,10 @@ int vloc_get_info(vloc_plan p, vloc_info* info) {
     std::memset(info, 0, sizeof(*info));
     info->n1 = p->n1; info->n2 = p->n2; info->n3 = p->n3;
     info->precision = p->dbl ? VLOC_F64 : VLOC_F32;
-    info->npw = p->npw;
+    info->npw = p->npw_user;
     info->nsticks = p->S; info->nplanes = p->NP; info->nparts = p->P;
     info->lines_per_tile = kLinesPerTile;
-    info->path = p->fast ? 1 : 0;
+    info->path = (p->fast ? 1 : 0) | (p->gamma ? 4 : 0);
     info->chunk_bands = p->chunk;
     info->workspace_bytes = (int64_t)p->ws_bytes;
     for (int a = 0; a < 3; ++a) {

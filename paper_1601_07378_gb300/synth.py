@@ -25,6 +25,7 @@ import numpy as np
 
 __all__ = [
     "sphere_glist",
+    "half_sphere",
     "canonical_order",
     "coefficients",
     "potential_modes",
@@ -72,6 +73,16 @@ def sphere_glist(n1: int, n2: int, n3: int, R: float, *, strict: bool = False,
     elif order != "canonical":
         raise ValueError(order)
     return np.ascontiguousarray(g)
+
+
+def half_sphere(g: np.ndarray) -> np.ndarray:
+    """One of each pair {G, -G} of a G -> -G symmetric list, plus G = 0, in
+    the list's order: h > 0, or h = 0 and k > 0, or h = k = 0 and l >= 0.
+    The input list of the Gamma-point real mode (Sec. 4.3)."""
+    g = np.asarray(g)
+    h, k, l = g[:, 0], g[:, 1], g[:, 2]
+    keep = (h > 0) | ((h == 0) & (k > 0)) | ((h == 0) & (k == 0) & (l >= 0))
+    return np.ascontiguousarray(g[keep])
 
 
 def coefficients(g: np.ndarray, nbands: int, seed: int, dtype=np.complex128) -> np.ndarray:

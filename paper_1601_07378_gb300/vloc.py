@@ -34,6 +34,7 @@ VLOC_PARTITION_IMPROVED = 0x020
 VLOC_GRAPH = 0x100
 VLOC_HOST_ONLY = 0x200
 VLOC_GENERIC_KERNELS = 0x400
+VLOC_GAMMA = 0x1000
 
 # every exported symbol declared in include/vloc.h
 EXPORTS = [
@@ -45,7 +46,7 @@ EXPORTS = [
 ]
 
 KERNEL_NAMES = ["k1_scatter_zpass", "k2_ypass_inv", "k3_xpass_v", "k2_ypass_fwd", "k4_zpass_gather",
-                "k3b_grad_v", "aux", "unused"]
+                "k3b_grad_v", "aux", "gamma_pack_unpack"]
 
 
 class VlocKernelStat(ctypes.Structure):
@@ -147,10 +148,15 @@ class VlocPlan:
 
     ``glist`` is an int array [npw, 3] of Miller indices; ``dtype`` is
     ``torch.complex64`` (FP32 path) or ``torch.complex128`` (FP64 path).
+    ``gamma=True`` selects the Gamma-point real mode (Sec. 4.3): ``glist`` is
+    half of a G -> -G symmetric sphere, the bands are real in r-space
+    (c(-G) = conj c(G) implied, c(0) taken real) and two of them share one
+    complex transform.
     """
 
     def __init__(self, grid, glist, dtype=None, *, partition: str = "greedy", chunk: int = 0,
-                 graph: bool = False, host_only: bool = False, generic: bool = False, stream=None):
+                 graph: bool = False, host_only: bool = False, generic: bool = False, gamma: bool = False,
+                 stream=None):
         import torch
         dtype = dtype or torch.complex64
         if dtype not in (torch.complex64, torch.complex128):
@@ -170,6 +176,9 @@ class VlocPlan:
             flags |= VLOC_HOST_ONLY
         if generic:
             flags |= VLOC_GENERIC_KERNELS
+        self.gamma = bool(gamma)
+        if gamma:
+            flags |= VLOC_GAMMA
         h = ctypes.c_void_p()
         sp = ctypes.c_void_p(None) if host_only else _stream_ptr(stream)
         _check(self.lib.vloc_plan_create(ctypes.byref(h), *self.grid,
@@ -205,6 +214,7 @@ class VlocPlan:
             "workspace_bytes": inf.workspace_bytes,
             "radix": [[inf.radix[a][i] for i in range(inf.nstages[a])] for a in range(3)],
             "compile_time_kernels": bool(inf.path & 1),
+            "gamma": bool(inf.path & 4),
         }
 
     def set_schedule(self, axis: int, radices):

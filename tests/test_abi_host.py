@@ -112,3 +112,25 @@ def test_radix_schedules(lib):
         plan = vloc.VlocPlan((n, 8, 8), [[0, 0, 0]], host_only=True)
         assert plan.info()["radix"][0] == rad
         assert int(np.prod(rad)) == n
+
+
+def test_gamma_host_plan_index_map_and_rejects():
+    # Gamma-point real mode (Sec. 4.3): the plan reports the caller's half
+    # list; a list holding both G and -G, or whose -G leaves the grid's
+    # index range, is rejected
+    import torch
+    n = (16, 18, 20)
+    g = synth.sphere_glist(*n, 4.5, order="shuffled", seed=3)
+    gh = synth.half_sphere(g)
+    p = vloc.VlocPlan(n, gh, torch.complex64, host_only=True, gamma=True)
+    inf = p.info()
+    assert inf["gamma"] and inf["npw"] == len(gh)
+    assert np.array_equal(p.index_map(), O.index_map(n, gh))
+    full = vloc.VlocPlan(n, g, torch.complex64, host_only=True)
+    assert p.info()["nsticks"] == full.info()["nsticks"]
+    with pytest.raises(vloc.VlocError) as e:
+        vloc.VlocPlan(n, g, torch.complex64, host_only=True, gamma=True)
+    assert e.value.code == -3
+    with pytest.raises(vloc.VlocError) as e:
+        vloc.VlocPlan(n, np.array([[-8, 0, 0]], dtype=np.int32), torch.complex64, host_only=True, gamma=True)
+    assert e.value.code == -3

@@ -107,3 +107,46 @@ def test_unmutated_oracle_passes(tmp_path):
     subprocess.check_call(["gcc", "-O2", "-std=c11", "-D_GNU_SOURCE", "-fopenmp", "-fPIC", "-shared",
                            "-o", str(so), str(path), "-lm"])
     assert not _pins_fail(ctypes.CDLL(str(so)))
+
+
+# ---- planted mistakes in the Gamma-point completion (Python side of the oracle)
+def _complete_no_conj(g_half, c_half):
+    g_half = np.asarray(g_half, dtype=np.int64).reshape(-1, 3)
+    c_half = np.asarray(c_half, dtype=np.complex128).reshape(-1, len(g_half))
+    nz = np.any(g_half != 0, axis=1)
+    return np.concatenate([g_half, -g_half[nz]]).astype(np.int32), np.concatenate([c_half, c_half[:, nz]], axis=1)
+
+
+def _complete_g0_complex(g_half, c_half):
+    g_half = np.asarray(g_half, dtype=np.int64).reshape(-1, 3)
+    c_half = np.asarray(c_half, dtype=np.complex128).reshape(-1, len(g_half))
+    nz = np.any(g_half != 0, axis=1)
+    return (np.concatenate([g_half, -g_half[nz]]).astype(np.int32),
+            np.concatenate([c_half, np.conj(c_half[:, nz])], axis=1))
+
+
+def _complete_same_G(g_half, c_half):
+    g_half = np.asarray(g_half, dtype=np.int64).reshape(-1, 3)
+    c_half = np.asarray(c_half, dtype=np.complex128).reshape(-1, len(g_half))
+    nz = np.any(g_half != 0, axis=1)
+    mirrored = g_half[nz] * np.array([-1, -1, 1])          # l not negated
+    return (np.concatenate([g_half, mirrored]).astype(np.int32),
+            np.concatenate([c_half.real * (~nz) + c_half * nz, np.conj(c_half[:, nz])], axis=1))
+
+
+@pytest.mark.parametrize("bad", [_complete_no_conj, _complete_g0_complex, _complete_same_G])
+def test_planted_gamma_mistake_is_caught(monkeypatch, bad):
+    n = (4, 6, 5)
+    g = synth.sphere_glist(*n, 2.2, order="shuffled", seed=1)
+    gh = synth.half_sphere(g)
+    c = synth.coefficients(gh, 2, seed=5)
+    V, _ = synth.potential(*n, "smooth", seed=7)
+    want = O.bf_real_apply(n, gh, c, V)
+    assert np.linalg.norm(O.gamma_apply(n, gh, c, V) - want) < 1e-12 * np.linalg.norm(want)
+    monkeypatch.setattr(O, "gamma_complete", bad)
+    try:
+        got = O.gamma_apply(n, gh, c, V)
+        caught = np.linalg.norm(got - want) > 1e-10 * np.linalg.norm(want)
+    except O.OracleError:
+        caught = True
+    assert caught

@@ -327,3 +327,56 @@ def test_greedy_balances_best():
                 L = O.part_loads(part, w, p)
                 r[name] = L.max() / L.min()
             assert r["greedy"] <= r["basic"] and r["greedy"] <= r["improved"]
+
+
+# ---- Gamma-point real mode (Sec. 4.3, last paragraph)
+def _gamma_case(n, R, nb, seed, order="canonical"):
+    g = synth.sphere_glist(*n, R, order=order, seed=seed)
+    gh = synth.half_sphere(g)
+    c = synth.coefficients(gh, nb, seed=seed)
+    V, _ = synth.potential(*n, kind="smooth", seed=seed + 1)
+    return gh, c, V
+
+
+def test_half_sphere_splits_pairs():
+    g = synth.sphere_glist(8, 8, 8, 2.5)
+    gh = synth.half_sphere(g)
+    full = {tuple(x) for x in g}
+    half = {tuple(x) for x in gh}
+    assert (0, 0, 0) in half
+    for G in full - {(0, 0, 0)}:
+        mG = tuple(-x for x in G)
+        assert (G in half) != (mG in half)
+    assert 2 * len(gh) - 1 == len(g)
+
+
+@pytest.mark.parametrize("n,R", TINY)
+def test_gamma_completion_gives_real_bands(n, R):
+    gh, c, _ = _gamma_case(n, R, 3, seed=5, order="shuffled")
+    gf, cf = O.gamma_complete(gh, c)
+    psi = O.np_to_real(n, gf, cf)
+    assert np.abs(psi.imag).max() < 1e-13 * np.abs(psi.real).max()
+    # an incomplete (half-only) band is not real
+    psi_h = O.np_to_real(n, gh, c)
+    assert np.abs(psi_h.imag).max() > 1e-3 * np.abs(psi_h.real).max()
+
+
+@pytest.mark.parametrize("n,R", TINY)
+def test_gamma_apply_matches_real_bruteforce(n, R):
+    gh, c, V = _gamma_case(n, R, 3, seed=9, order="shuffled")
+    got = O.gamma_apply(n, gh, c, V)
+    want = O.bf_real_apply(n, gh, c, V)
+    assert _rel(got, want) < 1e-12
+    # the G = 0 result of a real band is real
+    z = np.flatnonzero(~np.any(gh != 0, axis=1))
+    assert np.abs(got[:, z].imag).max() < 1e-14
+
+
+def test_gamma_result_is_hermitian():
+    n, R = (8, 8, 8), 2.5
+    gh, c, V = _gamma_case(n, R, 2, seed=3)
+    gf, cf = O.gamma_complete(gh, c)
+    out = O.apply(n, gf, cf, V)
+    nh = len(gh)
+    nz = np.any(gh != 0, axis=1)
+    assert np.allclose(out[:, nh:], np.conj(out[:, :nh][:, nz]), rtol=0, atol=1e-14)
