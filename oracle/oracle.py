@@ -23,6 +23,10 @@ it follows:
   c(-G) = conj c(G) (c(0) real), acted on by ``apply`` and read back on the
   half; ``bf_real_apply`` writes the same action with real plane-wave sums
   (cosines and sines, brute force, tiny grids).
+* ``to_recip`` (the r -> G half of the recipe after Eq. 3: naive DFT passes,
+  1/N, gather) with its brute force ``bf_to_recip``; ``density`` /
+  ``gamma_density``: rho(r) = sum_n f_n |psi_n(r)|^2 (Sec. 3.1, first
+  paragraph), from ``to_real``.
 * ``sticks`` / ``greedy_partition`` (Sec. 3.2, Fig. 2), ``basic_partition``
   (Sec. 4.1, Fig. 3-4) and ``improved_partition`` (Sec. 4.2).
 
@@ -283,26 +287,70 @@ def gamma_apply(n, g_half, c_half, V, nthreads: int = 0) -> np.ndarray:
     return apply(n, g_full, c_full, V, nthreads)[:, :len(g_half)]
 
 
-def bf_real_apply(n, g_half, c_half, V) -> np.ndarray:
-    """Real-arithmetic brute force of the Gamma-point action (tiny grids):
+def bf_real_psi(n, g_half, c_half) -> np.ndarray:
+    """Real bands of the Gamma-point mode summed in real arithmetic (tiny grids):
     psi(r) = Re c(0) + 2 sum_{G != 0 in half} [Re c(G) cos(th) - Im c(G) sin(th)],
-    th = 2 pi G.r / n; then out(G) = (1/N) sum_r V(r) psi(r) (cos(th) - i sin(th))."""
+    th = 2 pi G.r / n.  float64 [nb, N]."""
     n1, n2, n3 = n
-    N = n1 * n2 * n3
     g_half = np.asarray(g_half, dtype=np.float64).reshape(-1, 3)
     c_half = np.asarray(c_half, dtype=np.complex128).reshape(-1, len(g_half))
     r = np.stack(np.meshgrid(np.arange(n1) / n1, np.arange(n2) / n2, np.arange(n3) / n3,
                              indexing="ij"), axis=-1).reshape(-1, 3)
     th = 2.0 * np.pi * (r @ g_half.T)                     # [N, nh]
-    cos, sin = np.cos(th), np.sin(th)
-    w = np.where(np.any(g_half != 0, axis=1), 2.0, 1.0)   # G = 0 counted once
-    Vr = np.asarray(V, dtype=np.float64).reshape(-1)
-    out = np.empty_like(c_half)
-    for b in range(len(c_half)):
-        psi = cos @ (w * c_half[b].real) - sin @ (np.where(w == 2.0, 2.0, 0.0) * c_half[b].imag)
-        f = Vr * psi
-        out[b] = (f @ cos - 1j * (f @ sin)) / N
-    return out
+    nz = np.any(g_half != 0, axis=1)
+    wc = np.where(nz, 2.0, 1.0)                           # G = 0 counted once
+    ws = np.where(nz, 2.0, 0.0)
+    return np.stack([np.cos(th) @ (wc * cb.real) - np.sin(th) @ (ws * cb.imag) for cb in c_half])
+
+
+def bf_real_apply(n, g_half, c_half, V) -> np.ndarray:
+    """Real-arithmetic brute force of the Gamma-point action (tiny grids):
+    psi from ``bf_real_psi``, then out(G) = (1/N) sum_r V(r) psi(r) (cos(th) - i sin(th))."""
+    n1, n2, n3 = n
+    N = n1 * n2 * n3
+    gh = np.asarray(g_half, dtype=np.float64).reshape(-1, 3)
+    r = np.stack(np.meshgrid(np.arange(n1) / n1, np.arange(n2) / n2, np.arange(n3) / n3,
+                             indexing="ij"), axis=-1).reshape(-1, 3)
+    th = 2.0 * np.pi * (r @ gh.T)
+    f = bf_real_psi(n, g_half, c_half) * np.asarray(V, dtype=np.float64).reshape(1, -1)
+    return (f @ np.cos(th) - 1j * (f @ np.sin(th))) / N
+
+
+# ---- the two halves of the action on their own, and the charge density
+def to_recip(n, g, u, nthreads: int = 0) -> np.ndarray:
+    """The r -> G half of Sec. 2's two-FFT recipe: out(G) = (1/N) sum_r u(r)
+    exp(-2 pi i G.r / n) at the list's G (three naive DFT passes of the C
+    oracle, then the gather), complex128 [nb, npw] from u [nb, n1, n2, n3]."""
+    N = n[0] * n[1] * n[2]
+    a = np.asarray(u, dtype=np.complex128).reshape(-1, n[0], n[1], n[2])
+    for axis in range(3):
+        a = axis_dft(n, a, axis, -1, nthreads)
+    return a.reshape(a.shape[0], N)[:, index_map(n, g)] / N
+
+
+def bf_to_recip(n, g, u) -> np.ndarray:
+    """(1/N) sum_r u(r) exp(-2 pi i G.r / n) summed point by point (tiny grids)."""
+    n1, n2, n3 = n
+    r = np.stack(np.meshgrid(np.arange(n1) / n1, np.arange(n2) / n2, np.arange(n3) / n3,
+                             indexing="ij"), axis=-1).reshape(-1, 3)
+    E = np.exp(-2j * np.pi * (r @ np.asarray(g, dtype=np.float64).T))   # [N, npw]
+    return np.asarray(u, dtype=np.complex128).reshape(-1, n1 * n2 * n3) @ E / (n1 * n2 * n3)
+
+
+def density(n, g, c, occ=None, nthreads: int = 0) -> np.ndarray:
+    """Charge density of Sec. 3.1: rho(r) = sum_n f_n |psi_n(r)|^2 with
+    psi_n = F+ S c_n (the unnormalised G -> r transform) and f_n = occ[n]
+    (1 when occ is None).  float64 [n1, n2, n3]."""
+    psi = to_real(n, g, c, nthreads)
+    f = np.ones(psi.shape[0]) if occ is None else np.asarray(occ, dtype=np.float64)
+    assert f.shape == (psi.shape[0],)
+    return np.tensordot(f, psi.real ** 2 + psi.imag ** 2, axes=1)
+
+
+def gamma_density(n, g_half, c_half, occ=None, nthreads: int = 0) -> np.ndarray:
+    """Density of real bands given on half of the sphere (Sec. 4.3): complete, then ``density``."""
+    g_full, c_full = gamma_complete(g_half, c_half)
+    return density(n, g_full, c_full, occ, nthreads)
 
 
 def sticks(n, g):

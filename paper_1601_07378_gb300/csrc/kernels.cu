@@ -112,7 +112,10 @@ int launch_k1_scatter_zpass(int dbl, int fast, const DevTables& t, const LaunchA
 }
 int launch_k2_ypass(int dbl, int fast, int sign, const DevTables& t, const LaunchAxes& ax, const void* tw2,
                     long long nb, void* cyl, void* slab, cudaStream_t st) {
-    if (!dbl && fast) switch (t.n2) {
+    // the compile-time y- and x-passes move line pairs along z as 16-byte
+    // vectors, which needs an even n3 (every pair then starts on an even
+    // element); odd n3 takes the runtime-radix kernels
+    if (!dbl && fast && (t.n3 & 1) == 0) switch (t.n2) {
 #define VLOC_CASE(N) case N: return LaunchCT<float, N>::k2(sign, t, tw2, nb, cyl, slab, st);
         VLOC_CT_SIZES(VLOC_CASE)
 #undef VLOC_CASE
@@ -124,7 +127,7 @@ int launch_k2_ypass(int dbl, int fast, int sign, const DevTables& t, const Launc
 int launch_k3_xpass_v(int dbl, int fast, const DevTables& t, const LaunchAxes& ax, const void* tw1, const void* V,
                       long long nb, void* slab, cudaStream_t st) {
     // the compile-time x-pass reads V two lines at a time (8-byte loads)
-    if (!dbl && fast && ((uintptr_t)V & 7) == 0) switch (t.n1) {
+    if (!dbl && fast && (t.n3 & 1) == 0 && ((uintptr_t)V & 7) == 0) switch (t.n1) {
 #define VLOC_CASE(N) case N: return LaunchCT<float, N>::k3(t, tw1, V, nb, slab, st);
         VLOC_CT_SIZES(VLOC_CASE)
 #undef VLOC_CASE
@@ -146,7 +149,7 @@ int launch_k3b_grad_v(int dbl, int fast, const DevTables& t, const LaunchAxes& a
                       const void* slab_g, long long nb, int bpg, double* partial, int* used, cudaStream_t st) {
     const int ng = (int)((nb + bpg - 1) / bpg);
     *used = ng;
-    if (!dbl && fast) switch (t.n1) {
+    if (!dbl && fast && (t.n3 & 1) == 0) switch (t.n1) {
 #define VLOC_CASE(N) case N: return LaunchCT<float, N>::k3b(t, tw1, slab_c, slab_g, nb, bpg, partial, st);
         VLOC_CT_SIZES(VLOC_CASE)
 #undef VLOC_CASE

@@ -46,6 +46,8 @@ def run(n, g, c, V, prec, **kw):
     ((40, 36, 50), 8, 3, "canonical"),        # several z tiles with a ragged tail
     ((30, 45, 27), 7, 2, "shuffled"),         # radices 3, 5, 9, 15
     ((64, 64, 64), 16, 4, "canonical"),
+    ((48, 48, 25), 6, 3, "shuffled"),         # compile-time x/y lengths, odd z length
+    ((64, 60, 45), 10, 2, "canonical"),
 ])
 def test_apply_matches_oracle(prec, n, R, nb, order, generic):
     # generic=True forces the runtime-radix kernels on every axis; otherwise
@@ -200,8 +202,10 @@ def test_batched_matches_individual():
 
 
 @pytest.mark.parametrize("prec", ["f32", "f64"])
-def test_backward_matches_oracle(prec):
-    n, R, nb = (32, 32, 32), 8, 3
+@pytest.mark.parametrize("n,R", [((32, 32, 32), 8), ((48, 48, 25), 6)])
+def test_backward_matches_oracle(prec, n, R):
+    # (48, 48, 25): compile-time x/y lengths with an odd z length
+    nb = 3
     g, c, V = make_case(n, R, nb, seed=4, prec=prec)
     rng = np.random.default_rng(13)
     gout = (rng.standard_normal(c.shape) + 1j * rng.standard_normal(c.shape)).astype(c.dtype)

@@ -380,3 +380,52 @@ def test_gamma_result_is_hermitian():
     nh = len(gh)
     nz = np.any(gh != 0, axis=1)
     assert np.allclose(out[:, nh:], np.conj(out[:, :nh][:, nz]), rtol=0, atol=1e-14)
+
+
+# ---- the r -> G half on its own and the charge density (Sec. 2, Sec. 3.1)
+@pytest.mark.parametrize("n,R", TINY)
+def test_to_recip_bruteforce_and_round_trip(n, R):
+    g = synth.sphere_glist(*n, R, order="shuffled", seed=2)
+    rng = np.random.default_rng(4)
+    u = rng.standard_normal((2, *n)) + 1j * rng.standard_normal((2, *n))
+    assert _rel(O.to_recip(n, g, u), O.bf_to_recip(n, g, u)) < 1e-12
+    # F- F+ = N I on the grid, so the r -> G half undoes the G -> r half
+    c = synth.coefficients(g, 3, seed=6)
+    assert _rel(O.to_recip(n, g, O.to_real(n, g, c)), c) < 1e-13
+
+
+def test_to_recip_library_cross_check():
+    n = (12, 10, 9)
+    g = synth.sphere_glist(*n, 3.3)
+    u = np.random.default_rng(1).standard_normal((2, *n)) + 0j
+    lib = np.fft.fftn(u, axes=(1, 2, 3)).reshape(2, -1)[:, O.np_index_map(n, g)] / np.prod(n)
+    assert _rel(O.to_recip(n, g, u), lib) < 1e-13
+
+
+@pytest.mark.parametrize("n,R", TINY)
+def test_density_bruteforce_and_parseval(n, R):
+    g = synth.sphere_glist(*n, R, order="shuffled", seed=3)
+    c = synth.coefficients(g, 4, seed=8)
+    f = np.array([2.0, 1.5, 0.25, 0.0])
+    rho = O.density(n, g, c, f)
+    psi = O.bf_to_real(n, g, c).reshape(4, -1)
+    assert _rel(rho.ravel(), (f[:, None] * np.abs(psi) ** 2).sum(0)) < 1e-12
+    assert rho.min() >= 0.0
+    # Parseval for the unnormalised G -> r transform
+    N = np.prod(n)
+    assert abs(rho.sum() - N * (f * (np.abs(c) ** 2).sum(1)).sum()) < 1e-12 * rho.sum()
+
+
+def test_density_of_single_plane_wave_is_flat():
+    n = (6, 5, 4)
+    g = np.array([[1, -2, 1]], dtype=np.int32)
+    rho = O.density(n, g, np.array([[0.6 - 0.8j]]), [3.0])
+    assert np.allclose(rho, 3.0, rtol=0, atol=1e-14)
+
+
+@pytest.mark.parametrize("n,R", TINY)
+def test_gamma_density_matches_real_bruteforce(n, R):
+    gh, c, _ = _gamma_case(n, R, 3, seed=12, order="shuffled")
+    f = np.array([1.0, 0.5, 2.0])
+    want = (f[:, None] * O.bf_real_psi(n, gh, c) ** 2).sum(0)
+    assert _rel(O.gamma_density(n, gh, c, f).ravel(), want) < 1e-12
