@@ -366,6 +366,34 @@ def run_ours(args, rank, world, local_rank):
                  "kernel_share": {k: round(v[1] / sum(t for _, t in profg.values()), 4) for k, v in profg.items()}}
         del pg, cg, og
 
+    # ---- the halves on their own and the charge density (96^3, FP32)
+    halves = None
+    if not args.no_extra:
+        def leg(fn, k, nbands, bytes_per_band):
+            ms_l = time_steps(fn, k, 2, stream, dist_on)
+            rate = world * nbands / (ms_l / k / 1e3)
+            return {"value": rate, "unit": "bands/s", "ms_per_step": ms_l / k, "bands": nbands,
+                    "alg_GBps": rate / world * bytes_per_band / 1e9,
+                    "frac_of_hbm": rate / world * bytes_per_band / (peak * 1e9)}
+        Nn = GRID[0] * GRID[1] * GRID[2]
+        cyl_b, slab_b = info["nsticks"] * GRID[2] * 8, info["nplanes"] * GRID[1] * GRID[2] * 8
+        nh = 256
+        grid_d = torch.empty((nh, *GRID), dtype=torch.complex64, device="cuda")
+        rho_d = torch.empty(GRID, dtype=torch.float32, device="cuda")
+        kh = max(3, args.steps // 2)
+        halves = {
+            "to_real": leg(lambda: plan.to_real(c_d[:nh], grid_d), kh, nh,
+                           info["npw"] * 8 + 2 * cyl_b + 2 * slab_b + Nn * 8),
+            "to_recip": leg(lambda: plan.to_recip(grid_d, out_d[:nh]), kh, nh,
+                            Nn * 8 + 2 * slab_b + 2 * cyl_b + info["npw"] * 8),
+            "density": leg(lambda: plan.density(c_d, rho=rho_d), kh, NBANDS,
+                           info["npw"] * 8 + 2 * cyl_b + slab_b),
+            "what": "96^3, R = 24, FP32: psi = F+ S c to full grids (256 bands), r -> G of full grids "
+                    "(256 bands), rho = sum |psi_n|^2 (1024 bands); alg bytes per band: "
+                    "to_real/to_recip npw + 2 cyl + 2 slab + N, density npw + 2 cyl + slab (complex64)",
+        }
+        del grid_d, rho_d
+
     # ---- uneven multi-instance batch, one graph launch per step: 8 grids
     # 48^3 .. 144^3, R = n/4, 64 (i+1) bands each (FP32)
     batched = None
@@ -466,7 +494,7 @@ def run_ours(args, rank, world, local_rank):
             "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clocks,
             "fp64": f64, "adjoint": {"value": adj, "unit": "bands/s"},
             "grid_96x96x120": {"value": c2_value, "unit": "bands/s"},
-            "batched_uneven": batched, "autograd_512": autograd, "gamma_real": gamma,
+            "batched_uneven": batched, "autograd_512": autograd, "gamma_real": gamma, "half_transforms_density": halves,
             "cufft_comparison": cufft,
         }
         print(json.dumps(line), flush=True)

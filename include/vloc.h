@@ -168,12 +168,52 @@ int vloc_apply_adjoint(vloc_plan plan, const void* coeffs, const void* V, int64_
  *   grad_coeffs (nullable) = A^H grad_out = A grad_out.
  *   grad_V      (nullable, overwritten, real [n1][n2][n3]) =
  *       (1/N) sum_n Re( conj(F+ S grad_out_n) * F+ S c_n ),
- *   with psi_n = F+ S c_n recomputed band by band (no grid is stored); the
- *   band sum is accumulated in FP64 in a fixed order (deterministic).
- * Errors as vloc_apply.
+ *   with psi_n = F+ S c_n recomputed band by band (no grid is stored).
+ *   The band sum runs in groups of at most 16 bands (FP32 sums in the FP32
+ *   path, FP64 in the FP64 path) whose partial sums are added in FP64 in a
+ *   fixed order, so the result is deterministic.
+ * Errors as vloc_apply; VLOC_ERR_STATE for a VLOC_GAMMA plan; VLOC_ERR_SIZE
+ * when the dL/dV x-pass does not fit in shared memory (FP64, n1 > ~170).
  */
 int vloc_backward(vloc_plan plan, const void* coeffs, const void* grad_out, const void* V,
                   int64_t nbands, void* grad_coeffs, void* grad_V, void* stream);
+
+/*
+ * vloc_to_real -- the G -> r half of the action on its own (Sec. 2, the
+ * first FFT of the two-FFT recipe): psi_n = F+ S c_n on the full grid, the
+ * unnormalised e^{+} transform through the same compact z- and y-passes.
+ *   coeffs : device [nbands][npw] complex.
+ *   psi    : device [nbands][n1][n2][n3] complex, i3 fastest (written).
+ * No overlap between the two.  Not for VLOC_GAMMA plans (VLOC_ERR_STATE).
+ * Errors as vloc_apply.
+ */
+int vloc_to_real(vloc_plan plan, const void* coeffs, int64_t nbands, void* psi, void* stream);
+
+/*
+ * vloc_to_recip -- the r -> G half on its own (the second FFT of the
+ * recipe): out_n(G) = (1/N) sum_r u_n(r) e^{-2 pi i G.r/n} at the plan's G,
+ * through the output-pruned x-pass, the y-pass and the z-pass + gather.
+ *   u   : device [nbands][n1][n2][n3] complex (read only).
+ *   out : device [nbands][npw] complex (written).
+ * to_recip(to_real(c)) = c.  Not for VLOC_GAMMA plans.  Errors as vloc_apply.
+ */
+int vloc_to_recip(vloc_plan plan, const void* u, int64_t nbands, void* out, void* stream);
+
+/*
+ * vloc_density -- the charge density of Sec. 3.1, rho(r) = sum_n f_n
+ * |psi_n(r)|^2 with psi_n = F+ S c_n (unnormalised transform).
+ *   coeffs : device [nbands][npw] complex (the half list for VLOC_GAMMA
+ *            plans, whose bands are real: two travel per complex transform).
+ *   occ    : device [nbands] real weights f_n, or NULL for f_n = 1.
+ *   rho    : device real [n1][n2][n3], overwritten.
+ * The band sum runs as in vloc_backward (groups of at most 16 bands, their
+ * partial sums added in FP64 in a fixed order): deterministic.  No grid is
+ * stored.  nbands = 0 writes zeros.
+ * Errors as vloc_apply; VLOC_ERR_SIZE when the density x-pass does not fit
+ * in shared memory (FP64, n1 > ~170).
+ */
+int vloc_density(vloc_plan plan, const void* coeffs, const void* occ, int64_t nbands, void* rho,
+                 void* stream);
 
 /*
  * vloc_apply_batched -- ninst independent applies (plans of different grids
@@ -247,8 +287,10 @@ int vloc_apply_noalloc(vloc_plan plan, const void* coeffs, const void* V, int64_
  * every kernel of a plan's calls, for the roofline and profile reports.
  * Kernel slots: 0 scatter + inverse z-pass, 1 inverse y-pass, 2 x-pass with
  * V(r), 3 forward y-pass, 4 forward z-pass + gather, 5 dL/dV x-pass,
- * 6 auxiliary (zero / convert), 7 Gamma-point pack / unpack. */
-#define VLOC_NKERNELS 8
+ * 6 auxiliary (zero / convert / reduce), 7 Gamma-point pack / unpack,
+ * 8 inverse x-pass to a full grid, 9 forward x-pass from a full grid,
+ * 10 density x-pass, 11 unused. */
+#define VLOC_NKERNELS 12
 typedef struct vloc_kernel_stat {
     int64_t launches;
     double total_ms;

@@ -34,7 +34,8 @@ struct LaunchAxes {
 };
 
 // Kernel kinds (profiling slots).
-enum KernelKind { KK_SCATTER_Z = 0, KK_Y_INV = 1, KK_X_V = 2, KK_Y_FWD = 3, KK_Z_GATHER = 4, KK_GRAD_V = 5, KK_AUX = 6, KK_GAMMA = 7 };
+enum KernelKind { KK_SCATTER_Z = 0, KK_Y_INV = 1, KK_X_V = 2, KK_Y_FWD = 3, KK_Z_GATHER = 4, KK_GRAD_V = 5, KK_AUX = 6, KK_GAMMA = 7, KK_X_TO_GRID = 8,
+                  KK_X_FROM_GRID = 9, KK_DENSITY = 10 };
 
 // Typed launchers (defined in kernels_impl.cuh, instantiated per precision
 // in kernels_f32.cu / kernels_f64.cu).  Every pointer is a device pointer;
@@ -43,6 +44,7 @@ enum KernelKind { KK_SCATTER_Z = 0, KK_Y_INV = 1, KK_X_V = 2, KK_Y_FWD = 3, KK_Z
 template <typename T> struct Launch {
     static size_t smem(int n);
     static size_t smem_grad(int n);
+    static size_t smem_dens(int n);
     static int set_limits(int nmax, int optin);
     static int twiddles(void* tw, int n, cudaStream_t st);
     static int k1(const DevTables& t, const LaunchAxes& ax, const void* tw3, const void* coeffs, long long nb,
@@ -56,6 +58,13 @@ template <typename T> struct Launch {
     static int k3b(const DevTables& t, const LaunchAxes& ax, const void* tw1, const void* sc, const void* sg,
                    long long nb, int ngroups, double* partial, cudaStream_t st);
     static int finish_grad(const double* acc, void* g, long long N, cudaStream_t st);
+    // x-pass between the slab and a full grid [nb][n1][n2][n3]: sign +1
+    // slab -> grid (inverse), -1 grid -> slab (forward)
+    static int k3g(int sign, const DevTables& t, const LaunchAxes& ax, const void* tw1, long long nb, void* slab,
+                   void* grid, cudaStream_t st);
+    // density x-pass over nb slab bands in groups of bpg (see launch_k3d_density)
+    static int k3d(const DevTables& t, const LaunchAxes& ax, const void* tw1, const void* slab, long long nb, int bpg,
+                   const void* occ, long long b_base, int pair, long long nreal, double* partial, cudaStream_t st);
 };
 extern template struct Launch<float>;
 extern template struct Launch<double>;
@@ -70,6 +79,9 @@ template <typename T, int N> struct LaunchCT {
     static int k4(const DevTables& t, const void* tw3, const void* cyl, long long nb, void* out, cudaStream_t st);
     static int k3b(const DevTables& t, const void* tw1, const void* sc, const void* sg, long long nb, int bpg,
                    double* partial, cudaStream_t st);
+    static int k3g(int sign, const DevTables& t, const void* tw1, long long nb, void* slab, void* grid, cudaStream_t st);
+    static int k3d(const DevTables& t, const void* tw1, const void* slab, long long nb, int bpg, const void* occ,
+                   long long b_base, int pair, long long nreal, double* partial, cudaStream_t st);
 };
 
 // Precision dispatch (kernels.cu): dbl = 0 for float, 1 for double; `fast`
@@ -88,6 +100,17 @@ int launch_k4_zpass_gather(int dbl, int fast, const DevTables& t, const LaunchAx
 // groups (in order) into acc.  Returns the groups used via *used.
 int launch_k3b_grad_v(int dbl, int fast, const DevTables& t, const LaunchAxes& ax, const void* tw1, const void* slab_c,
                       const void* slab_g, long long nb, int bpg, double* partial, int* used, cudaStream_t st);
+// x-pass between slab and full grid (sign +1: slab -> grid, -1: grid -> slab).
+int launch_k3_grid(int dbl, int fast, int sign, const DevTables& t, const LaunchAxes& ax, const void* tw1,
+                   long long nb, void* slab, void* grid, cudaStream_t st);
+// Density x-pass: for slab bands b < nb (global index b_base + b) adds the
+// weighted |psi|^2 of groups of at most bpg bands into partial[group][N]
+// (occ: device weights or null; pair = 1 for Gamma-point pairs of nreal
+// real bands).  Returns the groups used via *used.
+int launch_k3d_density(int dbl, int fast, const DevTables& t, const LaunchAxes& ax, const void* tw1, const void* slab,
+                       long long nb, int bpg, const void* occ, long long b_base, int pair, long long nreal,
+                       double* partial, int* used, cudaStream_t st);
+size_t density_smem_bytes(int dbl, int n);
 int launch_reduce_partials(const double* partial, int ngroups, long long N, double* acc, cudaStream_t st);
 int launch_finish_grad_v(int dbl, const double* acc, void* gradV, long long N, cudaStream_t st);
 // Gamma-point real mode: pack bands (2p, 2p+1) of c [nb][nh] into complex

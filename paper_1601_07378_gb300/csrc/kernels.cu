@@ -159,6 +159,33 @@ int launch_k3b_grad_v(int dbl, int fast, const DevTables& t, const LaunchAxes& a
                : Launch<float>::k3b(t, ax, tw1, slab_c, slab_g, nb, ng, partial, st);
 }
 
+int launch_k3_grid(int dbl, int fast, int sign, const DevTables& t, const LaunchAxes& ax, const void* tw1,
+                   long long nb, void* slab, void* grid, cudaStream_t st) {
+    // the compile-time x-pass moves z line pairs as 16-byte vectors
+    if (!dbl && fast && (t.n3 & 1) == 0 && ((uintptr_t)grid & 15) == 0) switch (t.n1) {
+#define VLOC_CASE(N) case N: return LaunchCT<float, N>::k3g(sign, t, tw1, nb, slab, grid, st);
+        VLOC_CT_SIZES(VLOC_CASE)
+#undef VLOC_CASE
+        default: break;
+    }
+    return dbl ? Launch<double>::k3g(sign, t, ax, tw1, nb, slab, grid, st)
+               : Launch<float>::k3g(sign, t, ax, tw1, nb, slab, grid, st);
+}
+int launch_k3d_density(int dbl, int fast, const DevTables& t, const LaunchAxes& ax, const void* tw1, const void* slab,
+                       long long nb, int bpg, const void* occ, long long b_base, int pair, long long nreal,
+                       double* partial, int* used, cudaStream_t st) {
+    *used = (int)((nb + bpg - 1) / bpg);
+    if (!dbl && fast && (t.n3 & 1) == 0) switch (t.n1) {
+#define VLOC_CASE(N) case N: return LaunchCT<float, N>::k3d(t, tw1, slab, nb, bpg, occ, b_base, pair, nreal, partial, st);
+        VLOC_CT_SIZES(VLOC_CASE)
+#undef VLOC_CASE
+        default: break;
+    }
+    return dbl ? Launch<double>::k3d(t, ax, tw1, slab, nb, bpg, occ, b_base, pair, nreal, partial, st)
+               : Launch<float>::k3d(t, ax, tw1, slab, nb, bpg, occ, b_base, pair, nreal, partial, st);
+}
+size_t density_smem_bytes(int dbl, int n) { return dbl ? Launch<double>::smem_dens(n) : Launch<float>::smem_dens(n); }
+
 __global__ void k_reduce_partials(const double* __restrict__ partial, int ng, long long N, double* __restrict__ acc) {
     const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (i >= N) return;

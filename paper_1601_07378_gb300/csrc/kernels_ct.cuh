@@ -354,6 +354,127 @@ __global__ void __launch_bounds__(kThreads) k3b_ct(DevTables t, const float2* __
     }
 }
 
+// ------------------------------------------- half transforms and density
+struct GridRowsP {  // x line pair at fixed (y, z0 + 2 slot) of a full grid
+    float2* g;      // grid[b][0][y][z0]
+    long long pstride;
+    __device__ __forceinline__ P2f operator()(int e, int slot) const {
+        return *reinterpret_cast<const P2f*>(g + e * pstride + 2 * slot);
+    }
+    __device__ __forceinline__ void operator()(int e, int slot, P2f v) const {
+        *reinterpret_cast<P2f*>(g + e * pstride + 2 * slot) = v;
+    }
+};
+
+// S = +1: slab tile -> full grid (inverse x-pass, input pruned to the
+// occupied planes); S = -1: full grid -> slab tile (forward, output pruned).
+template <int S, int N>
+__global__ void __launch_bounds__(kThreads) k3g_ct(DevTables t, const float2* __restrict__ tw1, float2* slab,
+                                                  float2* grid) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int n2 = t.n2, n3 = t.n3;
+    float2* buf = reinterpret_cast<float2*>(smem_raw);
+    float2* stw = buf + N * kLdP;
+    int* xrow = reinterpret_cast<int*>(stw + N);
+    const int y = blockIdx.x;
+    const int z0 = blockIdx.y * kLines;
+    const long long b = blockIdx.z;
+    const int lines = min(kLines, n3 - z0);
+    load_tw<float>(stw, tw1, N);
+    for (int e = threadIdx.x; e < N; e += kThreads) xrow[e] = t.xrow_plane[e];
+    __syncthreads();
+    const long long pstride = (long long)n2 * n3;
+    XRowsP xr{slab + b * t.NP * pstride + (long long)y * n3 + z0, xrow, pstride};
+    GridRowsP gr{grid + b * (long long)N * pstride + (long long)y * n3 + z0, pstride};
+    const bool act = 2 * slot_of() < lines;
+    if constexpr (S > 0) fft_ct<N, +1, kWarps, false, false, false>(stw, xr, gr, buf, slot_of(), sub_of(), warp_of(), act);
+    else fft_ct<N, -1, kWarps, false, false, false>(stw, gr, xr, buf, slot_of(), sub_of(), warp_of(), act);
+}
+
+// Density x-pass for one (y, z tile, band group): each band's inverse
+// x-pass ends in registers, where the weighted |psi|^2 is added in FP32 over
+// the group's bands (at most 16); the group's partial sum is written in FP64
+// and the groups are added later in a fixed order.
+template <int N>
+__global__ void __launch_bounds__(kThreads) k3d_ct(DevTables t, const float2* __restrict__ tw1, const float2* slab,
+                                                  int nb, int bpg, const float* __restrict__ occ, long long b_base,
+                                                  int pair, long long nreal, double* __restrict__ partial) {
+    using SC = Sched<N>;
+    constexpr int nst = SC::nst;
+    static_assert(nst >= 2, "compile-time x-pass needs at least two stages");
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int n2 = t.n2, n3 = t.n3;
+    float2* buf = reinterpret_cast<float2*>(smem_raw);
+    float2* stw = buf + N * kLdP;
+    int* xrow = reinterpret_cast<int*>(stw + N);
+    const int slot = slot_of(), sub = sub_of(), warp = warp_of();
+    const int y = blockIdx.x;
+    const int z0 = blockIdx.y * kLines;
+    const int grp = blockIdx.z;
+    const int lines = min(kLines, n3 - z0);
+    const bool act = 2 * slot < lines;
+    load_tw<float>(stw, tw1, N);
+    for (int e = threadIdx.x; e < N; e += kThreads) xrow[e] = t.xrow_plane[e];
+    __syncthreads();
+    const long long pstride = (long long)n2 * n3;
+    using L = NatStage<N, +1, kWarps, nst - 1>;
+    constexpr int R = SC::R(nst - 1);
+    float2 acc[L::U][R];
+#pragma unroll
+    for (int u = 0; u < L::U; ++u)
+#pragma unroll
+        for (int r = 0; r < R; ++r) acc[u][r] = make_float2(0.f, 0.f);
+    SmemP sb{buf};
+    const int b1 = min(nb, (grp + 1) * bpg);
+    for (int b = grp * bpg; b < b1; ++b) {
+        double wxd, wyd;
+        density_weights(occ, b_base + b, pair, nreal, wxd, wyd);
+        const float wx = (float)wxd, wy = (float)wyd;
+        XRowsP xc{const_cast<float2*>(slab) + (long long)b * t.NP * pstride + (long long)y * n3 + z0, xrow, pstride};
+        NatStage<N, +1, kWarps, 0>::template run<false>(stw, xc, sb, slot, sub, warp, act);
+        __syncthreads();
+        if constexpr (nst >= 3) {
+            NatStage<N, +1, kWarps, 1>::template run<true>(stw, sb, sb, slot, sub, warp, act);
+            __syncthreads();
+        }
+        if constexpr (nst >= 4) {
+            NatStage<N, +1, kWarps, 2>::template run<true>(stw, sb, sb, slot, sub, warp, act);
+            __syncthreads();
+        }
+        if (act) {
+            P2f h[L::U][R];
+            L::compute(h, stw, sb, slot, sub, warp);
+#pragma unroll
+            for (int u = 0; u < L::U; ++u) {
+                const int i = 2 * (warp + u * kWarps) + sub;
+                if (L::NI % (2 * kWarps) == 0 || i < L::NI) {
+#pragma unroll
+                    for (int r = 0; r < R; ++r) {
+                        acc[u][r].x += wx * h[u][r].a.x * h[u][r].a.x + wy * h[u][r].a.y * h[u][r].a.y;
+                        acc[u][r].y += wx * h[u][r].b.x * h[u][r].b.x + wy * h[u][r].b.y * h[u][r].b.y;
+                    }
+                }
+            }
+        }
+        __syncthreads();
+    }
+    if (act) {
+        double* part = partial + (long long)grp * N * pstride + (long long)y * n3 + z0 + 2 * slot;
+#pragma unroll
+        for (int u = 0; u < L::U; ++u) {
+            const int i = 2 * (warp + u * kWarps) + sub;
+            if (L::NI % (2 * kWarps) == 0 || i < L::NI) {
+#pragma unroll
+                for (int r = 0; r < R; ++r) {
+                    double* q = part + (long long)(i + r * L::NI) * pstride;
+                    q[0] = (double)acc[u][r].x;
+                    q[1] = (double)acc[u][r].y;
+                }
+            }
+        }
+    }
+}
+
 // ------------------------------------------------------------ launchers
 template <int N> struct CtSmem {
     static constexpr size_t sm = ct_smem<N>();
@@ -408,6 +529,32 @@ int LaunchCT<T, N>::k3b(const DevTables& t, const void* tw1, const void* sc, con
     const double invN = 1.0 / ((double)t.n1 * t.n2 * t.n3);
     k3b_ct<N><<<grid, kThreads, sm, st>>>(t, (const float2*)tw1, (const float2*)sc, (const float2*)sg, (int)nb, bpg,
                                           partial, invN);
+    return (int)cudaGetLastError();
+}
+template <typename T, int N>
+int LaunchCT<T, N>::k3g(int sign, const DevTables& t, const void* tw1, long long nb, void* slab, void* grid,
+                        cudaStream_t st) {
+    const dim3 g3(t.n2, (t.n3 + kLines - 1) / kLines, (unsigned)nb);
+    if (sign > 0) {
+        static const cudaError_t once = CtSmem<N>::ensure(k3g_ct<+1, N>);
+        if (once) return (int)once;
+        k3g_ct<+1, N><<<g3, kThreads, CtSmem<N>::sm, st>>>(t, (const float2*)tw1, (float2*)slab, (float2*)grid);
+    } else {
+        static const cudaError_t once = CtSmem<N>::ensure(k3g_ct<-1, N>);
+        if (once) return (int)once;
+        k3g_ct<-1, N><<<g3, kThreads, CtSmem<N>::sm, st>>>(t, (const float2*)tw1, (float2*)slab, (float2*)grid);
+    }
+    return (int)cudaGetLastError();
+}
+template <typename T, int N>
+int LaunchCT<T, N>::k3d(const DevTables& t, const void* tw1, const void* slab, long long nb, int bpg, const void* occ,
+                        long long b_base, int pair, long long nreal, double* partial, cudaStream_t st) {
+    static const cudaError_t once = CtSmem<N>::ensure(k3d_ct<N>);
+    if (once) return (int)once;
+    const int ng = (int)((nb + bpg - 1) / bpg);
+    const dim3 grid(t.n2, (t.n3 + kLines - 1) / kLines, ng);
+    k3d_ct<N><<<grid, kThreads, CtSmem<N>::sm, st>>>(t, (const float2*)tw1, (const float2*)slab, (int)nb, bpg,
+                                                     (const float*)occ, b_base, pair, nreal, partial);
     return (int)cudaGetLastError();
 }
 template <typename T, int N>

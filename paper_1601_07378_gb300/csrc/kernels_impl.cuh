@@ -312,6 +312,105 @@ template <typename T> __global__ void k_finish_grad_v(const double* __restrict__
     if (i < N) g[i] = (T)acc[i];
 }
 
+// ------------------------------------------- half transforms and density
+// The two halves of the chain on their own (x-pass to / from a full grid),
+// and the charge density rho(r) = sum_n f_n |psi_n(r)|^2 (Sec. 3.1).
+template <typename T> struct GridRows {  // x line at fixed (y, z0 + l) of a full grid
+    V2<T>* g;           // grid[b][0][y][z0]
+    long long pstride;  // n2 * n3
+    __device__ __forceinline__ V2<T> operator()(int e, int l) const { return g[e * pstride + l]; }
+    __device__ __forceinline__ void operator()(int e, int l, V2<T> v) const { g[e * pstride + l] = v; }
+};
+
+// S = +1: inverse x-pass of a slab tile (input pruned to the occupied
+// planes) into the full grid [b][n1][n2][n3]; S = -1: forward x-pass of a
+// full grid, kept on the occupied planes of the slab (output pruned).
+template <typename T, int S>
+__global__ void __launch_bounds__(kThreads) k3_grid(DevTables t, AxisPlan ax, const V2<T>* __restrict__ tw1,
+                                                   V2<T>* slab, V2<T>* grid) {
+    using V = V2<T>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int n1 = t.n1, n2 = t.n2, n3 = t.n3;
+    V* P = reinterpret_cast<V*>(smem_raw);
+    V* Q = P + n1 * kLd;
+    V* stw = Q + n1 * kLd;
+    int* xrow = reinterpret_cast<int*>(stw + n1);
+    const int y = blockIdx.x;
+    const int z0 = blockIdx.y * kLines;
+    const long long b = blockIdx.z;
+    const int lines = min(kLines, n3 - z0);
+    load_tw<T>(stw, tw1, n1);
+    for (int e = threadIdx.x; e < n1; e += kThreads) xrow[e] = t.xrow_plane[e];
+    __syncthreads();
+    const long long pstride = (long long)n2 * n3;
+    XRows<T> xr{slab + b * t.NP * pstride + (long long)y * n3 + z0, xrow, pstride};
+    GridRows<T> gr{grid + b * (long long)n1 * pstride + (long long)y * n3 + z0, pstride};
+    if constexpr (S > 0) fft_lines<+1>(ax, stw, xr, gr, P, Q, lines);
+    else fft_lines<-1>(ax, stw, gr, xr, P, Q, lines);
+}
+
+// Weights of band b in the density: (f_b, f_b) for a complex band; for a
+// Gamma-point pair b = (2b, 2b + 1) packed as psi_2b + i psi_2b+1 (both
+// real), (f_2b, f_2b+1) on the real and imaginary parts, 0 past the last
+// real band.  f = 1 when occ is null.
+template <typename T>
+__device__ __forceinline__ void density_weights(const T* occ, long long b, int pair, long long nreal, double& wx,
+                                                double& wy) {
+    if (!pair) {
+        wx = wy = occ ? (double)occ[b] : 1.0;
+        return;
+    }
+    wx = occ ? (double)occ[2 * b] : 1.0;
+    wy = 2 * b + 1 < nreal ? (occ ? (double)occ[2 * b + 1] : 1.0) : 0.0;
+}
+template <typename T> struct AccumNorm {  // acc += wx re^2 + wy im^2
+    double* acc;                          // shared [n1][kLd]
+    double wx, wy;
+    __device__ __forceinline__ void operator()(int e, int l, V2<T> v) const {
+        acc[e * kLd + l] += wx * ((double)v.x * (double)v.x) + wy * ((double)v.y * (double)v.y);
+    }
+};
+
+// One (y, z tile, band group): psi = inverse x-pass of each band's slab tile,
+// acc += weighted |psi|^2 in FP64, then the group's partial sum is written
+// (groups are added later in a fixed order).
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k3d_density(DevTables t, AxisPlan ax, const V2<T>* __restrict__ tw1,
+                                                       const V2<T>* slab, int nb, int bpg, const T* __restrict__ occ,
+                                                       long long b_base, int pair, long long nreal,
+                                                       double* __restrict__ partial) {
+    using V = V2<T>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int n1 = t.n1, n2 = t.n2, n3 = t.n3;
+    V* P = reinterpret_cast<V*>(smem_raw);
+    V* Q = P + n1 * kLd;
+    V* stw = Q + n1 * kLd;
+    double* acc = reinterpret_cast<double*>(stw + n1);
+    int* xrow = reinterpret_cast<int*>(acc + n1 * kLd);
+    const int y = blockIdx.x;
+    const int z0 = blockIdx.y * kLines;
+    const int grp = blockIdx.z;
+    const int lines = min(kLines, n3 - z0);
+    load_tw<T>(stw, tw1, n1);
+    for (int e = threadIdx.x; e < n1; e += kThreads) xrow[e] = t.xrow_plane[e];
+    for (int i = threadIdx.x; i < n1 * kLd; i += kThreads) acc[i] = 0.0;
+    __syncthreads();
+    const long long pstride = (long long)n2 * n3;
+    const int b1 = min(nb, (grp + 1) * bpg);
+    for (int b = grp * bpg; b < b1; ++b) {
+        double wx, wy;
+        density_weights(occ, b_base + b, pair, nreal, wx, wy);
+        XRows<T> xc{const_cast<V*>(slab) + (long long)b * t.NP * pstride + (long long)y * n3 + z0, xrow, pstride};
+        fft_lines<+1>(ax, stw, xc, AccumNorm<T>{acc, wx, wy}, P, Q, lines);
+        __syncthreads();
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    double* part = partial + (long long)grp * n1 * pstride;
+    if (lane < lines) {
+        for (int e = warp; e < n1; e += kWarps) part[((long long)e * n2 + y) * n3 + z0 + lane] = acc[e * kLd + lane];
+    }
+}
+
 // ====================================================== typed launchers
 // Members of Launch<T> (declared in internal.h), instantiated once per
 // precision in kernels_f32.cu / kernels_f64.cu.
@@ -330,9 +429,14 @@ template <typename T> size_t Launch<T>::smem_grad(int n) {
     return 3 * (size_t)n * kLd * sizeof(V2<T>) + (size_t)n * kLd * sizeof(double) + (size_t)n * sizeof(V2<T>) +
            (size_t)n * sizeof(int) + 16;
 }
+template <typename T> size_t Launch<T>::smem_dens(int n) {
+    return 2 * (size_t)n * kLd * sizeof(V2<T>) + (size_t)n * sizeof(V2<T>) + (size_t)n * kLd * sizeof(double) +
+           (size_t)n * sizeof(int) + 16;
+}
 template <typename T> int Launch<T>::set_limits(int nmax, int optin) {
     const int b = (int)smem(nmax);
     const int bg = (int)smem_grad(nmax);
+    const int bd = (int)smem_dens(nmax);
     cudaError_t e;
     if ((e = cudaFuncSetAttribute(k1_scatter_zpass<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, b))) return e;
     if ((e = cudaFuncSetAttribute(k2_ypass<T, +1>, cudaFuncAttributeMaxDynamicSharedMemorySize, b))) return e;
@@ -340,6 +444,9 @@ template <typename T> int Launch<T>::set_limits(int nmax, int optin) {
     if ((e = cudaFuncSetAttribute(k3_xpass_v<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, b))) return e;
     if ((e = cudaFuncSetAttribute(k4_zpass_gather<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, b))) return e;
     if (bg <= optin && (e = cudaFuncSetAttribute(k3b_grad_v<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, bg))) return e;
+    if ((e = cudaFuncSetAttribute(k3_grid<T, +1>, cudaFuncAttributeMaxDynamicSharedMemorySize, b))) return e;
+    if ((e = cudaFuncSetAttribute(k3_grid<T, -1>, cudaFuncAttributeMaxDynamicSharedMemorySize, b))) return e;
+    if (bd <= optin && (e = cudaFuncSetAttribute(k3d_density<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, bd))) return e;
     return 0;
 }
 template <typename T> int Launch<T>::twiddles(void* tw, int n, cudaStream_t st) {
@@ -387,6 +494,27 @@ int Launch<T>::k3b(const DevTables& t, const LaunchAxes& ax, const void* tw1, co
     const double invN = 1.0 / ((double)t.n1 * t.n2 * t.n3);
     k3b_grad_v<T><<<grid, kThreads, smem_grad(t.n1), st>>>(t, axis_of(ax, 0), (const V2<T>*)tw1, (const V2<T>*)sc,
                                                            (const V2<T>*)sg, (int)nb, bpg, partial, invN);
+    return (int)cudaGetLastError();
+}
+template <typename T>
+int Launch<T>::k3g(int sign, const DevTables& t, const LaunchAxes& ax, const void* tw1, long long nb, void* slab,
+                   void* grid, cudaStream_t st) {
+    const dim3 grid3(t.n2, (t.n3 + kLines - 1) / kLines, (unsigned)nb);
+    if (sign > 0)
+        k3_grid<T, +1><<<grid3, kThreads, smem(t.n1), st>>>(t, axis_of(ax, 0), (const V2<T>*)tw1, (V2<T>*)slab,
+                                                             (V2<T>*)grid);
+    else
+        k3_grid<T, -1><<<grid3, kThreads, smem(t.n1), st>>>(t, axis_of(ax, 0), (const V2<T>*)tw1, (V2<T>*)slab,
+                                                             (V2<T>*)grid);
+    return (int)cudaGetLastError();
+}
+template <typename T>
+int Launch<T>::k3d(const DevTables& t, const LaunchAxes& ax, const void* tw1, const void* slab, long long nb, int bpg,
+                   const void* occ, long long b_base, int pair, long long nreal, double* partial, cudaStream_t st) {
+    const int ng = (int)((nb + bpg - 1) / bpg);
+    const dim3 grid(t.n2, (t.n3 + kLines - 1) / kLines, ng);
+    k3d_density<T><<<grid, kThreads, smem_dens(t.n1), st>>>(t, axis_of(ax, 0), (const V2<T>*)tw1, (const V2<T>*)slab,
+                                                            (int)nb, bpg, (const T*)occ, b_base, pair, nreal, partial);
     return (int)cudaGetLastError();
 }
 template <typename T> int Launch<T>::finish_grad(const double* acc, void* g, long long N, cudaStream_t st) {

@@ -714,6 +714,114 @@ int vloc_backward(vloc_plan p, const void* c, const void* gout, const void* V, i
     return VLOC_OK;
 }
 
+// ---- the two halves of the chain on their own, and the charge density
+int vloc_to_real(vloc_plan p, const void* c, int64_t nb, void* psi, void* stream) {
+    if (!p || nb < 0) return VLOC_ERR_ARG;
+    if ((p->flags & VLOC_HOST_ONLY) || p->gamma) return VLOC_ERR_STATE;
+    if (nb == 0) return VLOC_OK;
+    if (!c || !psi || !aligned(c, p->elem) || !aligned(psi, p->elem)) return VLOC_ERR_ARG;
+    const size_t bstride = (size_t)p->npw * p->elem, gstride = (size_t)p->N * p->elem;
+    if (overlap(c, nb * bstride, psi, nb * gstride)) return VLOC_ERR_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    const int dbl = p->dbl;
+    const DevTables& t = p->dt;
+    const LaunchAxes& ax = p->ax;
+    for (int64_t b0 = 0; b0 < nb; b0 += p->chunk) {
+        const long long cb = std::min<long long>(p->chunk, nb - b0);
+        const void* cc = (const char*)c + b0 * bstride;
+        void* gg = (char*)psi + b0 * gstride;
+        int rc;
+        if ((rc = launch(p, KK_SCATTER_Z, st, [&] { return launch_k1_scatter_zpass(dbl, p->fast, t, ax, p->d_tw[2], cc, cb, p->d_cyl, st); }))) return rc;
+        if ((rc = launch(p, KK_Y_INV, st, [&] { return launch_k2_ypass(dbl, p->fast, +1, t, ax, p->d_tw[1], cb, p->d_cyl, p->d_slab, st); }))) return rc;
+        if ((rc = launch(p, KK_X_TO_GRID, st, [&] { return launch_k3_grid(dbl, p->fast, +1, t, ax, p->d_tw[0], cb, p->d_slab, gg, st); }))) return rc;
+    }
+    return VLOC_OK;
+}
+
+int vloc_to_recip(vloc_plan p, const void* u, int64_t nb, void* out, void* stream) {
+    if (!p || nb < 0) return VLOC_ERR_ARG;
+    if ((p->flags & VLOC_HOST_ONLY) || p->gamma) return VLOC_ERR_STATE;
+    if (nb == 0) return VLOC_OK;
+    if (!u || !out || !aligned(u, p->elem) || !aligned(out, p->elem)) return VLOC_ERR_ARG;
+    const size_t bstride = (size_t)p->npw * p->elem, gstride = (size_t)p->N * p->elem;
+    if (overlap(u, nb * gstride, out, nb * bstride)) return VLOC_ERR_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    const int dbl = p->dbl;
+    const DevTables& t = p->dt;
+    const LaunchAxes& ax = p->ax;
+    for (int64_t b0 = 0; b0 < nb; b0 += p->chunk) {
+        const long long cb = std::min<long long>(p->chunk, nb - b0);
+        void* gg = (char*)const_cast<void*>(u) + b0 * gstride;
+        void* oo = (char*)out + b0 * bstride;
+        int rc;
+        if ((rc = launch(p, KK_X_FROM_GRID, st, [&] { return launch_k3_grid(dbl, p->fast, -1, t, ax, p->d_tw[0], cb, p->d_slab, gg, st); }))) return rc;
+        if ((rc = launch(p, KK_Y_FWD, st, [&] { return launch_k2_ypass(dbl, p->fast, -1, t, ax, p->d_tw[1], cb, p->d_cyl, p->d_slab, st); }))) return rc;
+        if ((rc = launch(p, KK_Z_GATHER, st, [&] { return launch_k4_zpass_gather(dbl, p->fast, t, ax, p->d_tw[2], p->d_cyl, cb, oo, st); }))) return rc;
+    }
+    return VLOC_OK;
+}
+
+int vloc_density(vloc_plan p, const void* c, const void* occ, int64_t nb, void* rho, void* stream) {
+    if (!p || nb < 0 || !rho) return VLOC_ERR_ARG;
+    if (p->flags & VLOC_HOST_ONLY) return VLOC_ERR_STATE;
+    const size_t re = p->dbl ? 8 : 4;
+    const size_t ustride = (size_t)p->npw_user * p->elem;
+    if (!aligned(rho, re) || (occ && !aligned(occ, re))) return VLOC_ERR_ARG;
+    if (nb > 0 && (!c || !aligned(c, p->elem))) return VLOC_ERR_ARG;
+    if (nb > 0 && overlap(rho, (size_t)p->N * re, c, nb * ustride)) return VLOC_ERR_ARG;
+    if (nb > 0 && occ && overlap(rho, (size_t)p->N * re, occ, nb * re)) return VLOC_ERR_ARG;
+    if (density_smem_bytes(p->dbl, p->n1) > (size_t)p->smem_optin) return VLOC_ERR_SIZE;
+    cudaStream_t st = (cudaStream_t)stream;
+    const int dbl = p->dbl;
+    const DevTables& t = p->dt;
+    const LaunchAxes& ax = p->ax;
+    int rc;
+    if ((rc = launch(p, KK_AUX, st, [&] { return launch_zero_f64(p->d_acc, p->N, st); }))) return rc;
+    const size_t slab_band = (size_t)p->NP * p->n2 * p->n3 * p->elem;
+    const long long per_pass = (long long)p->ngroups * kGradBandsPerGroup;  // bands per density x-pass
+    double* partial = p->d_acc + p->N;
+    // K1 + K2 on `cb` complex bands at `src` (stride npw), then the density
+    // x-pass; `base` is the global index of the chunk's first (pair) band.
+    auto chunk_density = [&](const void* src, long long cb, long long base, int pair) -> int {
+        int r;
+        if ((r = launch(p, KK_SCATTER_Z, st, [&] { return launch_k1_scatter_zpass(dbl, p->fast, t, ax, p->d_tw[2], src, cb, p->d_cyl, st); }))) return r;
+        if ((r = launch(p, KK_Y_INV, st, [&] { return launch_k2_ypass(dbl, p->fast, +1, t, ax, p->d_tw[1], cb, p->d_cyl, p->d_slab, st); }))) return r;
+        for (long long j0 = 0; j0 < cb; j0 += per_pass) {
+            const long long m = std::min(per_pass, cb - j0);
+            int used = 1;
+            const void* sl = (const char*)p->d_slab + j0 * slab_band;
+            if ((r = launch(p, KK_DENSITY, st, [&] {
+                     return launch_k3d_density(dbl, p->fast, t, ax, p->d_tw[0], sl, m, (int)kGradBandsPerGroup, occ,
+                                               base + j0, pair, nb, partial, &used, st);
+                 })))
+                return r;
+            if ((r = launch(p, KK_AUX, st, [&] { return launch_reduce_partials(partial, used, p->N, p->d_acc, st); }))) return r;
+        }
+        return VLOC_OK;
+    };
+    if (!p->gamma) {
+        for (int64_t b0 = 0; b0 < nb; b0 += p->chunk) {
+            const long long cb = std::min<long long>(p->chunk, nb - b0);
+            if ((rc = chunk_density((const char*)c + b0 * ustride, cb, b0, 0))) return rc;
+        }
+    } else {
+        // Gamma-point pairs: psi_2p + i psi_2p+1, both real, so |.|^2 splits
+        // into the two bands' squares on the real and imaginary parts
+        const long long npairs = (nb + 1) / 2;
+        for (long long p0 = 0; p0 < npairs; p0 += p->chunk) {
+            const long long cp = std::min<long long>(p->chunk, npairs - p0);
+            const long long bn = std::min<long long>(nb - 2 * p0, 2 * cp);
+            if ((rc = launch(p, KK_GAMMA, st, [&] {
+                     return launch_gamma_pack(dbl, (const char*)c + 2 * p0 * ustride, bn, p->npw_user, p->d_gamma_neg,
+                                              p->npw, p->d_gamma_buf, cp, st);
+                 })))
+                return rc;
+            if ((rc = chunk_density(p->d_gamma_buf, cp, p0, 1))) return rc;
+        }
+    }
+    return launch(p, KK_AUX, st, [&] { return launch_finish_grad_v(dbl, p->d_acc, rho, p->N, st); });
+}
+
 int vloc_apply_batched(int ninst, const vloc_plan* plans, const void* const* c, const void* const* V,
                        const int64_t* nb, void* const* out, void* stream) {
     if (ninst < 0 || (ninst > 0 && (!plans || !c || !V || !nb || !out))) return VLOC_ERR_ARG;

@@ -42,11 +42,12 @@ EXPORTS = [
     "vloc_apply_batched", "vloc_apply_host", "vloc_get_index_map", "vloc_get_partition",
     "vloc_get_info", "vloc_strerror", "vloc_version", "vloc_last_cuda_error",
     "vloc_profile", "vloc_get_profile", "vloc_get_launch_count", "vloc_apply_noalloc",
-    "vloc_plan_set_schedule",
+    "vloc_plan_set_schedule", "vloc_to_real", "vloc_to_recip", "vloc_density",
 ]
 
 KERNEL_NAMES = ["k1_scatter_zpass", "k2_ypass_inv", "k3_xpass_v", "k2_ypass_fwd", "k4_zpass_gather",
-                "k3b_grad_v", "aux", "gamma_pack_unpack"]
+                "k3b_grad_v", "aux", "gamma_pack_unpack", "k3_to_grid", "k3_from_grid", "k3d_density",
+                "unused"]
 
 
 class VlocKernelStat(ctypes.Structure):
@@ -108,6 +109,9 @@ def load(path: str | None = None) -> ctypes.CDLL:
         lib.vloc_plan_set_schedule.argtypes = [vp, c_int, c_int, ctypes.POINTER(i32)]
         lib.vloc_get_profile.argtypes = [vp, ctypes.POINTER(VlocKernelStat)]
         lib.vloc_get_launch_count.argtypes = [vp, ctypes.POINTER(i64)]
+        lib.vloc_to_real.argtypes = [vp, vp, i64, vp, vp]
+        lib.vloc_to_recip.argtypes = [vp, vp, i64, vp, vp]
+        lib.vloc_density.argtypes = [vp, vp, vp, i64, vp, vp]
         for name in EXPORTS:
             getattr(lib, name)
         _lib = lib
@@ -227,9 +231,9 @@ class VlocPlan:
         _check(self.lib.vloc_profile(self.handle, int(enable)), "vloc_profile")
 
     def get_profile(self) -> dict:
-        arr = (VlocKernelStat * 8)()
+        arr = (VlocKernelStat * len(KERNEL_NAMES))()
         _check(self.lib.vloc_get_profile(self.handle, arr), "vloc_get_profile")
-        return {KERNEL_NAMES[i]: (int(arr[i].launches), float(arr[i].total_ms)) for i in range(8) if arr[i].launches}
+        return {KERNEL_NAMES[i]: (int(arr[i].launches), float(arr[i].total_ms)) for i in range(len(KERNEL_NAMES)) if arr[i].launches}
 
     def launch_count(self) -> int:
         n = ctypes.c_int64()
@@ -291,6 +295,47 @@ class VlocPlan:
                                       _ptr(gc) if gc is not None else None,
                                       _ptr(gV) if gV is not None else None, _stream_ptr(stream)), "vloc_backward")
         return gc, gV
+
+    def to_real(self, c, psi=None, *, stream=None):
+        """psi_n = F+ S c_n on the full grid: [nb, n1, n2, n3] complex."""
+        import torch
+        self._check_c(c)
+        nb = c.numel() // self.npw
+        if psi is None:
+            psi = torch.empty((nb, *self.grid), dtype=self.dtype, device=c.device)
+        elif not psi.is_cuda or psi.dtype != self.dtype or not psi.is_contiguous() or \
+                psi.numel() != nb * int(np.prod(self.grid)):
+            raise ValueError("psi must be a contiguous CUDA tensor of nb full grids")
+        _check(self.lib.vloc_to_real(self.handle, _ptr(c), nb, _ptr(psi), _stream_ptr(stream)), "vloc_to_real")
+        return psi
+
+    def to_recip(self, u, out=None, *, stream=None):
+        """out_n(G) = (1/N) sum_r u_n(r) exp(-2 pi i G.r/n) for full grids u [nb, n1, n2, n3]."""
+        import torch
+        N = int(np.prod(self.grid))
+        if not u.is_cuda or u.dtype != self.dtype or not u.is_contiguous() or u.numel() % N:
+            raise ValueError("u must be a contiguous CUDA tensor of full grids")
+        nb = u.numel() // N
+        if out is None:
+            out = torch.empty((nb, self.npw), dtype=self.dtype, device=u.device)
+        else:
+            self._check_c(out, "out")
+        _check(self.lib.vloc_to_recip(self.handle, _ptr(u), nb, _ptr(out), _stream_ptr(stream)), "vloc_to_recip")
+        return out
+
+    def density(self, c, occ=None, rho=None, *, stream=None):
+        """rho(r) = sum_n f_n |psi_n(r)|^2 (f_n = occ[n], 1 when None): real [n1, n2, n3]."""
+        import torch
+        self._check_c(c)
+        nb = c.numel() // self.npw
+        if occ is not None and (not occ.is_cuda or occ.dtype != self.real_dtype or not occ.is_contiguous()
+                                or occ.numel() != nb):
+            raise ValueError(f"occ must be a contiguous CUDA {self.real_dtype} tensor of nb weights")
+        if rho is None:
+            rho = torch.empty(self.grid, dtype=self.real_dtype, device=c.device)
+        _check(self.lib.vloc_density(self.handle, _ptr(c), _ptr(occ) if occ is not None else None, nb, _ptr(rho),
+                                     _stream_ptr(stream)), "vloc_density")
+        return rho
 
     def apply_host(self, c_host, V_host, out_host=None, *, stream=None):
         """A c with host (CPU, preferably pinned) tensors; copies inside the call."""
