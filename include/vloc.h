@@ -155,6 +155,18 @@ int vloc_plan_destroy(vloc_plan plan);
 int vloc_apply(vloc_plan plan, const void* coeffs, const void* V, int64_t nbands, void* out,
                void* stream);
 
+/*
+ * vloc_apply_h -- out = (diag(d) + A) c: the local-potential action plus a
+ * term diagonal in G, added in the gather of the last kernel (for a
+ * Kohn-Sham Hamiltonian d(G) = |k + G|^2 / 2, the kinetic energy, Eq. 1).
+ *   diag : device real [npw] (plan precision), in the caller's G order; NULL
+ *          gives vloc_apply.  Must not overlap out.
+ * Other arguments, aliasing and errors as vloc_apply (Gamma-point plans
+ * included: d is given on the half list).
+ */
+int vloc_apply_h(vloc_plan plan, const void* coeffs, const void* V, const void* diag, int64_t nbands,
+                 void* out, void* stream);
+
 /* vloc_apply_adjoint -- out = A^H c.  With real V the operator is Hermitian
  * (A^H = A), so this is the same action; it is a separate entry so that the
  * operator contract used by the backward pass is explicit.  Arguments and

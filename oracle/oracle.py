@@ -27,6 +27,12 @@ it follows:
   1/N, gather) with its brute force ``bf_to_recip``; ``density`` /
   ``gamma_density``: rho(r) = sum_n f_n |psi_n(r)|^2 (Sec. 3.1, first
   paragraph), from ``to_real``.
+* ``kinetic`` / ``dense_h`` / ``lowest_eigs``: the Kohn-Sham Hamiltonian of
+  Eq. 1 at the Gamma point with a local potential only, H = |G|^2 / 2 + V_loc,
+  as a dense matrix whose columns are ``apply`` on unit vectors plus the
+  kinetic diagonal, and its lowest eigenvalues by numpy's dense solver (the
+  reference for the iterative eigensolver, Sec. 2: H is applied, never
+  assembled, in production).
 * ``sticks`` / ``greedy_partition`` (Sec. 3.2, Fig. 2), ``basic_partition``
   (Sec. 4.1, Fig. 3-4) and ``improved_partition`` (Sec. 4.2).
 
@@ -351,6 +357,27 @@ def gamma_density(n, g_half, c_half, occ=None, nthreads: int = 0) -> np.ndarray:
     """Density of real bands given on half of the sphere (Sec. 4.3): complete, then ``density``."""
     g_full, c_full = gamma_complete(g_half, c_half)
     return density(n, g_full, c_full, occ, nthreads)
+
+
+def kinetic(g, cell) -> np.ndarray:
+    """|G|^2 / 2 with G = 2 pi (h / L1, k / L2, l / L3) for an orthorhombic
+    cell of side lengths ``cell`` (Eq. 1's kinetic term at k = 0)."""
+    gg = 2.0 * np.pi * np.asarray(g, dtype=np.float64) / np.asarray(cell, dtype=np.float64)[None, :]
+    return 0.5 * (gg ** 2).sum(axis=1)
+
+
+def dense_h(n, g, V, T, nthreads: int = 0) -> np.ndarray:
+    """H[:, j] = T_j e_j + A e_j over the plane-wave basis (complex128 [npw, npw])."""
+    npw = len(np.asarray(g).reshape(-1, 3))
+    cols = apply(n, g, np.eye(npw, dtype=np.complex128), V, nthreads)   # row j = A e_j
+    H = cols.T.copy()
+    H[np.arange(npw), np.arange(npw)] += np.asarray(T, dtype=np.float64)
+    return H
+
+
+def lowest_eigs(n, g, V, T, k: int, nthreads: int = 0) -> np.ndarray:
+    """The k lowest eigenvalues of ``dense_h`` (numpy's Hermitian solver)."""
+    return np.linalg.eigvalsh(dense_h(n, g, V, T, nthreads))[:k]
 
 
 def sticks(n, g):

@@ -53,8 +53,10 @@ template <typename T> struct Launch {
                   void* slab, cudaStream_t st);
     static int k3(const DevTables& t, const LaunchAxes& ax, const void* tw1, const void* V, long long nb, void* slab,
                   cudaStream_t st);
+    // out = (1/N) gather + diag * cin (diag, cin: null, or [npw] real and the
+    // chunk's coefficients [nb][npw])
     static int k4(const DevTables& t, const LaunchAxes& ax, const void* tw3, const void* cyl, long long nb, void* out,
-                  cudaStream_t st);
+                  const void* diag, const void* cin, cudaStream_t st);
     static int k3b(const DevTables& t, const LaunchAxes& ax, const void* tw1, const void* sc, const void* sg,
                    long long nb, int ngroups, double* partial, cudaStream_t st);
     static int finish_grad(const double* acc, void* g, long long N, cudaStream_t st);
@@ -76,7 +78,8 @@ template <typename T, int N> struct LaunchCT {
     static int k1(const DevTables& t, const void* tw3, const void* coeffs, long long nb, void* cyl, cudaStream_t st);
     static int k2(int sign, const DevTables& t, const void* tw2, long long nb, void* cyl, void* slab, cudaStream_t st);
     static int k3(const DevTables& t, const void* tw1, const void* V, long long nb, void* slab, cudaStream_t st);
-    static int k4(const DevTables& t, const void* tw3, const void* cyl, long long nb, void* out, cudaStream_t st);
+    static int k4(const DevTables& t, const void* tw3, const void* cyl, long long nb, void* out, const void* diag,
+                  const void* cin, cudaStream_t st);
     static int k3b(const DevTables& t, const void* tw1, const void* sc, const void* sg, long long nb, int bpg,
                    double* partial, cudaStream_t st);
     static int k3g(int sign, const DevTables& t, const void* tw1, long long nb, void* slab, void* grid, cudaStream_t st);
@@ -94,7 +97,7 @@ int launch_k2_ypass(int dbl, int fast, int sign, const DevTables& t, const Launc
 int launch_k3_xpass_v(int dbl, int fast, const DevTables& t, const LaunchAxes& ax, const void* tw1, const void* V,
                       long long nb, void* slab, cudaStream_t st);
 int launch_k4_zpass_gather(int dbl, int fast, const DevTables& t, const LaunchAxes& ax, const void* tw3, const void* cyl,
-                           long long nb, void* out, cudaStream_t st);
+                           long long nb, void* out, const void* diag, const void* cin, cudaStream_t st);
 // dL/dV x-pass over nb bands in groups of at most `bpg` bands; each group's
 // partial sum goes to partial[group][N]; launch_reduce_partials then adds the
 // groups (in order) into acc.  Returns the groups used via *used.
@@ -119,7 +122,7 @@ int launch_finish_grad_v(int dbl, const double* acc, void* gradV, long long N, c
 int launch_gamma_pack(int dbl, const void* c, long long nb, long long nh, const int* neg, long long nfull, void* C,
                       long long np, cudaStream_t st);
 int launch_gamma_unpack(int dbl, const void* U, long long np, long long nfull, const int* neg, long long nh,
-                        void* out, long long nb, cudaStream_t st);
+                        void* out, long long nb, const void* diag, const void* c, cudaStream_t st);
 int launch_zero_f64(double* p, long long n, cudaStream_t st);
 size_t smem_bytes_for(int dbl, int n);
 size_t grad_smem_bytes(int dbl, int n);

@@ -40,9 +40,9 @@ __global__ void k_gamma_pack(const V* __restrict__ c, long long nb, long long nh
     row[q] = u;
     row[n] = w;
 }
-template <typename V>
+template <typename V, typename T>
 __global__ void k_gamma_unpack(const V* __restrict__ U, long long nfull, const int* __restrict__ neg, long long nh,
-                               V* __restrict__ out, long long nb) {
+                               V* out, long long nb, const T* __restrict__ diag, const V* c) {
     const long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     const long long p = blockIdx.y;
     if (q >= nh) return;
@@ -51,8 +51,18 @@ __global__ void k_gamma_unpack(const V* __restrict__ U, long long nfull, const i
     V a, b;
     a.x = (x.x + y.x) * 0.5f; a.y = (x.y - y.y) * 0.5f;   // (U(G) + conj U(-G)) / 2
     b.x = (x.y + y.y) * 0.5f; b.y = (y.x - x.x) * 0.5f;   // (U(G) - conj U(-G)) / 2i
+    const bool has_b = 2 * p + 1 < nb;
+    if (diag) {  // H = diag + A; c is read before out is written (they may alias)
+        const T d = diag[q];
+        const V ca = c[(2 * p) * nh + q];
+        a.x += d * ca.x; a.y += d * ca.y;
+        if (has_b) {
+            const V cb = c[(2 * p + 1) * nh + q];
+            b.x += d * cb.x; b.y += d * cb.y;
+        }
+    }
     out[(2 * p) * nh + q] = a;
-    if (2 * p + 1 < nb) out[(2 * p + 1) * nh + q] = b;
+    if (has_b) out[(2 * p + 1) * nh + q] = b;
 }
 int launch_gamma_pack(int dbl, const void* c, long long nb, long long nh, const int* neg, long long nfull, void* C,
                       long long np, cudaStream_t st) {
@@ -62,10 +72,14 @@ int launch_gamma_pack(int dbl, const void* c, long long nb, long long nh, const 
     return (int)cudaGetLastError();
 }
 int launch_gamma_unpack(int dbl, const void* U, long long np, long long nfull, const int* neg, long long nh,
-                        void* out, long long nb, cudaStream_t st) {
+                        void* out, long long nb, const void* diag, const void* c, cudaStream_t st) {
     const dim3 grid((unsigned)((nh + 255) / 256), (unsigned)np);
-    if (dbl) k_gamma_unpack<double2><<<grid, 256, 0, st>>>((const double2*)U, nfull, neg, nh, (double2*)out, nb);
-    else k_gamma_unpack<float2><<<grid, 256, 0, st>>>((const float2*)U, nfull, neg, nh, (float2*)out, nb);
+    if (dbl)
+        k_gamma_unpack<double2, double><<<grid, 256, 0, st>>>((const double2*)U, nfull, neg, nh, (double2*)out, nb,
+                                                              (const double*)diag, (const double2*)c);
+    else
+        k_gamma_unpack<float2, float><<<grid, 256, 0, st>>>((const float2*)U, nfull, neg, nh, (float2*)out, nb,
+                                                            (const float*)diag, (const float2*)c);
     return (int)cudaGetLastError();
 }
 
@@ -136,14 +150,16 @@ int launch_k3_xpass_v(int dbl, int fast, const DevTables& t, const LaunchAxes& a
     return dbl ? Launch<double>::k3(t, ax, tw1, V, nb, slab, st) : Launch<float>::k3(t, ax, tw1, V, nb, slab, st);
 }
 int launch_k4_zpass_gather(int dbl, int fast, const DevTables& t, const LaunchAxes& ax, const void* tw3,
-                           const void* cyl, long long nb, void* out, cudaStream_t st) {
+                           const void* cyl, long long nb, void* out, const void* diag, const void* cin,
+                           cudaStream_t st) {
     if (!dbl && fast) switch (t.n3) {
-#define VLOC_CASE(N) case N: return LaunchCT<float, N>::k4(t, tw3, cyl, nb, out, st);
+#define VLOC_CASE(N) case N: return LaunchCT<float, N>::k4(t, tw3, cyl, nb, out, diag, cin, st);
         VLOC_CT_SIZES(VLOC_CASE)
 #undef VLOC_CASE
         default: break;
     }
-    return dbl ? Launch<double>::k4(t, ax, tw3, cyl, nb, out, st) : Launch<float>::k4(t, ax, tw3, cyl, nb, out, st);
+    return dbl ? Launch<double>::k4(t, ax, tw3, cyl, nb, out, diag, cin, st)
+               : Launch<float>::k4(t, ax, tw3, cyl, nb, out, diag, cin, st);
 }
 int launch_k3b_grad_v(int dbl, int fast, const DevTables& t, const LaunchAxes& ax, const void* tw1, const void* slab_c,
                       const void* slab_g, long long nb, int bpg, double* partial, int* used, cudaStream_t st) {

@@ -44,7 +44,8 @@ __device__ __forceinline__ void scatter_entries_p(const int2* __restrict__ ent, 
     }
 }
 __device__ __forceinline__ void gather_entries_p(const int2* __restrict__ ent, int e0, int e1, const float2* buf,
-                                                 float2* __restrict__ o, float scale) {
+                                                 float2* o, float scale, const float* __restrict__ diag,
+                                                 const float2* cin) {
     for (int base = e0 + (int)threadIdx.x; base < e1; base += kBatch * kThreads) {
         int2 en[kBatch];
 #pragma unroll
@@ -52,9 +53,23 @@ __device__ __forceinline__ void gather_entries_p(const int2* __restrict__ ent, i
             const int e = base + u * kThreads;
             en[u] = e < e1 ? ent[e] : make_int2(0, -1);
         }
+        if (diag) {  // H = diag + A (c is read before out is written: they may alias)
+            float d[kBatch];
+            float2 ci[kBatch];
 #pragma unroll
-        for (int u = 0; u < kBatch; ++u)
-            if (en[u].y >= 0) o[en[u].x] = cscale(buf[(en[u].y & 0xffff) * kLdP + (en[u].y >> 16)], scale);
+            for (int u = 0; u < kBatch; ++u)
+                if (en[u].y >= 0) { d[u] = diag[en[u].x]; ci[u] = cin[en[u].x]; }
+#pragma unroll
+            for (int u = 0; u < kBatch; ++u)
+                if (en[u].y >= 0) {
+                    const float2 v = cscale(buf[(en[u].y & 0xffff) * kLdP + (en[u].y >> 16)], scale);
+                    o[en[u].x] = make_float2(v.x + d[u] * ci[u].x, v.y + d[u] * ci[u].y);
+                }
+        } else {
+#pragma unroll
+            for (int u = 0; u < kBatch; ++u)
+                if (en[u].y >= 0) o[en[u].x] = cscale(buf[(en[u].y & 0xffff) * kLdP + (en[u].y >> 16)], scale);
+        }
     }
 }
 template <int NN>
@@ -251,7 +266,8 @@ __global__ void __launch_bounds__(kThreads) k3_ct(DevTables t, const float2* __r
 // ------------------------------------------------------------------ K4
 template <int N>
 __global__ void __launch_bounds__(kThreads) k4_ct(DevTables t, const float2* __restrict__ tw3,
-                                                 const float2* __restrict__ cyl, float2* __restrict__ out, float scale) {
+                                                 const float2* __restrict__ cyl, float2* out, float scale,
+                                                 const float* __restrict__ diag, const float2* cin) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float2* buf = reinterpret_cast<float2*>(smem_raw);
     float2* stw = buf + N * kLdP;
@@ -264,7 +280,8 @@ __global__ void __launch_bounds__(kThreads) k4_ct(DevTables t, const float2* __r
     fft_ct<N, -1, kWarps, false, true, true>(stw, SmemP{buf}, SmemP{buf}, buf, slot_of(), sub_of(), warp_of(),
                                              2 * slot_of() < lines);
     __syncthreads();
-    gather_entries_p(t.tile_pw, t.tile_pw_ptr[tile], t.tile_pw_ptr[tile + 1], buf, out + b * t.npw, scale);
+    gather_entries_p(t.tile_pw, t.tile_pw_ptr[tile], t.tile_pw_ptr[tile + 1], buf, out + b * t.npw, scale, diag,
+                     diag ? cin + b * t.npw : cin);
 }
 
 // ----------------------------------------------------------------- K3b
@@ -559,12 +576,13 @@ int LaunchCT<T, N>::k3d(const DevTables& t, const void* tw1, const void* slab, l
 }
 template <typename T, int N>
 int LaunchCT<T, N>::k4(const DevTables& t, const void* tw3, const void* cyl, long long nb, void* out,
-                       cudaStream_t st) {
+                       const void* diag, const void* cin, cudaStream_t st) {
     static const cudaError_t once = CtSmem<N>::ensure(k4_ct<N>);
     if (once) return (int)once;
     const float scale = (float)(1.0 / ((double)t.n1 * t.n2 * t.n3));
     k4_ct<N><<<dim3(t.T, (unsigned)nb), kThreads, CtSmem<N>::sm, st>>>(t, (const float2*)tw3, (const float2*)cyl,
-                                                                       (float2*)out, scale);
+                                                                       (float2*)out, scale, (const float*)diag,
+                                                                       (const float2*)cin);
     return (int)cudaGetLastError();
 }
 

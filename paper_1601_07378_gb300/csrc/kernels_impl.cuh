@@ -67,10 +67,16 @@ __device__ __forceinline__ void scatter_entries(const int2* __restrict__ ent, in
 
 template <typename V, typename T>
 __device__ __forceinline__ void gather_entries(const int2* __restrict__ ent, int e0, int e1, const V* buf,
-                                               V* __restrict__ o, T scale) {
+                                               V* o, T scale, const T* __restrict__ diag, const V* cin) {
     for (int e = e0 + (int)threadIdx.x; e < e1; e += kThreads) {
         const int2 en = ent[e];
-        o[en.x] = cscale(buf[(en.y & 0xffff) * kLd + (en.y >> 16)], scale);
+        V v = cscale(buf[(en.y & 0xffff) * kLd + (en.y >> 16)], scale);
+        if (diag) {  // H = diag + A: add the diagonal term (read before the write: out may alias c)
+            const T d = diag[en.x];
+            const V ci = cin[en.x];
+            v = cmk<V>(v.x + d * ci.x, v.y + d * ci.y);
+        }
+        o[en.x] = v;
     }
 }
 
@@ -230,8 +236,8 @@ __global__ void __launch_bounds__(kThreads) k3_xpass_v(DevTables t, AxisPlan ax,
 // ------------------------------------------------------------------ K4
 template <typename T>
 __global__ void __launch_bounds__(kThreads) k4_zpass_gather(DevTables t, AxisPlan az, const V2<T>* __restrict__ tw3,
-                                                           const V2<T>* __restrict__ cyl, V2<T>* __restrict__ out,
-                                                           T scale) {
+                                                           const V2<T>* __restrict__ cyl, V2<T>* out, T scale,
+                                                           const T* __restrict__ diag, const V2<T>* cin) {
     using V = V2<T>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int n3 = t.n3;
@@ -247,7 +253,8 @@ __global__ void __launch_bounds__(kThreads) k4_zpass_gather(DevTables t, AxisPla
     V* D = final_buf(az.nst, P, Q);
     fft_lines<-1>(az, stw, Smem<V>{Q}, Smem<V>{D}, P, Q, lines);
     __syncthreads();
-    gather_entries(t.tile_pw, t.tile_pw_ptr[tile], t.tile_pw_ptr[tile + 1], D, out + b * t.npw, scale);
+    gather_entries(t.tile_pw, t.tile_pw_ptr[tile], t.tile_pw_ptr[tile + 1], D, out + b * t.npw, scale, diag,
+                   diag ? cin + b * t.npw : cin);
 }
 
 // ----------------------------------------------------------- K3b (dL/dV)
@@ -479,10 +486,10 @@ int Launch<T>::k3(const DevTables& t, const LaunchAxes& ax, const void* tw1, con
 }
 template <typename T>
 int Launch<T>::k4(const DevTables& t, const LaunchAxes& ax, const void* tw3, const void* cyl, long long nb, void* out,
-                  cudaStream_t st) {
+                  const void* diag, const void* cin, cudaStream_t st) {
     const T scale = (T)(1.0 / ((double)t.n1 * t.n2 * t.n3));
     k4_zpass_gather<T><<<dim3(t.T, (unsigned)nb), kThreads, smem(t.n3), st>>>(
-        t, axis_of(ax, 2), (const V2<T>*)tw3, (const V2<T>*)cyl, (V2<T>*)out, scale);
+        t, axis_of(ax, 2), (const V2<T>*)tw3, (const V2<T>*)cyl, (V2<T>*)out, scale, (const T*)diag, (const V2<T>*)cin);
     return (int)cudaGetLastError();
 }
 template <typename T>

@@ -123,7 +123,7 @@ extern "C" int vloc_apply_noalloc(vloc_plan plan, const void* coeffs, const void
         if (launch_k2_ypass(dbl, 1, +1, t, ax, tw[1], cb, cyl, slab, st)) return VLOC_ERR_CUDA;
         if (launch_k3_xpass_v(dbl, 1, t, ax, tw[0], V, cb, slab, st)) return VLOC_ERR_CUDA;
         if (launch_k2_ypass(dbl, 1, -1, t, ax, tw[1], cb, cyl, slab, st)) return VLOC_ERR_CUDA;
-        if (launch_k4_zpass_gather(dbl, 1, t, ax, tw[2], cyl, cb, oo, st)) return VLOC_ERR_CUDA;
+        if (launch_k4_zpass_gather(dbl, 1, t, ax, tw[2], cyl, cb, oo, nullptr, nullptr, st)) return VLOC_ERR_CUDA;
     }
     return VLOC_OK;
 }

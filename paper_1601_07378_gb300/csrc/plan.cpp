@@ -528,7 +528,9 @@ static int launch(vloc_plan p, int kind, cudaStream_t st, F&& f) {
 extern "C" {
 
 // out = A c over workspace chunks: K1, K2(+), K3, K2(-), K4 per chunk.
-static int apply_impl(vloc_plan p, const void* c, const void* V, int64_t nb, void* out, cudaStream_t st) {
+// With `diag` (device real [npw]) the gather adds diag * c: out = (diag + A) c.
+static int apply_impl(vloc_plan p, const void* c, const void* V, int64_t nb, void* out, cudaStream_t st,
+                      const void* diag = nullptr) {
     const size_t bstride = (size_t)p->npw * p->elem;
     const int dbl = p->dbl;
     const DevTables& t = p->dt;
@@ -542,7 +544,7 @@ static int apply_impl(vloc_plan p, const void* c, const void* V, int64_t nb, voi
         if ((rc = launch(p, KK_Y_INV, st, [&] { return launch_k2_ypass(dbl, p->fast, +1, t, ax, p->d_tw[1], cb, p->d_cyl, p->d_slab, st); }))) return rc;
         if ((rc = launch(p, KK_X_V, st, [&] { return launch_k3_xpass_v(dbl, p->fast, t, ax, p->d_tw[0], V, cb, p->d_slab, st); }))) return rc;
         if ((rc = launch(p, KK_Y_FWD, st, [&] { return launch_k2_ypass(dbl, p->fast, -1, t, ax, p->d_tw[1], cb, p->d_cyl, p->d_slab, st); }))) return rc;
-        if ((rc = launch(p, KK_Z_GATHER, st, [&] { return launch_k4_zpass_gather(dbl, p->fast, t, ax, p->d_tw[2], p->d_cyl, cb, oo, st); }))) return rc;
+        if ((rc = launch(p, KK_Z_GATHER, st, [&] { return launch_k4_zpass_gather(dbl, p->fast, t, ax, p->d_tw[2], p->d_cyl, cb, oo, diag, cc, st); }))) return rc;
     }
     return VLOC_OK;
 }
@@ -552,7 +554,8 @@ static int apply_impl(vloc_plan p, const void* c, const void* V, int64_t nb, voi
 // Gamma-point real mode: bands 2p and 2p+1 (real in r-space) travel as one
 // complex band a + i b through the chain; each result pair is separated with
 // U(G) and conj U(-G).
-static int gamma_apply(vloc_plan p, const void* c, const void* V, int64_t nb, void* out, cudaStream_t st) {
+static int gamma_apply(vloc_plan p, const void* c, const void* V, int64_t nb, void* out, cudaStream_t st,
+                       const void* diag) {
     const long long npairs = (nb + 1) / 2;
     const size_t full = (size_t)p->npw * p->elem;
     char* C = (char*)p->d_gamma_buf;
@@ -570,15 +573,16 @@ static int gamma_apply(vloc_plan p, const void* c, const void* V, int64_t nb, vo
         if ((rc = apply_impl(p, C, V, cp, U, st))) return rc;
         if ((rc = launch(p, KK_GAMMA, st, [&] {
                  return launch_gamma_unpack(p->dbl, U, cp, p->npw, p->d_gamma_neg, p->npw_user, (char*)out + b0 * ustride,
-                                            bn, st);
+                                            bn, diag, (const char*)c + b0 * ustride, st);
              })))
             return rc;
     }
     return VLOC_OK;
 }
 
-static int apply_any(vloc_plan p, const void* c, const void* V, int64_t nb, void* out, cudaStream_t st) {
-    return p->gamma ? gamma_apply(p, c, V, nb, out, st) : apply_impl(p, c, V, nb, out, st);
+static int apply_any(vloc_plan p, const void* c, const void* V, int64_t nb, void* out, cudaStream_t st,
+                     const void* diag = nullptr) {
+    return p->gamma ? gamma_apply(p, c, V, nb, out, st, diag) : apply_impl(p, c, V, nb, out, st, diag);
 }
 
 // Replay (or capture, then replay) the work `enqueue` puts on a stream as one
@@ -652,6 +656,19 @@ int vloc_apply(vloc_plan p, const void* c, const void* V, int64_t nb, void* out,
         return graph_run(p, {p}, {(uintptr_t)c, (uintptr_t)V, (uintptr_t)nb, (uintptr_t)out}, (cudaStream_t)stream,
                          [&](cudaStream_t cs) { return apply_any(p, c, V, nb, out, cs); });
     return apply_any(p, c, V, nb, out, (cudaStream_t)stream);
+}
+
+int vloc_apply_h(vloc_plan p, const void* c, const void* V, const void* diag, int64_t nb, void* out, void* stream) {
+    int rc = check_io(p, c, V, nb, out);
+    if (rc || nb == 0) return rc;
+    if (!diag) return vloc_apply(p, c, V, nb, out, stream);
+    const size_t re = p->dbl ? 8 : 4;
+    if (!aligned(diag, re)) return VLOC_ERR_ARG;
+    if (overlap(diag, (size_t)p->npw_user * re, out, (size_t)nb * p->npw_user * p->elem)) return VLOC_ERR_ARG;
+    if (p->flags & VLOC_GRAPH)
+        return graph_run(p, {p}, {(uintptr_t)c, (uintptr_t)V, (uintptr_t)nb, (uintptr_t)out, (uintptr_t)diag},
+                         (cudaStream_t)stream, [&](cudaStream_t cs) { return apply_any(p, c, V, nb, out, cs, diag); });
+    return apply_any(p, c, V, nb, out, (cudaStream_t)stream, diag);
 }
 
 int vloc_apply_adjoint(vloc_plan p, const void* c, const void* V, int64_t nb, void* out, void* stream) {
@@ -756,7 +773,7 @@ int vloc_to_recip(vloc_plan p, const void* u, int64_t nb, void* out, void* strea
         int rc;
         if ((rc = launch(p, KK_X_FROM_GRID, st, [&] { return launch_k3_grid(dbl, p->fast, -1, t, ax, p->d_tw[0], cb, p->d_slab, gg, st); }))) return rc;
         if ((rc = launch(p, KK_Y_FWD, st, [&] { return launch_k2_ypass(dbl, p->fast, -1, t, ax, p->d_tw[1], cb, p->d_cyl, p->d_slab, st); }))) return rc;
-        if ((rc = launch(p, KK_Z_GATHER, st, [&] { return launch_k4_zpass_gather(dbl, p->fast, t, ax, p->d_tw[2], p->d_cyl, cb, oo, st); }))) return rc;
+        if ((rc = launch(p, KK_Z_GATHER, st, [&] { return launch_k4_zpass_gather(dbl, p->fast, t, ax, p->d_tw[2], p->d_cyl, cb, oo, nullptr, nullptr, st); }))) return rc;
     }
     return VLOC_OK;
 }

@@ -43,6 +43,7 @@ EXPORTS = [
     "vloc_get_info", "vloc_strerror", "vloc_version", "vloc_last_cuda_error",
     "vloc_profile", "vloc_get_profile", "vloc_get_launch_count", "vloc_apply_noalloc",
     "vloc_plan_set_schedule", "vloc_to_real", "vloc_to_recip", "vloc_density",
+    "vloc_apply_h",
 ]
 
 KERNEL_NAMES = ["k1_scatter_zpass", "k2_ypass_inv", "k3_xpass_v", "k2_ypass_fwd", "k4_zpass_gather",
@@ -109,6 +110,7 @@ def load(path: str | None = None) -> ctypes.CDLL:
         lib.vloc_plan_set_schedule.argtypes = [vp, c_int, c_int, ctypes.POINTER(i32)]
         lib.vloc_get_profile.argtypes = [vp, ctypes.POINTER(VlocKernelStat)]
         lib.vloc_get_launch_count.argtypes = [vp, ctypes.POINTER(i64)]
+        lib.vloc_apply_h.argtypes = [vp, vp, vp, vp, i64, vp, vp]
         lib.vloc_to_real.argtypes = [vp, vp, i64, vp, vp]
         lib.vloc_to_recip.argtypes = [vp, vp, i64, vp, vp]
         lib.vloc_density.argtypes = [vp, vp, vp, i64, vp, vp]
@@ -170,6 +172,7 @@ class VlocPlan:
         self.dtype = dtype
         self.real_dtype = torch.float32 if dtype == torch.complex64 else torch.float64
         g = np.ascontiguousarray(np.asarray(glist, dtype=np.int32).reshape(-1, 3))
+        self.glist = g
         self.npw = len(g)
         flags = VLOC_F32 if dtype == torch.complex64 else VLOC_F64
         flags |= {"greedy": VLOC_PARTITION_GREEDY, "basic": VLOC_PARTITION_BASIC,
@@ -280,6 +283,22 @@ class VlocPlan:
         fn = self.lib.vloc_apply_adjoint if adjoint else self.lib.vloc_apply
         _check(fn(self.handle, _ptr(c), _ptr(V), nb, _ptr(out), _stream_ptr(stream)),
                "vloc_apply_adjoint" if adjoint else "vloc_apply")
+        return out
+
+    def apply_h(self, c, V, diag, out=None, *, stream=None):
+        """out = (diag(d) + A) c: V_loc plus a term diagonal in G (e.g. kinetic |k+G|^2/2)."""
+        import torch
+        self._check_c(c)
+        self._check_V(V)
+        if not diag.is_cuda or diag.dtype != self.real_dtype or not diag.is_contiguous() or diag.numel() != self.npw:
+            raise ValueError(f"diag must be a contiguous CUDA {self.real_dtype} tensor of npw={self.npw} entries")
+        if out is None:
+            out = torch.empty_like(c)
+        else:
+            self._check_c(out, "out")
+        nb = c.numel() // self.npw
+        _check(self.lib.vloc_apply_h(self.handle, _ptr(c), _ptr(V), _ptr(diag), nb, _ptr(out), _stream_ptr(stream)),
+               "vloc_apply_h")
         return out
 
     def backward(self, c, grad_out, V, *, need_c: bool = True, need_V: bool = True, stream=None):

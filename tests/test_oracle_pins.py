@@ -429,3 +429,29 @@ def test_gamma_density_matches_real_bruteforce(n, R):
     f = np.array([1.0, 0.5, 2.0])
     want = (f[:, None] * O.bf_real_psi(n, gh, c) ** 2).sum(0)
     assert _rel(O.gamma_density(n, gh, c, f).ravel(), want) < 1e-12
+
+
+# ---- the Hamiltonian H = |G|^2/2 + V_loc (Eq. 1 at the Gamma point)
+def test_dense_h_free_electrons_and_hermiticity():
+    n = (12, 12, 12)
+    g = synth.sphere_glist(*n, 3.1, order="shuffled", seed=2)
+    T = O.kinetic(g, (10.0, 11.0, 12.0))
+    # constant V = v0: eigenvalues are |G|^2 / 2 + v0 exactly
+    H0 = O.dense_h(n, g, np.full(n, 0.7), T)
+    assert np.allclose(np.linalg.eigvalsh(H0), np.sort(T) + 0.7, rtol=0, atol=1e-12)
+    V, _ = synth.potential(*n, "smooth", seed=4)
+    H = O.dense_h(n, g, V, T)
+    assert np.abs(H - H.conj().T).max() < 1e-14
+    # H applied to a vector = kinetic diagonal + the oracle's action
+    x = synth.coefficients(g, 1, seed=5)[0]
+    assert np.allclose(H @ x, T * x + O.apply(n, g, x, V)[0], rtol=0, atol=1e-13)
+    # first-order perturbation: for a weak potential the lowest level is v(0)
+    eps = 1e-4
+    e = O.lowest_eigs(n, g, 1.0 + eps * (V - V.mean()), T, 1)
+    assert abs(e[0] - 1.0) < 1e-6
+
+
+def test_kinetic_units():
+    g = np.array([[1, 0, 0], [0, 2, 0], [1, 1, 1]])
+    T = O.kinetic(g, (2 * np.pi, 2 * np.pi, 2 * np.pi))
+    assert np.allclose(T, [0.5, 2.0, 1.5])
