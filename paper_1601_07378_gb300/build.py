@@ -1,7 +1,9 @@
 """Build the sm_103a shared library libvloc.so in-tree (no cmake, no pip).
 
-Two translation units are compiled in parallel with nvcc (kernels.cu and
-plan.cpp) and linked into ``paper_1601_07378_gb300/_build/libvloc.so``
+The translation units of ``csrc/`` (the compile-time-length kernels split
+over three files, one per precision for the runtime-radix kernels, the
+dispatch, the plan and the no-alloc entry) are compiled in parallel with
+nvcc and linked into ``paper_1601_07378_gb300/_build/libvloc.so``
 against the shared CUDA runtime, so the library shares the runtime PyTorch
 already loaded.  ``python -m paper_1601_07378_gb300.build`` rebuilds it.
 """

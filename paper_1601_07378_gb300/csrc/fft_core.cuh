@@ -65,6 +65,15 @@ template <int S, typename V> __device__ __forceinline__ V mul_si(V a) {
 }
 template <typename V> __device__ __forceinline__ V czero() { return cmk<V>(0, 0); }
 
+// FP32 complex values are one float2: their componentwise operations (add,
+// subtract, scale by a real) map onto the paired FP32 instructions of
+// sm_100+ (one instruction for both components).  Declared before the DFT
+// templates so that unqualified calls with float2 arguments find them.
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return __fadd2_rn(a, make_float2(-b.x, -b.y)); }
+__device__ __forceinline__ float2 cscale(float2 a, float s) { return __fmul2_rn(a, make_float2(s, s)); }
+__device__ __forceinline__ float2 cfma(float2 a, float s, float2 b) { return __ffma2_rn(make_float2(s, s), b, a); }
+
 // Two FP32 complex values of adjacent lines carried by one lane (one 16-byte
 // vector): every operation applies to both; twiddles are shared.
 struct __align__(16) P2f {

@@ -15,7 +15,27 @@
 #include "fft_ct.cuh"
 #include "kernels_impl.cuh"
 
+// Minimum resident CTAs per SM asked of the compiler (caps a kernel's
+// registers at 65536 / (128 x MINB)).  Measured on GB300 at 96^3: the z- and
+// y-pass kernels gain from more resident CTAs (K1: 6, K2: 6, K4: 7), the
+// x-pass loses (its register-held chain wants the registers).  Applied up to
+// length 96; longer lines keep the compiler's choice (the caps would spill).
+#ifndef VLOC_MINB_K1
+#define VLOC_MINB_K1 6
+#endif
+#ifndef VLOC_MINB_K2
+#define VLOC_MINB_K2 6
+#endif
+#ifndef VLOC_MINB_K3
+#define VLOC_MINB_K3 1
+#endif
+#ifndef VLOC_MINB_K4
+#define VLOC_MINB_K4 7
+#endif
+
 namespace vloc {
+
+constexpr int minb(int n, int m) { return n <= 96 ? m : 1; }
 
 template <int N> __host__ __device__ constexpr size_t ct_smem() {
     return (size_t)N * kLdP * sizeof(float2) + (size_t)N * sizeof(float2) + (size_t)N * sizeof(int) + 16;
@@ -144,7 +164,7 @@ struct XRowsP {  // x rows at fixed y: the occupied planes
 
 // ------------------------------------------------------------------ K1
 template <int N>
-__global__ void __launch_bounds__(kThreads) k1_ct(DevTables t, const float2* __restrict__ tw3,
+__global__ void __launch_bounds__(kThreads, minb(N, VLOC_MINB_K1)) k1_ct(DevTables t, const float2* __restrict__ tw3,
                                                  const float2* __restrict__ coeffs, float2* __restrict__ cyl) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float2* buf = reinterpret_cast<float2*>(smem_raw);
@@ -165,7 +185,7 @@ __global__ void __launch_bounds__(kThreads) k1_ct(DevTables t, const float2* __r
 
 // ------------------------------------------------------------------ K2
 template <int S, int N>
-__global__ void __launch_bounds__(kThreads) k2_ct(DevTables t, const float2* __restrict__ tw2, float2* cyl,
+__global__ void __launch_bounds__(kThreads, minb(N, VLOC_MINB_K2)) k2_ct(DevTables t, const float2* __restrict__ tw2, float2* cyl,
                                                  float2* slab) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int n3 = t.n3;
@@ -190,7 +210,7 @@ __global__ void __launch_bounds__(kThreads) k2_ct(DevTables t, const float2* __r
 
 // ------------------------------------------------------------------ K3
 template <int N>
-__global__ void __launch_bounds__(kThreads) k3_ct(DevTables t, const float2* __restrict__ tw1,
+__global__ void __launch_bounds__(kThreads, minb(N, VLOC_MINB_K3)) k3_ct(DevTables t, const float2* __restrict__ tw1,
                                                  const float* __restrict__ Vr, float2* slab) {
     using SC = Sched<N>;
     constexpr int nst = SC::nst;
@@ -265,7 +285,7 @@ __global__ void __launch_bounds__(kThreads) k3_ct(DevTables t, const float2* __r
 
 // ------------------------------------------------------------------ K4
 template <int N>
-__global__ void __launch_bounds__(kThreads) k4_ct(DevTables t, const float2* __restrict__ tw3,
+__global__ void __launch_bounds__(kThreads, minb(N, VLOC_MINB_K4)) k4_ct(DevTables t, const float2* __restrict__ tw3,
                                                  const float2* __restrict__ cyl, float2* out, float scale,
                                                  const float* __restrict__ diag, const float2* cin) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
