@@ -92,35 +92,37 @@ __device__ __forceinline__ void gather_entries_p(const int2* __restrict__ ent, i
         }
     }
 }
+// Tile rows <-> cylinder: warp w moves lines w, w + 4, ...; lane j moves
+// elements z = j, j + 32, ... of the line (coalesced along the stick, no
+// index division).
 template <int NN>
 __device__ __forceinline__ void rows_out_p(const float2* buf, float2* __restrict__ cb, const int* sticks, int lines) {
-    const int total = lines * NN;
-    for (int i = threadIdx.x; i < total; i += kThreads) {
-        const int l = i / NN, z = i - l * NN;
-        cb[(long long)sticks[l] * NN + z] = buf[z * kLdP + l];
+    constexpr int K = (NN + 31) / 32;
+    const int lane = threadIdx.x & 31;
+    for (int l = threadIdx.x >> 5; l < lines; l += kWarps) {
+        float2* row = cb + (long long)sticks[l] * NN;
+        float2 v[K];
+#pragma unroll
+        for (int k = 0; k < K; ++k)
+            if (NN % 32 == 0 || lane + 32 * k < NN) v[k] = buf[(lane + 32 * k) * kLdP + l];
+#pragma unroll
+        for (int k = 0; k < K; ++k)
+            if (NN % 32 == 0 || lane + 32 * k < NN) row[lane + 32 * k] = v[k];
     }
 }
 template <int NN>
 __device__ __forceinline__ void rows_in_p(float2* buf, const float2* __restrict__ cb, const int* sticks, int lines) {
-    const int total = lines * NN;
-    for (int base = threadIdx.x; base < total; base += kBatch * kThreads) {
-        float2 val[kBatch];
+    constexpr int K = (NN + 31) / 32;
+    const int lane = threadIdx.x & 31;
+    for (int l = threadIdx.x >> 5; l < lines; l += kWarps) {
+        const float2* row = cb + (long long)sticks[l] * NN;
+        float2 v[K];
 #pragma unroll
-        for (int u = 0; u < kBatch; ++u) {
-            const int i = base + u * kThreads;
-            if (i < total) {
-                const int l = i / NN, z = i - l * NN;
-                val[u] = cb[(long long)sticks[l] * NN + z];
-            }
-        }
+        for (int k = 0; k < K; ++k)
+            if (NN % 32 == 0 || lane + 32 * k < NN) v[k] = row[lane + 32 * k];
 #pragma unroll
-        for (int u = 0; u < kBatch; ++u) {
-            const int i = base + u * kThreads;
-            if (i < total) {
-                const int l = i / NN, z = i - l * NN;
-                buf[z * kLdP + l] = val[u];
-            }
-        }
+        for (int k = 0; k < K; ++k)
+            if (NN % 32 == 0 || lane + 32 * k < NN) buf[(lane + 32 * k) * kLdP + l] = v[k];
     }
 }
 
@@ -173,7 +175,8 @@ __global__ void __launch_bounds__(kThreads, minb(N, VLOC_MINB_K1)) k1_ct(DevTabl
     const long long b = blockIdx.y;
     load_tw<float>(stw, tw3, N);
     const int s0 = t.tile_ptr[tile], lines = t.tile_ptr[tile + 1] - s0;
-    for (int i = threadIdx.x; i < N * kLdP; i += kThreads) buf[i] = make_float2(0.f, 0.f);
+    for (int i = threadIdx.x; i < N * kLdP / 2; i += kThreads)
+        reinterpret_cast<float4*>(buf)[i] = make_float4(0.f, 0.f, 0.f, 0.f);
     __syncthreads();
     scatter_entries_p(t.tile_pw, t.tile_pw_ptr[tile], t.tile_pw_ptr[tile + 1], coeffs + b * t.npw, buf);
     __syncthreads();
