@@ -133,27 +133,27 @@ struct CylRowsP {  // rows = the plane's sticks (via rowmap), -1 = absent row
     int n3, z0;
     __device__ __forceinline__ P2f operator()(int e, int slot) const {
         const int s = rowmap[e];
-        return s >= 0 ? *reinterpret_cast<const P2f*>(cb + (long long)s * n3 + z0 + 2 * slot) : czero<P2f>();
+        return s >= 0 ? *reinterpret_cast<const P2f*>(cb + s * n3 + z0 + 2 * slot) : czero<P2f>();
     }
     __device__ __forceinline__ void operator()(int e, int slot, P2f v) const {
         const int s = rowmap[e];
-        if (s >= 0) *reinterpret_cast<P2f*>(cb + (long long)s * n3 + z0 + 2 * slot) = v;
+        if (s >= 0) *reinterpret_cast<P2f*>(cb + s * n3 + z0 + 2 * slot) = v;
     }
 };
 struct SlabRowsP {  // every y row of one plane's tile
     float2* p;       // slab[b][plane][0][z0]
     int n3;
     __device__ __forceinline__ P2f operator()(int e, int slot) const {
-        return *reinterpret_cast<const P2f*>(p + (long long)e * n3 + 2 * slot);
+        return *reinterpret_cast<const P2f*>(p + e * n3 + 2 * slot);
     }
     __device__ __forceinline__ void operator()(int e, int slot, P2f v) const {
-        *reinterpret_cast<P2f*>(p + (long long)e * n3 + 2 * slot) = v;
+        *reinterpret_cast<P2f*>(p + e * n3 + 2 * slot) = v;
     }
 };
 struct XRowsP {  // x rows at fixed y: the occupied planes
     float2* sb;      // slab[b][0][y][z0]
     const int* xrow;
-    long long pstride;
+    int pstride;  // n2 * n3 (in-band offsets stay 32-bit)
     __device__ __forceinline__ P2f operator()(int e, int slot) const {
         const int p = xrow[e];
         return p >= 0 ? *reinterpret_cast<const P2f*>(sb + p * pstride + 2 * slot) : czero<P2f>();
@@ -232,8 +232,8 @@ __global__ void __launch_bounds__(kThreads, minb(N, VLOC_MINB_K3)) k3_ct(DevTabl
     load_tw<float>(stw, tw1, N);
     for (int e = threadIdx.x; e < N; e += kThreads) xrow[e] = t.xrow_plane[e];
     __syncthreads();
-    const long long pstride = (long long)n2 * n3;
-    XRowsP xr{slab + b * t.NP * pstride + (long long)y * n3 + z0, xrow, pstride};
+    const int pstride = n2 * n3;
+    XRowsP xr{slab + b * t.NP * (long long)pstride + y * n3 + z0, xrow, pstride};
     const float* vrow = Vr + (long long)y * n3 + z0 + 2 * slot;
     SmemP sb{buf};
 
@@ -263,7 +263,7 @@ __global__ void __launch_bounds__(kThreads, minb(N, VLOC_MINB_K3)) k3_ct(DevTabl
             if (L::NI % (2 * kWarps) == 0 || i < L::NI) {
 #pragma unroll
                 for (int r = 0; r < R; ++r) {
-                    const float2 w = *reinterpret_cast<const float2*>(vrow + (long long)(i + r * L::NI) * pstride);
+                    const float2 w = *reinterpret_cast<const float2*>(vrow + (i + r * L::NI) * pstride);
                     h[u][r].a = cscale(h[u][r].a, w.x);
                     h[u][r].b = cscale(h[u][r].b, w.y);
                 }
@@ -335,7 +335,7 @@ __global__ void __launch_bounds__(kThreads) k3b_ct(DevTables t, const float2* __
     load_tw<float>(stw, tw1, N);
     for (int e = threadIdx.x; e < N; e += kThreads) xrow[e] = t.xrow_plane[e];
     __syncthreads();
-    const long long pstride = (long long)n2 * n3;
+    const int pstride = n2 * n3;
     using L = NatStage<N, +1, kWarps, nst - 1>;
     constexpr int R = SC::R(nst - 1);
     float2 acc[L::U][R];
@@ -346,8 +346,8 @@ __global__ void __launch_bounds__(kThreads) k3b_ct(DevTables t, const float2* __
     SmemP sa{bufA}, sb{bufB};
     const int b1 = min(nb, (grp + 1) * bpg);
     for (int b = grp * bpg; b < b1; ++b) {
-        XRowsP xc{const_cast<float2*>(slab_c) + (long long)b * t.NP * pstride + (long long)y * n3 + z0, xrow, pstride};
-        XRowsP xg{const_cast<float2*>(slab_g) + (long long)b * t.NP * pstride + (long long)y * n3 + z0, xrow, pstride};
+        XRowsP xc{const_cast<float2*>(slab_c) + (long long)b * t.NP * pstride + y * n3 + z0, xrow, pstride};
+        XRowsP xg{const_cast<float2*>(slab_g) + (long long)b * t.NP * pstride + y * n3 + z0, xrow, pstride};
         fft_ct<N, +1, kWarps, false, false, true>(stw, xc, sa, bufA, slot, sub, warp, act);  // psi -> A
         NatStage<N, +1, kWarps, 0>::template run<false>(stw, xg, sb, slot, sub, warp, act);
         __syncthreads();
@@ -378,14 +378,14 @@ __global__ void __launch_bounds__(kThreads) k3b_ct(DevTables t, const float2* __
         __syncthreads();
     }
     if (act) {
-        double* part = partial + (long long)grp * t.n1 * pstride + (long long)y * n3 + z0 + 2 * slot;
+        double* part = partial + (long long)grp * t.n1 * pstride + y * n3 + z0 + 2 * slot;
 #pragma unroll
         for (int u = 0; u < L::U; ++u) {
             const int i = 2 * (warp + u * kWarps) + sub;
             if (L::NI % (2 * kWarps) == 0 || i < L::NI) {
 #pragma unroll
                 for (int r = 0; r < R; ++r) {
-                    double* q = part + (long long)(i + r * L::NI) * pstride;
+                    double* q = part + (i + r * L::NI) * pstride;
                     q[0] = (double)acc[u][r].x * invN;
                     q[1] = (double)acc[u][r].y * invN;
                 }
@@ -397,7 +397,7 @@ __global__ void __launch_bounds__(kThreads) k3b_ct(DevTables t, const float2* __
 // ------------------------------------------- half transforms and density
 struct GridRowsP {  // x line pair at fixed (y, z0 + 2 slot) of a full grid
     float2* g;      // grid[b][0][y][z0]
-    long long pstride;
+    int pstride;
     __device__ __forceinline__ P2f operator()(int e, int slot) const {
         return *reinterpret_cast<const P2f*>(g + e * pstride + 2 * slot);
     }
@@ -423,9 +423,9 @@ __global__ void __launch_bounds__(kThreads) k3g_ct(DevTables t, const float2* __
     load_tw<float>(stw, tw1, N);
     for (int e = threadIdx.x; e < N; e += kThreads) xrow[e] = t.xrow_plane[e];
     __syncthreads();
-    const long long pstride = (long long)n2 * n3;
-    XRowsP xr{slab + b * t.NP * pstride + (long long)y * n3 + z0, xrow, pstride};
-    GridRowsP gr{grid + b * (long long)N * pstride + (long long)y * n3 + z0, pstride};
+    const int pstride = n2 * n3;
+    XRowsP xr{slab + b * t.NP * (long long)pstride + y * n3 + z0, xrow, pstride};
+    GridRowsP gr{grid + b * (long long)N * pstride + y * n3 + z0, pstride};
     const bool act = 2 * slot_of() < lines;
     if constexpr (S > 0) fft_ct<N, +1, kWarps, false, false, false>(stw, xr, gr, buf, slot_of(), sub_of(), warp_of(), act);
     else fft_ct<N, -1, kWarps, false, false, false>(stw, gr, xr, buf, slot_of(), sub_of(), warp_of(), act);
@@ -456,7 +456,7 @@ __global__ void __launch_bounds__(kThreads) k3d_ct(DevTables t, const float2* __
     load_tw<float>(stw, tw1, N);
     for (int e = threadIdx.x; e < N; e += kThreads) xrow[e] = t.xrow_plane[e];
     __syncthreads();
-    const long long pstride = (long long)n2 * n3;
+    const int pstride = n2 * n3;
     using L = NatStage<N, +1, kWarps, nst - 1>;
     constexpr int R = SC::R(nst - 1);
     float2 acc[L::U][R];
@@ -470,7 +470,7 @@ __global__ void __launch_bounds__(kThreads) k3d_ct(DevTables t, const float2* __
         double wxd, wyd;
         density_weights(occ, b_base + b, pair, nreal, wxd, wyd);
         const float wx = (float)wxd, wy = (float)wyd;
-        XRowsP xc{const_cast<float2*>(slab) + (long long)b * t.NP * pstride + (long long)y * n3 + z0, xrow, pstride};
+        XRowsP xc{const_cast<float2*>(slab) + (long long)b * t.NP * pstride + y * n3 + z0, xrow, pstride};
         NatStage<N, +1, kWarps, 0>::template run<false>(stw, xc, sb, slot, sub, warp, act);
         __syncthreads();
         if constexpr (nst >= 3) {
@@ -499,14 +499,14 @@ __global__ void __launch_bounds__(kThreads) k3d_ct(DevTables t, const float2* __
         __syncthreads();
     }
     if (act) {
-        double* part = partial + (long long)grp * N * pstride + (long long)y * n3 + z0 + 2 * slot;
+        double* part = partial + (long long)grp * N * pstride + y * n3 + z0 + 2 * slot;
 #pragma unroll
         for (int u = 0; u < L::U; ++u) {
             const int i = 2 * (warp + u * kWarps) + sub;
             if (L::NI % (2 * kWarps) == 0 || i < L::NI) {
 #pragma unroll
                 for (int r = 0; r < R; ++r) {
-                    double* q = part + (long long)(i + r * L::NI) * pstride;
+                    double* q = part + (i + r * L::NI) * pstride;
                     q[0] = (double)acc[u][r].x;
                     q[1] = (double)acc[u][r].y;
                 }
