@@ -94,25 +94,30 @@ template <int N, int R, int NS, int S, int W> struct CtStage {
     static constexpr int U = (NI + 2 * W - 1) / (2 * W);
     static constexpr int TWS = N / (NS * R);
 
+    // unit i (caller checks i < NI): load, twiddle, R-point DFT
+    template <class Src>
+    __device__ __forceinline__ static void compute_unit(P2f (&h)[R], const float2* __restrict__ tw, const Src& src,
+                                                       int i, int slot) {
+#pragma unroll
+        for (int r = 0; r < R; ++r) h[r] = src(i + r * NI, slot);
+        if constexpr (NS > 1) {
+            const int base = (i % NS) * TWS;
+#pragma unroll
+            for (int r = 1; r < R; ++r) {
+                const float2 w = tw[r * base];
+                h[r] = S > 0 ? cmul(h[r], w) : cmulc(h[r], w);
+            }
+        }
+        Dft<R, S>::run(h);
+    }
+
     template <class Src>
     __device__ __forceinline__ static void compute(P2f (&h)[U][R], const float2* __restrict__ tw, const Src& src,
                                                   int slot, int sub, int warp) {
 #pragma unroll
         for (int u = 0; u < U; ++u) {
             const int i = 2 * (warp + u * W) + sub;
-            if (NI % (2 * W) == 0 || i < NI) {
-#pragma unroll
-                for (int r = 0; r < R; ++r) h[u][r] = src(i + r * NI, slot);
-                if constexpr (NS > 1) {
-                    const int base = (i % NS) * TWS;
-#pragma unroll
-                    for (int r = 1; r < R; ++r) {
-                        const float2 w = tw[r * base];
-                        h[u][r] = S > 0 ? cmul(h[u][r], w) : cmulc(h[u][r], w);
-                    }
-                }
-                Dft<R, S>::run(h[u]);
-            }
+            if (NI % (2 * W) == 0 || i < NI) compute_unit(h[u], tw, src, i, slot);
         }
     }
 

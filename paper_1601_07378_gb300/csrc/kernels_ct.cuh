@@ -360,17 +360,17 @@ __global__ void __launch_bounds__(kThreads) k3b_ct(DevTables t, const float2* __
             __syncthreads();
         }
         if (act) {
-            P2f h[L::U][R];
-            L::compute(h, stw, sb, slot, sub, warp);
 #pragma unroll
             for (int u = 0; u < L::U; ++u) {
                 const int i = 2 * (warp + u * kWarps) + sub;
                 if (L::NI % (2 * kWarps) == 0 || i < L::NI) {
+                    P2f h[R];
+                    L::compute_unit(h, stw, sb, i, slot);
 #pragma unroll
                     for (int r = 0; r < R; ++r) {
                         const P2f p = sa(i + r * L::NI, slot);
-                        acc[u][r].x += h[u][r].a.x * p.a.x + h[u][r].a.y * p.a.y;
-                        acc[u][r].y += h[u][r].b.x * p.b.x + h[u][r].b.y * p.b.y;
+                        acc[u][r].x += h[r].a.x * p.a.x + h[r].a.y * p.a.y;
+                        acc[u][r].y += h[r].b.x * p.b.x + h[r].b.y * p.b.y;
                     }
                 }
             }
@@ -436,7 +436,7 @@ __global__ void __launch_bounds__(kThreads) k3g_ct(DevTables t, const float2* __
 // the group's bands (at most 16); the group's partial sum is written in FP64
 // and the groups are added later in a fixed order.
 template <int N>
-__global__ void __launch_bounds__(kThreads) k3d_ct(DevTables t, const float2* __restrict__ tw1, const float2* slab,
+__global__ void __launch_bounds__(kThreads, minb(N, 5)) k3d_ct(DevTables t, const float2* __restrict__ tw1, const float2* slab,
                                                   int nb, int bpg, const float* __restrict__ occ, long long b_base,
                                                   int pair, long long nreal, double* __restrict__ partial) {
     using SC = Sched<N>;
@@ -482,16 +482,18 @@ __global__ void __launch_bounds__(kThreads) k3d_ct(DevTables t, const float2* __
             __syncthreads();
         }
         if (act) {
-            P2f h[L::U][R];
-            L::compute(h, stw, sb, slot, sub, warp);
+            // one unit at a time (keeps the registers of one unit's values
+            // next to the accumulators)
 #pragma unroll
             for (int u = 0; u < L::U; ++u) {
                 const int i = 2 * (warp + u * kWarps) + sub;
                 if (L::NI % (2 * kWarps) == 0 || i < L::NI) {
+                    P2f h[R];
+                    L::compute_unit(h, stw, sb, i, slot);
 #pragma unroll
                     for (int r = 0; r < R; ++r) {
-                        acc[u][r].x += wx * h[u][r].a.x * h[u][r].a.x + wy * h[u][r].a.y * h[u][r].a.y;
-                        acc[u][r].y += wx * h[u][r].b.x * h[u][r].b.x + wy * h[u][r].b.y * h[u][r].b.y;
+                        acc[u][r].x += wx * h[r].a.x * h[r].a.x + wy * h[r].a.y * h[r].a.y;
+                        acc[u][r].y += wx * h[r].b.x * h[r].b.x + wy * h[r].b.y * h[r].b.y;
                     }
                 }
             }
