@@ -17,7 +17,7 @@
 
 // Minimum resident CTAs per SM asked of the compiler (caps a kernel's
 // registers at 65536 / (128 x MINB)).  Measured on GB300 at 96^3: the z- and
-// y-pass kernels gain from more resident CTAs (K1: 6, K2: 6, K4: 7), the
+// y-pass kernels gain from more resident CTAs (K1, K2, K4: 6), the
 // x-pass loses (its register-held chain wants the registers).  Applied up to
 // length 96; longer lines keep the compiler's choice (the caps would spill).
 #ifndef VLOC_MINB_K1
@@ -29,8 +29,11 @@
 #ifndef VLOC_MINB_K3
 #define VLOC_MINB_K3 1
 #endif
+#ifndef VLOC_K3_WARPS
+#define VLOC_K3_WARPS 4
+#endif
 #ifndef VLOC_MINB_K4
-#define VLOC_MINB_K4 7
+#define VLOC_MINB_K4 6
 #endif
 
 namespace vloc {
@@ -46,22 +49,44 @@ __device__ __forceinline__ int sub_of() { return (threadIdx.x >> 4) & 1; }
 __device__ __forceinline__ int warp_of() { return threadIdx.x >> 5; }
 
 // ------------------------------------------------------------- tile I/O
-__device__ __forceinline__ void scatter_entries_p(const int2* __restrict__ ent, int e0, int e1,
-                                                  const float2* __restrict__ c, float2* buf) {
-    for (int base = e0 + (int)threadIdx.x; base < e1; base += kBatch * kThreads) {
-        int2 en[kBatch];
-        float2 val[kBatch];
+// One batch of a tile's plane-wave entries starting at `base` (stride
+// kThreads): the entries and their coefficients into registers, then into
+// the tile buffer.
+__device__ __forceinline__ void entries_load_p(const int2* __restrict__ ent, int base, int e1,
+                                               const float2* __restrict__ c, int2 (&en)[kBatch],
+                                               float2 (&val)[kBatch]) {
 #pragma unroll
-        for (int u = 0; u < kBatch; ++u) {
-            const int e = base + u * kThreads;
-            en[u] = e < e1 ? ent[e] : make_int2(0, -1);
-        }
-#pragma unroll
-        for (int u = 0; u < kBatch; ++u) val[u] = en[u].y >= 0 ? c[en[u].x] : make_float2(0.f, 0.f);
-#pragma unroll
-        for (int u = 0; u < kBatch; ++u)
-            if (en[u].y >= 0) buf[(en[u].y & 0xffff) * kLdP + (en[u].y >> 16)] = val[u];
+    for (int u = 0; u < kBatch; ++u) {
+        const int e = base + u * kThreads;
+        en[u] = e < e1 ? ent[e] : make_int2(0, -1);
     }
+#pragma unroll
+    for (int u = 0; u < kBatch; ++u) val[u] = en[u].y >= 0 ? c[en[u].x] : make_float2(0.f, 0.f);
+}
+__device__ __forceinline__ void entries_store_p(float2* buf, const int2 (&en)[kBatch], const float2 (&val)[kBatch]) {
+#pragma unroll
+    for (int u = 0; u < kBatch; ++u)
+        if (en[u].y >= 0) buf[(en[u].y & 0xffff) * kLdP + (en[u].y >> 16)] = val[u];
+}
+// Clear the tile buffer (N rows) and scatter the tile's plane waves into it;
+// the first batch's loads are issued before the clearing so their latency
+// hides behind it.  Ends with a barrier.
+template <int N>
+__device__ __forceinline__ void scatter_tile_p(const int2* __restrict__ ent, int e0, int e1,
+                                               const float2* __restrict__ c, float2* buf) {
+    int2 en[kBatch];
+    float2 val[kBatch];
+    const int base0 = e0 + (int)threadIdx.x;
+    entries_load_p(ent, base0, e1, c, en, val);
+    for (int i = threadIdx.x; i < N * kLdP / 2; i += kThreads)
+        reinterpret_cast<float4*>(buf)[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    __syncthreads();
+    entries_store_p(buf, en, val);
+    for (int base = base0 + kBatch * kThreads; base < e1; base += kBatch * kThreads) {
+        entries_load_p(ent, base, e1, c, en, val);
+        entries_store_p(buf, en, val);
+    }
+    __syncthreads();
 }
 __device__ __forceinline__ void gather_entries_p(const int2* __restrict__ ent, int e0, int e1, const float2* buf,
                                                  float2* o, float scale, const float* __restrict__ diag,
@@ -114,15 +139,24 @@ template <int NN>
 __device__ __forceinline__ void rows_in_p(float2* buf, const float2* __restrict__ cb, const int* sticks, int lines) {
     constexpr int K = (NN + 31) / 32;
     const int lane = threadIdx.x & 31;
-    for (int l = threadIdx.x >> 5; l < lines; l += kWarps) {
+    // two lines per pass: twice the loads in flight
+    for (int l = threadIdx.x >> 5; l < lines; l += 2 * kWarps) {
+        const int l2 = l + kWarps;
         const float2* row = cb + (long long)sticks[l] * NN;
-        float2 v[K];
+        const float2* row2 = cb + (long long)sticks[l2 < lines ? l2 : l] * NN;
+        float2 v[K], v2[K];
 #pragma unroll
         for (int k = 0; k < K; ++k)
-            if (NN % 32 == 0 || lane + 32 * k < NN) v[k] = row[lane + 32 * k];
+            if (NN % 32 == 0 || lane + 32 * k < NN) {
+                v[k] = row[lane + 32 * k];
+                v2[k] = row2[lane + 32 * k];
+            }
 #pragma unroll
         for (int k = 0; k < K; ++k)
-            if (NN % 32 == 0 || lane + 32 * k < NN) buf[(lane + 32 * k) * kLdP + l] = v[k];
+            if (NN % 32 == 0 || lane + 32 * k < NN) {
+                buf[(lane + 32 * k) * kLdP + l] = v[k];
+                if (l2 < lines) buf[(lane + 32 * k) * kLdP + l2] = v2[k];
+            }
     }
 }
 
@@ -175,11 +209,7 @@ __global__ void __launch_bounds__(kThreads, minb(N, VLOC_MINB_K1)) k1_ct(DevTabl
     const long long b = blockIdx.y;
     load_tw<float>(stw, tw3, N);
     const int s0 = t.tile_ptr[tile], lines = t.tile_ptr[tile + 1] - s0;
-    for (int i = threadIdx.x; i < N * kLdP / 2; i += kThreads)
-        reinterpret_cast<float4*>(buf)[i] = make_float4(0.f, 0.f, 0.f, 0.f);
-    __syncthreads();
-    scatter_entries_p(t.tile_pw, t.tile_pw_ptr[tile], t.tile_pw_ptr[tile + 1], coeffs + b * t.npw, buf);
-    __syncthreads();
+    scatter_tile_p<N>(t.tile_pw, t.tile_pw_ptr[tile], t.tile_pw_ptr[tile + 1], coeffs + b * t.npw, buf);
     fft_ct<N, +1, kWarps, false, true, true>(stw, SmemP{buf}, SmemP{buf}, buf, slot_of(), sub_of(), warp_of(),
                                              2 * slot_of() < lines);
     __syncthreads();
@@ -212,8 +242,9 @@ __global__ void __launch_bounds__(kThreads, minb(N, VLOC_MINB_K2)) k2_ct(DevTabl
 }
 
 // ------------------------------------------------------------------ K3
-template <int N>
-__global__ void __launch_bounds__(kThreads, minb(N, VLOC_MINB_K3)) k3_ct(DevTables t, const float2* __restrict__ tw1,
+// W warps per CTA (the tile is always 32 lines; more warps split its units).
+template <int N, int W>
+__global__ void __launch_bounds__(32 * W, minb(N, VLOC_MINB_K3)) k3_ct(DevTables t, const float2* __restrict__ tw1,
                                                  const float* __restrict__ Vr, float2* slab) {
     using SC = Sched<N>;
     constexpr int nst = SC::nst;
@@ -229,8 +260,10 @@ __global__ void __launch_bounds__(kThreads, minb(N, VLOC_MINB_K3)) k3_ct(DevTabl
     const long long b = blockIdx.z;
     const int lines = min(kLines, n3 - z0);
     const bool act = 2 * slot < lines;
-    load_tw<float>(stw, tw1, N);
-    for (int e = threadIdx.x; e < N; e += kThreads) xrow[e] = t.xrow_plane[e];
+    for (int e = threadIdx.x; e < N; e += 32 * W) {
+        stw[e] = tw1[e];
+        xrow[e] = t.xrow_plane[e];
+    }
     __syncthreads();
     const int pstride = n2 * n3;
     XRowsP xr{slab + b * t.NP * (long long)pstride + y * n3 + z0, xrow, pstride};
@@ -238,20 +271,20 @@ __global__ void __launch_bounds__(kThreads, minb(N, VLOC_MINB_K3)) k3_ct(DevTabl
     SmemP sb{buf};
 
     // inverse x-FFT, stages 0 .. nst-2 (global rows -> buffer)
-    NatStage<N, +1, kWarps, 0>::template run<false>(stw, xr, sb, slot, sub, warp, act);
+    NatStage<N, +1, W, 0>::template run<false>(stw, xr, sb, slot, sub, warp, act);
     __syncthreads();
     if constexpr (nst >= 3) {
-        NatStage<N, +1, kWarps, 1>::template run<true>(stw, sb, sb, slot, sub, warp, act);
+        NatStage<N, +1, W, 1>::template run<true>(stw, sb, sb, slot, sub, warp, act);
         __syncthreads();
     }
     if constexpr (nst >= 4) {
-        NatStage<N, +1, kWarps, 2>::template run<true>(stw, sb, sb, slot, sub, warp, act);
+        NatStage<N, +1, W, 2>::template run<true>(stw, sb, sb, slot, sub, warp, act);
         __syncthreads();
     }
     // last inverse stage -> psi(x) * V(x, y, z) -> first forward stage of the
     // reversed schedule, in registers: both work on elements i + r N/R.
-    using L = NatStage<N, +1, kWarps, nst - 1>;
-    using F = RevStage<N, -1, kWarps, 0>;
+    using L = NatStage<N, +1, W, nst - 1>;
+    using F = RevStage<N, -1, W, 0>;
     constexpr int R = SC::R(nst - 1);
     static_assert(F::NI == L::NI && SC::RR(0) == R, "chained stages must share units");
     P2f h[L::U][R];
@@ -259,8 +292,8 @@ __global__ void __launch_bounds__(kThreads, minb(N, VLOC_MINB_K3)) k3_ct(DevTabl
         L::compute(h, stw, sb, slot, sub, warp);
 #pragma unroll
         for (int u = 0; u < L::U; ++u) {
-            const int i = 2 * (warp + u * kWarps) + sub;
-            if (L::NI % (2 * kWarps) == 0 || i < L::NI) {
+            const int i = 2 * (warp + u * W) + sub;
+            if (L::NI % (2 * W) == 0 || i < L::NI) {
 #pragma unroll
                 for (int r = 0; r < R; ++r) {
                     const float2 w = *reinterpret_cast<const float2*>(vrow + (i + r * L::NI) * pstride);
@@ -276,14 +309,14 @@ __global__ void __launch_bounds__(kThreads, minb(N, VLOC_MINB_K3)) k3_ct(DevTabl
     __syncthreads();
     // forward x-FFT, remaining stages (buffer -> occupied global rows)
     if constexpr (nst >= 3) {
-        RevStage<N, -1, kWarps, 1>::template run<true>(stw, sb, sb, slot, sub, warp, act);
+        RevStage<N, -1, W, 1>::template run<true>(stw, sb, sb, slot, sub, warp, act);
         __syncthreads();
     }
     if constexpr (nst >= 4) {
-        RevStage<N, -1, kWarps, 2>::template run<true>(stw, sb, sb, slot, sub, warp, act);
+        RevStage<N, -1, W, 2>::template run<true>(stw, sb, sb, slot, sub, warp, act);
         __syncthreads();
     }
-    RevStage<N, -1, kWarps, nst - 1>::template run<false>(stw, sb, xr, slot, sub, warp, act);
+    RevStage<N, -1, W, nst - 1>::template run<false>(stw, sb, xr, slot, sub, warp, act);
 }
 
 // ------------------------------------------------------------------ K4
@@ -553,10 +586,11 @@ int LaunchCT<T, N>::k2(int sign, const DevTables& t, const void* tw2, long long 
 }
 template <typename T, int N>
 int LaunchCT<T, N>::k3(const DevTables& t, const void* tw1, const void* V, long long nb, void* slab, cudaStream_t st) {
-    static const cudaError_t once = CtSmem<N>::ensure(k3_ct<N>);
+    static const cudaError_t once = CtSmem<N>::ensure(k3_ct<N, VLOC_K3_WARPS>);
     if (once) return (int)once;
     const dim3 grid(t.n2, (t.n3 + kLines - 1) / kLines, (unsigned)nb);
-    k3_ct<N><<<grid, kThreads, CtSmem<N>::sm, st>>>(t, (const float2*)tw1, (const float*)V, (float2*)slab);
+    k3_ct<N, VLOC_K3_WARPS><<<grid, 32 * VLOC_K3_WARPS, CtSmem<N>::sm, st>>>(t, (const float2*)tw1, (const float*)V,
+                                                                           (float2*)slab);
     return (int)cudaGetLastError();
 }
 template <typename T, int N>
