@@ -78,6 +78,12 @@ extern "C" {
                                        /* bands are real in r-space and travel two  */
                                        /* per complex transform.  Apply / adjoint / */
                                        /* batched only.                             */
+#define VLOC_DOUBLE_FLOAT       0x2000 /* with VLOC_F64: apply in double-float       */
+                                       /* arithmetic (hi + lo FP32 pairs, ~48 bits,  */
+                                       /* on the FP32 pipes); FP64 data in and out.  */
+                                       /* Used when every axis length has compiled   */
+                                       /* kernels (info.path bit 3), else native FP64*/
+                                       /* (apply / adjoint / H / batched only).      */
 #define VLOC_HOST_ONLY          0x200  /* build host tables only (no device memory, */
                                        /* no CUDA call); for introspection: the     */
                                        /* device calls then return VLOC_ERR_STATE   */
@@ -98,7 +104,8 @@ typedef struct vloc_info {
     int32_t radix[3][4];         /* per-axis radix schedule (0 = unused)          */
     int32_t nstages[3];
     int32_t path;                /* bit 0: compile-time-length kernels enabled;   */
-                                 /* bit 2: Gamma-point real mode                  */
+                                 /* bit 2: Gamma-point real mode;                 */
+                                 /* bit 3: double-float FP64 apply in use         */
 } vloc_info;
 
 /*
@@ -115,7 +122,8 @@ typedef struct vloc_info {
  *   npw        : number of plane waves, >= 1.
  *   flags      : exactly one of VLOC_F32 / VLOC_F64, optionally one
  *                partition flag, VLOC_GRAPH, VLOC_HOST_ONLY,
- *                VLOC_GENERIC_KERNELS and VLOC_GAMMA.  With VLOC_GAMMA every
+ *                VLOC_GENERIC_KERNELS, VLOC_GAMMA and VLOC_DOUBLE_FLOAT (with
+ *                VLOC_F64 only, else VLOC_ERR_ARG).  With VLOC_GAMMA every
  *                -G must be a valid index too (else VLOC_ERR_GLIST), and
  *                npw counts the half list (the caller's arrays).
  *   max_bands_per_chunk : bands per workspace chunk (<= 0: automatic, a

@@ -1,8 +1,8 @@
 """Build the sm_103a shared library libvloc.so in-tree (no cmake, no pip).
 
-The translation units of ``csrc/`` (the compile-time-length kernels split
-over three files, one per precision for the runtime-radix kernels, the
-dispatch, the plan and the no-alloc entry) are compiled in parallel with
+The translation units of ``csrc/`` (the compile-time-length FP32 and
+double-float kernels split over three files each, one per precision for the
+runtime-radix kernels, the dispatch, the plan and the no-alloc entry) are compiled in parallel with
 nvcc and linked into ``paper_1601_07378_gb300/_build/libvloc.so``
 against the shared CUDA runtime, so the library shares the runtime PyTorch
 already loaded.  ``python -m paper_1601_07378_gb300.build`` rebuilds it.
@@ -21,8 +21,8 @@ LIB = os.path.join(BUILD, "libvloc.so")
 ROOT = os.path.dirname(HERE)
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["kernels_ct_a.cu", "kernels_ct_b.cu", "kernels_ct_c.cu", "kernels_f32.cu", "kernels_f64.cu",
-           "kernels.cu", "plan.cpp", "noalloc.cu"]
+SOURCES = ["kernels_ct_a.cu", "kernels_ct_b.cu", "kernels_ct_c.cu", "kernels_df_a.cu", "kernels_df_b.cu",
+           "kernels_df_c.cu", "kernels_f32.cu", "kernels_f64.cu", "kernels.cu", "plan.cpp", "noalloc.cu"]
 
 
 def _cuda_home() -> str:

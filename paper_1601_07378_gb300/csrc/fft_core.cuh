@@ -91,6 +91,108 @@ __device__ __forceinline__ P2f cmul_cs(P2f x, float c, float s) { return {cmul_c
 template <int S> __device__ __forceinline__ P2f mul_si(P2f x) { return {mul_si<S>(x.a), mul_si<S>(x.b)}; }
 template <> __device__ __forceinline__ P2f czero<P2f>() { return {make_float2(0.f, 0.f), make_float2(0.f, 0.f)}; }
 
+// ---------------------------------------------- double-float arithmetic
+// A real value held as hi + lo, two FP32 with |lo| <= ulp(hi) / 2 (about 48
+// significant bits), in a float2 (x = hi, y = lo).  Sums use the two-sum
+// of Knuth / Moller, products an FMA for the rounding error of hi * hi
+// (Dekker's algorithm with a fused multiply-add); each result is
+// renormalised with a fast two-sum.  Errors stay within a few units of
+// 2^-48 relative to the operands' magnitudes, the bound an FFT's norm-wise
+// error analysis needs.
+__device__ __forceinline__ float2 df_add(float2 a, float2 b) {
+    const float s = a.x + b.x;
+    const float bb = s - a.x;
+    const float e = ((a.x - (s - bb)) + (b.x - bb)) + (a.y + b.y);
+    const float hi = s + e;
+    return make_float2(hi, e - (hi - s));
+}
+__device__ __forceinline__ float2 df_neg(float2 a) { return make_float2(-a.x, -a.y); }
+__device__ __forceinline__ float2 fneg2_(float2 a) { return make_float2(-a.x, -a.y); }
+__device__ __forceinline__ float2 df_mul(float2 a, float2 b) {
+    const float p = a.x * b.x;
+    float e = fmaf(a.x, b.x, -p);
+    e = fmaf(a.x, b.y, e);
+    e = fmaf(a.y, b.x, e);
+    const float hi = p + e;
+    return make_float2(hi, e - (hi - p));
+}
+// hi + lo split of a double (hi = nearest FP32, lo = nearest FP32 of the rest)
+__host__ __device__ __forceinline__ float2 df_split(double v) {
+    const float hi = (float)v;
+    return make_float2(hi, (float)(v - (double)hi));
+}
+__device__ __forceinline__ double df_value(float2 a) { return (double)a.x + (double)a.y; }
+
+// Complex double-float value held as a pair of high parts and a pair of low
+// parts, hi = (re.hi, im.hi), lo = (re.lo, im.lo): the real and imaginary
+// double-float operations then run side by side as paired FP32 instructions
+// (sm_100+).  16 bytes, the size of an FP64 complex.  Scalar constants of the
+// DFTs arrive as doubles and are split at compile time.
+struct __align__(16) DFc {
+    float2 hi, lo;
+};
+template <> struct ScalarOf<DFc> { using type = double; };
+// twiddle w = c + i s as broadcast pairs: (c.hi, c.hi), (c.lo, c.lo),
+// (-s.hi, s.hi), (-s.lo, s.lo)
+struct __align__(16) TwDF {
+    float2 ch, cl, sh, sl;
+};
+__host__ __device__ __forceinline__ TwDF twdf_make(double c, double s) {
+    const float2 cc = df_split(c), ss = df_split(s);
+    return TwDF{make_float2(cc.x, cc.x), make_float2(cc.y, cc.y), make_float2(-ss.x, ss.x), make_float2(-ss.y, ss.y)};
+}
+__device__ __forceinline__ DFc df2_neg(DFc x) { return {fneg2_(x.hi), fneg2_(x.lo)}; }
+// paired double-float sum (two-sum of the high parts, then renormalise)
+__device__ __forceinline__ DFc cadd(DFc x, DFc y) {
+    const float2 s = __fadd2_rn(x.hi, y.hi);
+    const float2 bb = __fadd2_rn(s, fneg2_(x.hi));
+    const float2 e = __fadd2_rn(__fadd2_rn(__fadd2_rn(x.hi, fneg2_(__fadd2_rn(s, fneg2_(bb)))),
+                                           __fadd2_rn(y.hi, fneg2_(bb))),
+                                __fadd2_rn(x.lo, y.lo));
+    const float2 hi = __fadd2_rn(s, e);
+    return {hi, __fadd2_rn(e, fneg2_(__fadd2_rn(hi, fneg2_(s))))};
+}
+__device__ __forceinline__ DFc csub(DFc x, DFc y) { return cadd(x, df2_neg(y)); }
+__device__ __forceinline__ DFc cneg(DFc x) { return df2_neg(x); }
+// componentwise double-float product of x with the pair (bh + bl)
+__device__ __forceinline__ DFc df2_mul(DFc x, float2 bh, float2 bl) {
+    const float2 p = __fmul2_rn(x.hi, bh);
+    float2 e = __ffma2_rn(x.hi, bh, fneg2_(p));
+    e = __ffma2_rn(x.hi, bl, e);
+    e = __ffma2_rn(x.lo, bh, e);
+    const float2 hi = __fadd2_rn(p, e);
+    return {hi, __fadd2_rn(e, fneg2_(__fadd2_rn(hi, fneg2_(p))))};
+}
+__device__ __forceinline__ DFc df2_swap(DFc x) {  // (re, im) -> (im, re)
+    return {make_float2(x.hi.y, x.hi.x), make_float2(x.lo.y, x.lo.x)};
+}
+__device__ __forceinline__ DFc cmul(DFc x, TwDF w) {  // x * w = x c + (im, re) (-s, s)
+    return cadd(df2_mul(x, w.ch, w.cl), df2_mul(df2_swap(x), w.sh, w.sl));
+}
+__device__ __forceinline__ DFc cmulc(DFc x, TwDF w) {  // x * conj(w) = x c - (im, re) (-s, s)
+    return cadd(df2_mul(x, w.ch, w.cl), df2_neg(df2_mul(df2_swap(x), w.sh, w.sl)));
+}
+__device__ __forceinline__ DFc cscale(DFc x, double s) {
+    const float2 d = df_split(s);
+    return df2_mul(x, make_float2(d.x, d.x), make_float2(d.y, d.y));
+}
+__device__ __forceinline__ DFc cfma(DFc x, double s, DFc y) { return cadd(x, cscale(y, s)); }  // x + s y
+__device__ __forceinline__ DFc cmul_cs(DFc x, double c, double s) { return cmul(x, twdf_make(c, s)); }
+template <int S> __device__ __forceinline__ DFc mul_si(DFc x) {  // x * (S i): (re, im) -> (-S im, S re)
+    const DFc w = df2_swap(x);
+    return S > 0 ? DFc{make_float2(-w.hi.x, w.hi.y), make_float2(-w.lo.x, w.lo.y)}
+                 : DFc{make_float2(w.hi.x, -w.hi.y), make_float2(w.lo.x, -w.lo.y)};
+}
+template <> __device__ __forceinline__ DFc czero<DFc>() { return {make_float2(0.f, 0.f), make_float2(0.f, 0.f)}; }
+// FP64 complex <-> DFc
+__device__ __forceinline__ DFc df_from(double2 v) {
+    const float2 a = df_split(v.x), b = df_split(v.y);
+    return {make_float2(a.x, b.x), make_float2(a.y, b.y)};
+}
+__device__ __forceinline__ double2 df_to(DFc v) {
+    return make_double2((double)v.hi.x + (double)v.lo.x, (double)v.hi.y + (double)v.lo.y);
+}
+
 // ------------------------------------------------- compile-time cos / sin
 // exp(2 pi i m / R) from Taylor series on the first octant (|x| <= pi/4,
 // truncation below 1e-21), with exact integer quadrant reduction.

@@ -76,35 +76,38 @@ template <int N> struct Sched {
 // Shared line buffer for lane pairs: [N][kLdP] FP32 complex, pitch even so a
 // pair of adjacent lines is one aligned 16-byte vector.
 constexpr int kLdP = kLines + 2;
-struct SmemP {
+template <class V> struct SmemT {  // [N][kLdP] float2 slots; V is 16 bytes per slot
     float2* p;
-    __device__ __forceinline__ P2f operator()(int e, int slot) const {
-        return *reinterpret_cast<const P2f*>(p + e * kLdP + 2 * slot);
+    __device__ __forceinline__ V operator()(int e, int slot) const {
+        return *reinterpret_cast<const V*>(p + e * kLdP + 2 * slot);
     }
-    __device__ __forceinline__ void operator()(int e, int slot, P2f v) const {
-        *reinterpret_cast<P2f*>(p + e * kLdP + 2 * slot) = v;
+    __device__ __forceinline__ void operator()(int e, int slot, V v) const {
+        *reinterpret_cast<V*>(p + e * kLdP + 2 * slot) = v;
     }
 };
+using SmemP = SmemT<P2f>;
 
-// One compile-time Stockham stage over a 32-line tile.  Each lane carries
-// the pair of lines (2 slot, 2 slot + 1), slot = lane % 16, so a warp works
-// on two units at once (sub = lane / 16); the CTA's W warps share the units.
-template <int N, int R, int NS, int S, int W> struct CtStage {
+// One compile-time Stockham stage over a tile of 16 slots.  Each lane carries
+// one 16-byte value V per element of its slot (slot = lane % 16): a pair of
+// FP32 lines (P2f, 32-line tiles) or one double-float line (DFc, 16-line
+// tiles); a warp works on two units at once (sub = lane / 16) and the CTA's
+// W warps share the units.  TW is the twiddle type of V.
+template <int N, int R, int NS, int S, int W, class V = P2f, class TW = float2> struct CtStage {
     static constexpr int NI = N / R;
     static constexpr int U = (NI + 2 * W - 1) / (2 * W);
     static constexpr int TWS = N / (NS * R);
 
     // unit i (caller checks i < NI): load, twiddle, R-point DFT
     template <class Src>
-    __device__ __forceinline__ static void compute_unit(P2f (&h)[R], const float2* __restrict__ tw, const Src& src,
-                                                       int i, int slot) {
+    __device__ __forceinline__ static void compute_unit(V (&h)[R], const TW* __restrict__ tw, const Src& src, int i,
+                                                       int slot) {
 #pragma unroll
         for (int r = 0; r < R; ++r) h[r] = src(i + r * NI, slot);
         if constexpr (NS > 1) {
             const int base = (i % NS) * TWS;
 #pragma unroll
             for (int r = 1; r < R; ++r) {
-                const float2 w = tw[r * base];
+                const TW w = tw[r * base];
                 h[r] = S > 0 ? cmul(h[r], w) : cmulc(h[r], w);
             }
         }
@@ -112,8 +115,8 @@ template <int N, int R, int NS, int S, int W> struct CtStage {
     }
 
     template <class Src>
-    __device__ __forceinline__ static void compute(P2f (&h)[U][R], const float2* __restrict__ tw, const Src& src,
-                                                  int slot, int sub, int warp) {
+    __device__ __forceinline__ static void compute(V (&h)[U][R], const TW* __restrict__ tw, const Src& src, int slot,
+                                                  int sub, int warp) {
 #pragma unroll
         for (int u = 0; u < U; ++u) {
             const int i = 2 * (warp + u * W) + sub;
@@ -122,7 +125,7 @@ template <int N, int R, int NS, int S, int W> struct CtStage {
     }
 
     template <class Dst>
-    __device__ __forceinline__ static void store(const P2f (&h)[U][R], const Dst& dst, int slot, int sub, int warp) {
+    __device__ __forceinline__ static void store(const V (&h)[U][R], const Dst& dst, int slot, int sub, int warp) {
 #pragma unroll
         for (int u = 0; u < U; ++u) {
             const int i = 2 * (warp + u * W) + sub;
@@ -138,9 +141,9 @@ template <int N, int R, int NS, int S, int W> struct CtStage {
     // compute + store; HOLD puts a CTA barrier between them (the stage reads
     // and writes the same shared buffer).
     template <bool HOLD, class Src, class Dst>
-    __device__ __forceinline__ static void run(const float2* __restrict__ tw, const Src& src, const Dst& dst, int slot,
+    __device__ __forceinline__ static void run(const TW* __restrict__ tw, const Src& src, const Dst& dst, int slot,
                                               int sub, int warp, bool act) {
-        P2f h[U][R];
+        V h[U][R];
         if (act) compute(h, tw, src, slot, sub, warp);
         if constexpr (HOLD) __syncthreads();
         if (act) store(h, dst, slot, sub, warp);
@@ -148,22 +151,25 @@ template <int N, int R, int NS, int S, int W> struct CtStage {
 };
 
 // Stage s of the natural (sign S) schedule of length N.
-template <int N, int S, int W, int s> using NatStage = CtStage<N, Sched<N>::R(s), Sched<N>::NS(s), S, W>;
+template <int N, int S, int W, int s, class V = P2f, class TW = float2>
+using NatStage = CtStage<N, Sched<N>::R(s), Sched<N>::NS(s), S, W, V, TW>;
 // Stage s of the reversed schedule.
-template <int N, int S, int W, int s> using RevStage = CtStage<N, Sched<N>::RR(s), Sched<N>::NSR(s), S, W>;
+template <int N, int S, int W, int s, class V = P2f, class TW = float2>
+using RevStage = CtStage<N, Sched<N>::RR(s), Sched<N>::NSR(s), S, W, V, TW>;
 
 // Full transform with one shared buffer `buf` ([N][kLdP] FP32 complex).
 // `in` may be global or `buf` itself (IN_BUF), `out` may be global or `buf`
 // (OUT_BUF).  The caller provides a barrier before the call if `buf` was in
 // use; the call ends without a barrier.
-template <int N, int S, int W, bool REV, bool IN_BUF, bool OUT_BUF, class In, class Out>
-__device__ __forceinline__ void fft_ct(const float2* __restrict__ tw, const In& in, const Out& out, float2* buf,
-                                       int slot, int sub, int warp, bool act) {
+template <int N, int S, int W, bool REV, bool IN_BUF, bool OUT_BUF, class V = P2f, class TW = float2, class In,
+          class Out>
+__device__ __forceinline__ void fft_ct(const TW* __restrict__ tw, const In& in, const Out& out, float2* buf, int slot,
+                                       int sub, int warp, bool act) {
     constexpr int nst = Sched<N>::nst;
-    SmemP sb{buf};
+    SmemT<V> sb{buf};
     auto stage = [&](auto sc, const auto& src, const auto& dst, auto hold) {
         constexpr int s = decltype(sc)::value;
-        using St = std::conditional_t<REV, RevStage<N, S, W, s>, NatStage<N, S, W, s>>;
+        using St = std::conditional_t<REV, RevStage<N, S, W, s, V, TW>, NatStage<N, S, W, s, V, TW>>;
         St::template run<decltype(hold)::value>(tw, src, dst, slot, sub, warp, act);
     };
     if constexpr (nst == 1) {

@@ -87,8 +87,25 @@ template <typename T, int N> struct LaunchCT {
                    long long b_base, int pair, long long nreal, double* partial, cudaStream_t st);
 };
 
+// Double-float launchers (kernels_df.cuh) for the same lengths, FP64 data:
+// twiddle tables are TwDF [n], V is hi + lo pairs [N], the cylinder and slab
+// hold double-float complex values (16 bytes).
+template <int N> struct LaunchDF {
+    static int k1(const DevTables& t, const void* tw3, const void* coeffs, long long nb, void* cyl, cudaStream_t st);
+    static int k2(int sign, const DevTables& t, const void* tw2, long long nb, void* cyl, void* slab, cudaStream_t st);
+    static int k3(const DevTables& t, const void* tw1, const void* Vdf, long long nb, void* slab, cudaStream_t st);
+    static int k4(const DevTables& t, const void* tw3, const void* cyl, long long nb, void* out, const void* diag,
+                  const void* cin, cudaStream_t st);
+};
+bool has_df(int n);
+// TwDF table [n] from an FP64 twiddle table; V [N] FP64 -> hi + lo pairs
+int launch_twiddles_df(const void* tw64, void* twdf, int n, cudaStream_t st);
+int launch_v_to_df(const void* V, void* Vdf, long long N, cudaStream_t st);
+
 // Precision dispatch (kernels.cu): dbl = 0 for float, 1 for double; `fast`
-// selects the compile-time-length kernels when one exists for the axis.
+// selects the compile-time-length kernels when one exists for the axis (FP32),
+// and fast = 2 with dbl = 1 the double-float kernels (every axis must have
+// them: the caller checks has_df).
 int launch_twiddles(int dbl, void* tw, int n, cudaStream_t st);
 int launch_k1_scatter_zpass(int dbl, int fast, const DevTables& t, const LaunchAxes& ax, const void* tw3, const void* coeffs,
                             long long nb, void* cyl, cudaStream_t st);

@@ -8,6 +8,7 @@
 #include <mutex>
 
 #include "internal.h"
+#include "fft_core.cuh"
 
 namespace vloc {
 
@@ -104,6 +105,26 @@ int set_smem_limits(int dbl, int nmax, int optin) {
 int launch_twiddles(int dbl, void* tw, int n, cudaStream_t st) {
     return dbl ? Launch<double>::twiddles(tw, n, st) : Launch<float>::twiddles(tw, n, st);
 }
+bool has_ct(int n);
+bool has_df(int n) { return has_ct(n); }
+
+__global__ void k_twiddles_df(const double2* __restrict__ tw, TwDF* __restrict__ out, int n) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j < n) out[j] = twdf_make(tw[j].x, tw[j].y);
+}
+int launch_twiddles_df(const void* tw64, void* twdf, int n, cudaStream_t st) {
+    k_twiddles_df<<<(n + 127) / 128, 128, 0, st>>>((const double2*)tw64, (TwDF*)twdf, n);
+    return (int)cudaGetLastError();
+}
+__global__ void k_v_to_df(const double* __restrict__ V, float2* __restrict__ out, long long N) {
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i < N) out[i] = df_split(V[i]);
+}
+int launch_v_to_df(const void* V, void* Vdf, long long N, cudaStream_t st) {
+    k_v_to_df<<<(unsigned)((N + 255) / 256), 256, 0, st>>>((const double*)V, (float2*)Vdf, N);
+    return (int)cudaGetLastError();
+}
+
 bool has_ct(int n) {
     switch (n) {
 #define VLOC_CASE(N) case N:
@@ -116,6 +137,12 @@ bool has_ct(int n) {
 
 int launch_k1_scatter_zpass(int dbl, int fast, const DevTables& t, const LaunchAxes& ax, const void* tw3,
                             const void* coeffs, long long nb, void* cyl, cudaStream_t st) {
+    if (dbl && fast == 2) switch (t.n3) {
+#define VLOC_CASE(N) case N: return LaunchDF<N>::k1(t, tw3, coeffs, nb, cyl, st);
+        VLOC_CT_SIZES(VLOC_CASE)
+#undef VLOC_CASE
+        default: return (int)cudaErrorInvalidValue;
+    }
     if (!dbl && fast) switch (t.n3) {
 #define VLOC_CASE(N) case N: return LaunchCT<float, N>::k1(t, tw3, coeffs, nb, cyl, st);
         VLOC_CT_SIZES(VLOC_CASE)
@@ -126,6 +153,12 @@ int launch_k1_scatter_zpass(int dbl, int fast, const DevTables& t, const LaunchA
 }
 int launch_k2_ypass(int dbl, int fast, int sign, const DevTables& t, const LaunchAxes& ax, const void* tw2,
                     long long nb, void* cyl, void* slab, cudaStream_t st) {
+    if (dbl && fast == 2) switch (t.n2) {
+#define VLOC_CASE(N) case N: return LaunchDF<N>::k2(sign, t, tw2, nb, cyl, slab, st);
+        VLOC_CT_SIZES(VLOC_CASE)
+#undef VLOC_CASE
+        default: return (int)cudaErrorInvalidValue;
+    }
     // the compile-time y- and x-passes move line pairs along z as 16-byte
     // vectors, which needs an even n3 (every pair then starts on an even
     // element); odd n3 takes the runtime-radix kernels
@@ -140,6 +173,12 @@ int launch_k2_ypass(int dbl, int fast, int sign, const DevTables& t, const Launc
 }
 int launch_k3_xpass_v(int dbl, int fast, const DevTables& t, const LaunchAxes& ax, const void* tw1, const void* V,
                       long long nb, void* slab, cudaStream_t st) {
+    if (dbl && fast == 2) switch (t.n1) {  // V: hi + lo pairs
+#define VLOC_CASE(N) case N: return LaunchDF<N>::k3(t, tw1, V, nb, slab, st);
+        VLOC_CT_SIZES(VLOC_CASE)
+#undef VLOC_CASE
+        default: return (int)cudaErrorInvalidValue;
+    }
     // the compile-time x-pass reads V two lines at a time (8-byte loads)
     if (!dbl && fast && (t.n3 & 1) == 0 && ((uintptr_t)V & 7) == 0) switch (t.n1) {
 #define VLOC_CASE(N) case N: return LaunchCT<float, N>::k3(t, tw1, V, nb, slab, st);
@@ -152,6 +191,12 @@ int launch_k3_xpass_v(int dbl, int fast, const DevTables& t, const LaunchAxes& a
 int launch_k4_zpass_gather(int dbl, int fast, const DevTables& t, const LaunchAxes& ax, const void* tw3,
                            const void* cyl, long long nb, void* out, const void* diag, const void* cin,
                            cudaStream_t st) {
+    if (dbl && fast == 2) switch (t.n3) {
+#define VLOC_CASE(N) case N: return LaunchDF<N>::k4(t, tw3, cyl, nb, out, diag, cin, st);
+        VLOC_CT_SIZES(VLOC_CASE)
+#undef VLOC_CASE
+        default: return (int)cudaErrorInvalidValue;
+    }
     if (!dbl && fast) switch (t.n3) {
 #define VLOC_CASE(N) case N: return LaunchCT<float, N>::k4(t, tw3, cyl, nb, out, diag, cin, st);
         VLOC_CT_SIZES(VLOC_CASE)

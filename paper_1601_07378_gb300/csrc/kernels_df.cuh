@@ -1,0 +1,307 @@
+// kernels_df.cuh -- the chain for FP64 data computed in double-float
+// arithmetic on the FP32 pipes (the double-float plan option).
+//
+// GB300's FP64 rate is a small fraction of its FP32 rate, so an FP64 chain is
+// bound by its FP64 instructions.  Here the coefficients and the result stay
+// FP64 in memory, while every transform runs on complex values whose parts
+// are hi + lo pairs of FP32 (DFc, fft_core.cuh; the real and imaginary
+// parts' operations paired in FP32 instructions): about 48 significant bits,
+// the accuracy of an FP64 FFT to within a few units of 2^-48.  Each lane
+// carries one line per slot, so a tile is 16 lines (z-pass: half of a
+// 32-stick plan tile per CTA; y/x-passes: 16 consecutive z).  The cylinder
+// and slab hold DFc (16 bytes, the size of an FP64 complex), V is converted
+// to hi + lo once per call, and only the scatter and the gather convert
+// between FP64 and double-float.  Same Stockham stages and compile-time
+// schedules as the FP32 lane-pair kernels (fft_ct.cuh).
+#pragma once
+
+#include "fft_ct.cuh"
+#include "kernels_impl.cuh"
+
+namespace vloc {
+
+constexpr int kLinesDF = 16;
+
+// lane roles as in the FP32 lane-pair kernels: slot = line, two unit halves
+__device__ __forceinline__ int slot_of_df() { return threadIdx.x & 15; }
+__device__ __forceinline__ int sub_of_df() { return (threadIdx.x >> 4) & 1; }
+__device__ __forceinline__ int warp_of_df() { return threadIdx.x >> 5; }
+
+template <int N> __host__ __device__ constexpr size_t df_smem() {
+    return (size_t)N * kLdP * sizeof(float2) + (size_t)N * sizeof(TwDF) + (size_t)N * sizeof(int) + 16;
+}
+
+
+// element (row e, line l) of a tile buffer
+__device__ __forceinline__ DFc& df_at(float2* buf, int e, int l) {
+    return *reinterpret_cast<DFc*>(buf + e * kLdP + 2 * l);
+}
+
+__device__ __forceinline__ void load_twdf(TwDF* stw, const TwDF* __restrict__ tw, int n) {
+    for (int j = threadIdx.x; j < n; j += kThreads) stw[j] = tw[j];
+}
+
+// Global row accessors (one DFc per slot)
+struct CylRowsD {  // rows = the plane's sticks (via rowmap), -1 = absent row
+    DFc* cb;
+    const int* rowmap;
+    int n3, z0;
+    __device__ __forceinline__ DFc operator()(int e, int slot) const {
+        const int s = rowmap[e];
+        return s >= 0 ? cb[s * n3 + z0 + slot] : czero<DFc>();
+    }
+    __device__ __forceinline__ void operator()(int e, int slot, DFc v) const {
+        const int s = rowmap[e];
+        if (s >= 0) cb[s * n3 + z0 + slot] = v;
+    }
+};
+struct SlabRowsD {  // every y row of one plane's tile
+    DFc* p;         // slab[b][plane][0][z0]
+    int n3;
+    __device__ __forceinline__ DFc operator()(int e, int slot) const { return p[e * n3 + slot]; }
+    __device__ __forceinline__ void operator()(int e, int slot, DFc v) const { p[e * n3 + slot] = v; }
+};
+struct XRowsD {  // x rows at fixed y: the occupied planes
+    DFc* sb;     // slab[b][0][y][z0]
+    const int* xrow;
+    int pstride;
+    __device__ __forceinline__ DFc operator()(int e, int slot) const {
+        const int p = xrow[e];
+        return p >= 0 ? sb[p * pstride + slot] : czero<DFc>();
+    }
+    __device__ __forceinline__ void operator()(int e, int slot, DFc v) const {
+        const int p = xrow[e];
+        if (p >= 0) sb[p * pstride + slot] = v;
+    }
+};
+
+// ------------------------------------------------------------------ K1
+// CTA (tile, band, half): lines [16 half, 16 half + 16) of the plan tile.
+template <int N>
+__global__ void __launch_bounds__(kThreads) k1_df(DevTables t, const TwDF* __restrict__ tw3,
+                                                 const double2* __restrict__ coeffs, DFc* __restrict__ cyl) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float2* buf = reinterpret_cast<float2*>(smem_raw);
+    TwDF* stw = reinterpret_cast<TwDF*>(buf + N * kLdP);
+    const int tile = blockIdx.x;
+    const long long b = blockIdx.y;
+    const int l0 = kLinesDF * (int)blockIdx.z;
+    const int s0 = t.tile_ptr[tile] + l0;
+    const int lines = min(kLinesDF, t.tile_ptr[tile + 1] - s0);
+    if (lines <= 0) return;  // uniform over the CTA
+    load_twdf(stw, tw3, N);
+    for (int i = threadIdx.x; i < N * kLdP / 2; i += kThreads)
+        reinterpret_cast<float4*>(buf)[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    __syncthreads();
+    const double2* c = coeffs + b * t.npw;
+    for (int e = t.tile_pw_ptr[tile] + (int)threadIdx.x; e < t.tile_pw_ptr[tile + 1]; e += kThreads) {
+        const int2 en = t.tile_pw[e];
+        const int l = (en.y >> 16) - l0;
+        if (l >= 0 && l < kLinesDF) df_at(buf, en.y & 0xffff, l) = df_from(c[en.x]);
+    }
+    __syncthreads();
+    fft_ct<N, +1, kWarps, false, true, true, DFc, TwDF>(stw, SmemT<DFc>{buf}, SmemT<DFc>{buf}, buf, slot_of_df(),
+                                                       sub_of_df(), warp_of_df(), slot_of_df() < lines);
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    for (int l = threadIdx.x >> 5; l < lines; l += kWarps) {
+        DFc* row = cyl + (b * t.S + t.tile_sticks[s0 + l]) * (long long)N;
+        for (int z = lane; z < N; z += 32) row[z] = df_at(buf, z, l);
+    }
+}
+
+// ------------------------------------------------------------------ K2
+template <int S, int N>
+__global__ void __launch_bounds__(kThreads) k2_df(DevTables t, const TwDF* __restrict__ tw2, DFc* cyl, DFc* slab) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int n3 = t.n3;
+    float2* buf = reinterpret_cast<float2*>(smem_raw);
+    TwDF* stw = reinterpret_cast<TwDF*>(buf + N * kLdP);
+    int* rowmap = reinterpret_cast<int*>(stw + N);
+    const int plane = blockIdx.x;
+    const int z0 = blockIdx.y * kLinesDF;
+    const long long b = blockIdx.z;
+    const int lines = min(kLinesDF, n3 - z0);
+    load_twdf(stw, tw2, N);
+    for (int e = threadIdx.x; e < N; e += kThreads) rowmap[e] = -1;
+    __syncthreads();
+    for (int s = t.plane_ptr[plane] + threadIdx.x; s < t.plane_ptr[plane + 1]; s += kThreads) rowmap[t.stick_row[s]] = s;
+    __syncthreads();
+    CylRowsD cr{cyl + b * (long long)t.S * n3, rowmap, n3, z0};
+    SlabRowsD sr{slab + ((b * t.NP + plane) * (long long)N) * n3 + z0, n3};
+    const bool act = slot_of_df() < lines;
+    if constexpr (S > 0)
+        fft_ct<N, +1, kWarps, false, false, false, DFc, TwDF>(stw, cr, sr, buf, slot_of_df(), sub_of_df(), warp_of_df(),
+                                                             act);
+    else
+        fft_ct<N, -1, kWarps, false, false, false, DFc, TwDF>(stw, sr, cr, buf, slot_of_df(), sub_of_df(), warp_of_df(),
+                                                             act);
+}
+
+// ------------------------------------------------------------------ K3
+// x-pass, x V(r) (V as hi + lo pairs), x-return; the last inverse stage, the
+// multiply and the first forward stage of the reversed schedule in registers.
+template <int N>
+__global__ void __launch_bounds__(kThreads) k3_df(DevTables t, const TwDF* __restrict__ tw1,
+                                                 const float2* __restrict__ Vdf, DFc* slab) {
+    using SC = Sched<N>;
+    constexpr int nst = SC::nst;
+    static_assert(nst >= 2, "compile-time x-pass needs at least two stages");
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int n2 = t.n2, n3 = t.n3;
+    float2* buf = reinterpret_cast<float2*>(smem_raw);
+    TwDF* stw = reinterpret_cast<TwDF*>(buf + N * kLdP);
+    int* xrow = reinterpret_cast<int*>(stw + N);
+    const int slot = slot_of_df(), sub = sub_of_df(), warp = warp_of_df();
+    const int y = blockIdx.x;
+    const int z0 = blockIdx.y * kLinesDF;
+    const long long b = blockIdx.z;
+    const int lines = min(kLinesDF, n3 - z0);
+    const bool act = slot < lines;
+    load_twdf(stw, tw1, N);
+    for (int e = threadIdx.x; e < N; e += kThreads) xrow[e] = t.xrow_plane[e];
+    __syncthreads();
+    const int pstride = n2 * n3;
+    XRowsD xr{slab + b * t.NP * (long long)pstride + y * n3 + z0, xrow, pstride};
+    const float2* vrow = Vdf + (long long)y * n3 + z0 + slot;
+    SmemT<DFc> sb{buf};
+
+    NatStage<N, +1, kWarps, 0, DFc, TwDF>::template run<false>(stw, xr, sb, slot, sub, warp, act);
+    __syncthreads();
+    if constexpr (nst >= 3) {
+        NatStage<N, +1, kWarps, 1, DFc, TwDF>::template run<true>(stw, sb, sb, slot, sub, warp, act);
+        __syncthreads();
+    }
+    if constexpr (nst >= 4) {
+        NatStage<N, +1, kWarps, 2, DFc, TwDF>::template run<true>(stw, sb, sb, slot, sub, warp, act);
+        __syncthreads();
+    }
+    using L = NatStage<N, +1, kWarps, nst - 1, DFc, TwDF>;
+    using F = RevStage<N, -1, kWarps, 0, DFc, TwDF>;
+    constexpr int R = SC::R(nst - 1);
+    static_assert(F::NI == L::NI && SC::RR(0) == R, "chained stages must share units");
+    DFc h[L::U][R];
+    if (act) {
+        L::compute(h, stw, sb, slot, sub, warp);
+#pragma unroll
+        for (int u = 0; u < L::U; ++u) {
+            const int i = 2 * (warp + u * kWarps) + sub;
+            if (L::NI % (2 * kWarps) == 0 || i < L::NI) {
+#pragma unroll
+                for (int r = 0; r < R; ++r) {
+                    const float2 w = vrow[(i + r * L::NI) * pstride];  // V as (hi, lo)
+                    h[u][r] = df2_mul(h[u][r], make_float2(w.x, w.x), make_float2(w.y, w.y));
+                }
+                Dft<R, -1>::run(h[u]);
+            }
+        }
+    }
+    __syncthreads();
+    if (act) F::store(h, sb, slot, sub, warp);
+    __syncthreads();
+    if constexpr (nst >= 3) {
+        RevStage<N, -1, kWarps, 1, DFc, TwDF>::template run<true>(stw, sb, sb, slot, sub, warp, act);
+        __syncthreads();
+    }
+    if constexpr (nst >= 4) {
+        RevStage<N, -1, kWarps, 2, DFc, TwDF>::template run<true>(stw, sb, sb, slot, sub, warp, act);
+        __syncthreads();
+    }
+    RevStage<N, -1, kWarps, nst - 1, DFc, TwDF>::template run<false>(stw, sb, xr, slot, sub, warp, act);
+}
+
+// ------------------------------------------------------------------ K4
+template <int N>
+__global__ void __launch_bounds__(kThreads) k4_df(DevTables t, const TwDF* __restrict__ tw3,
+                                                 const DFc* __restrict__ cyl, double2* out, double scale,
+                                                 const double* __restrict__ diag, const double2* cin) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float2* buf = reinterpret_cast<float2*>(smem_raw);
+    TwDF* stw = reinterpret_cast<TwDF*>(buf + N * kLdP);
+    const int tile = blockIdx.x;
+    const long long b = blockIdx.y;
+    const int l0 = kLinesDF * (int)blockIdx.z;
+    const int s0 = t.tile_ptr[tile] + l0;
+    const int lines = min(kLinesDF, t.tile_ptr[tile + 1] - s0);
+    if (lines <= 0) return;  // uniform over the CTA
+    load_twdf(stw, tw3, N);
+    const int lane = threadIdx.x & 31;
+    for (int l = threadIdx.x >> 5; l < lines; l += kWarps) {
+        const DFc* row = cyl + (b * t.S + t.tile_sticks[s0 + l]) * (long long)N;
+        for (int z = lane; z < N; z += 32) df_at(buf, z, l) = row[z];
+    }
+    __syncthreads();
+    fft_ct<N, -1, kWarps, false, true, true, DFc, TwDF>(stw, SmemT<DFc>{buf}, SmemT<DFc>{buf}, buf, slot_of_df(),
+                                                       sub_of_df(), warp_of_df(), slot_of_df() < lines);
+    __syncthreads();
+    const float2 sc = df_split(scale);
+    double2* o = out + b * t.npw;
+    const double2* ci = diag ? cin + b * t.npw : cin;
+    for (int e = t.tile_pw_ptr[tile] + (int)threadIdx.x; e < t.tile_pw_ptr[tile + 1]; e += kThreads) {
+        const int2 en = t.tile_pw[e];
+        const int l = (en.y >> 16) - l0;
+        if (l < 0 || l >= kLinesDF) continue;
+        const DFc v = df_at(buf, en.y & 0xffff, l);
+        double2 r = df_to(df2_mul(v, make_float2(sc.x, sc.x), make_float2(sc.y, sc.y)));
+        if (diag) {  // H = diag + A (c is read before out is written: they may alias)
+            const double d = diag[en.x];
+            const double2 cc = ci[en.x];
+            r.x += d * cc.x;
+            r.y += d * cc.y;
+        }
+        o[en.x] = r;
+    }
+}
+
+// ------------------------------------------------------------ launchers
+template <int N> struct DfSmem {
+    static constexpr size_t sm = df_smem<N>();
+    template <class K> static cudaError_t ensure(K kernel) {
+        if (sm <= 48 * 1024) return cudaSuccess;
+        return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    }
+};
+
+template <int N>
+int LaunchDF<N>::k1(const DevTables& t, const void* tw3, const void* coeffs, long long nb, void* cyl, cudaStream_t st) {
+    static const cudaError_t once = DfSmem<N>::ensure(k1_df<N>);
+    if (once) return (int)once;
+    k1_df<N><<<dim3(t.T, (unsigned)nb, 2), kThreads, DfSmem<N>::sm, st>>>(t, (const TwDF*)tw3, (const double2*)coeffs,
+                                                                          (DFc*)cyl);
+    return (int)cudaGetLastError();
+}
+template <int N>
+int LaunchDF<N>::k2(int sign, const DevTables& t, const void* tw2, long long nb, void* cyl, void* slab,
+                    cudaStream_t st) {
+    const dim3 grid(t.NP, (t.n3 + kLinesDF - 1) / kLinesDF, (unsigned)nb);
+    if (sign > 0) {
+        static const cudaError_t once = DfSmem<N>::ensure(k2_df<+1, N>);
+        if (once) return (int)once;
+        k2_df<+1, N><<<grid, kThreads, DfSmem<N>::sm, st>>>(t, (const TwDF*)tw2, (DFc*)cyl, (DFc*)slab);
+    } else {
+        static const cudaError_t once = DfSmem<N>::ensure(k2_df<-1, N>);
+        if (once) return (int)once;
+        k2_df<-1, N><<<grid, kThreads, DfSmem<N>::sm, st>>>(t, (const TwDF*)tw2, (DFc*)cyl, (DFc*)slab);
+    }
+    return (int)cudaGetLastError();
+}
+template <int N>
+int LaunchDF<N>::k3(const DevTables& t, const void* tw1, const void* Vdf, long long nb, void* slab, cudaStream_t st) {
+    static const cudaError_t once = DfSmem<N>::ensure(k3_df<N>);
+    if (once) return (int)once;
+    const dim3 grid(t.n2, (t.n3 + kLinesDF - 1) / kLinesDF, (unsigned)nb);
+    k3_df<N><<<grid, kThreads, DfSmem<N>::sm, st>>>(t, (const TwDF*)tw1, (const float2*)Vdf, (DFc*)slab);
+    return (int)cudaGetLastError();
+}
+template <int N>
+int LaunchDF<N>::k4(const DevTables& t, const void* tw3, const void* cyl, long long nb, void* out, const void* diag,
+                    const void* cin, cudaStream_t st) {
+    static const cudaError_t once = DfSmem<N>::ensure(k4_df<N>);
+    if (once) return (int)once;
+    const double scale = 1.0 / ((double)t.n1 * t.n2 * t.n3);
+    k4_df<N><<<dim3(t.T, (unsigned)nb, 2), kThreads, DfSmem<N>::sm, st>>>(
+        t, (const TwDF*)tw3, (const DFc*)cyl, (double2*)out, scale, (const double*)diag, (const double2*)cin);
+    return (int)cudaGetLastError();
+}
+
+}  // namespace vloc

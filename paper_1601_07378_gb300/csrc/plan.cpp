@@ -111,6 +111,9 @@ struct vloc_plan_s {
     long long npw = 0, N = 0;
     int S = 0, NP = 0, P = 0, T = 0;
     int fast = 1;  // compile-time-length kernels where available
+    bool df = false;            // FP64 apply in double-float arithmetic
+    void* d_twdf[3] = {nullptr, nullptr, nullptr};  // TwDF tables per axis
+    void* d_vdf = nullptr;      // V as hi + lo pairs [N]
     bool gamma = false;       // Gamma-point real mode (half-sphere coefficients)
     long long npw_user = 0;   // plane waves per band in the caller's arrays
     int* d_gamma_neg = nullptr;  // full-list index of -G for each caller G
@@ -189,6 +192,8 @@ static void free_plan(vloc_plan p) {
     cudaFree(p->d_slab);
     cudaFree(p->d_acc);
     cudaFree(p->d_gamma_neg);
+    for (int a = 0; a < 3; ++a) cudaFree(p->d_twdf[a]);
+    cudaFree(p->d_vdf);
     cudaFree(p->d_gamma_buf);
     cudaFree(p->d_stage);
     for (cudaEvent_t e : p->prof_pool) cudaEventDestroy(e);
@@ -215,7 +220,9 @@ int vloc_plan_create(vloc_plan* out, int n1, int n2, int n3, const int32_t* g, i
     const int part_flag = flags & 0x0F0;
     if (part_flag != VLOC_PARTITION_GREEDY && part_flag != VLOC_PARTITION_BASIC && part_flag != VLOC_PARTITION_IMPROVED)
         return VLOC_ERR_ARG;
-    if (flags & ~(0x003 | 0x0F0 | VLOC_GRAPH | VLOC_HOST_ONLY | VLOC_GENERIC_KERNELS | VLOC_GAMMA)) return VLOC_ERR_ARG;
+    if (flags & ~(0x003 | 0x0F0 | VLOC_GRAPH | VLOC_HOST_ONLY | VLOC_GENERIC_KERNELS | VLOC_GAMMA | VLOC_DOUBLE_FLOAT))
+        return VLOC_ERR_ARG;
+    if ((flags & VLOC_DOUBLE_FLOAT) && prec != VLOC_F64) return VLOC_ERR_ARG;
     const bool host_only = (flags & VLOC_HOST_ONLY) != 0;
     const int ns[3] = {n1, n2, n3};
     for (int a = 0; a < 3; ++a)
@@ -253,6 +260,7 @@ int vloc_plan_create(vloc_plan* out, int n1, int n2, int n3, const int32_t* g, i
     p->gamma = (flags & VLOC_GAMMA) != 0;
     p->elem = elem;
     p->fast = (flags & VLOC_GENERIC_KERNELS) ? 0 : 1;
+    p->df = (flags & VLOC_DOUBLE_FLOAT) && !(flags & VLOC_GENERIC_KERNELS) && has_df(n1) && has_df(n2) && has_df(n3);
     for (int a = 0; a < 3; ++a) {
         p->ax.n[a] = ns[a];
         if (!plan_radices(ns[a], &p->ax.nst[a], p->ax.radix[a])) { free_plan(p); return VLOC_ERR_SIZE; }
@@ -425,6 +433,13 @@ int vloc_plan_create(vloc_plan* out, int n1, int n2, int n3, const int32_t* g, i
         if (launch_twiddles(dbl, p->d_tw[a], ns[a], st)) { free_plan(p); return cuda_fail(cudaGetLastError(), "twiddles"); }
     }
     if ((e = (cudaError_t)set_smem_limits(dbl, nmax, maxopt))) { free_plan(p); return cuda_fail(e, "cudaFuncSetAttribute"); }
+    if (p->df) {
+        for (int a = 0; a < 3; ++a) {
+            if ((e = cudaMalloc(&p->d_twdf[a], (size_t)ns[a] * 32))) { free_plan(p); return cuda_fail(e, "cudaMalloc(df twiddles)"); }
+            if (launch_twiddles_df(p->d_tw[a], p->d_twdf[a], ns[a], st)) { free_plan(p); return cuda_fail(cudaGetLastError(), "df twiddles"); }
+        }
+        if ((e = cudaMalloc(&p->d_vdf, (size_t)N * 8))) { free_plan(p); return cuda_fail(e, "cudaMalloc(df V)"); }
+    }
 
     // ---- workspace: cylinder [chunk][S][n3] + slab [chunk][NP][n2][n3]
     const size_t per_band = ((size_t)S * n3 + (size_t)NP * n2 * n3) * elem;
@@ -474,6 +489,7 @@ int vloc_plan_set_schedule(vloc_plan p, int axis, int nst, const int32_t* radix)
     p->ax.nst[axis] = nst;
     for (int i = 0; i < 4; ++i) p->ax.radix[axis][i] = i < nst ? radix[i] : 0;
     p->fast = 0;
+    p->df = false;
     for (auto& g : p->graphs)
         if (g.exec) cudaGraphExecDestroy(g.exec);
     p->graphs.clear();
@@ -543,6 +559,22 @@ static int apply_impl(vloc_plan p, const void* c, const void* V, int64_t nb, voi
     const int dbl = p->dbl;
     const DevTables& t = p->dt;
     const LaunchAxes& ax = p->ax;
+    if (p->df) {
+        // double-float chain: its own twiddle tables, V as hi + lo pairs
+        int rc;
+        if ((rc = launch(p, KK_AUX, st, [&] { return launch_v_to_df(V, p->d_vdf, p->N, st); }))) return rc;
+        for (int64_t b0 = 0; b0 < nb; b0 += p->chunk) {
+            const long long cb = std::min<long long>(p->chunk, nb - b0);
+            const void* cc = (const char*)c + b0 * bstride;
+            void* oo = (char*)out + b0 * bstride;
+            if ((rc = launch(p, KK_SCATTER_Z, st, [&] { return launch_k1_scatter_zpass(1, 2, t, ax, p->d_twdf[2], cc, cb, p->d_cyl, st); }))) return rc;
+            if ((rc = launch(p, KK_Y_INV, st, [&] { return launch_k2_ypass(1, 2, +1, t, ax, p->d_twdf[1], cb, p->d_cyl, p->d_slab, st); }))) return rc;
+            if ((rc = launch(p, KK_X_V, st, [&] { return launch_k3_xpass_v(1, 2, t, ax, p->d_twdf[0], p->d_vdf, cb, p->d_slab, st); }))) return rc;
+            if ((rc = launch(p, KK_Y_FWD, st, [&] { return launch_k2_ypass(1, 2, -1, t, ax, p->d_twdf[1], cb, p->d_cyl, p->d_slab, st); }))) return rc;
+            if ((rc = launch(p, KK_Z_GATHER, st, [&] { return launch_k4_zpass_gather(1, 2, t, ax, p->d_twdf[2], p->d_cyl, cb, oo, diag, cc, st); }))) return rc;
+        }
+        return VLOC_OK;
+    }
     for (int64_t b0 = 0; b0 < nb; b0 += p->chunk) {
         const long long cb = std::min<long long>(p->chunk, nb - b0);
         const void* cc = (const char*)c + b0 * bstride;
@@ -1050,7 +1082,7 @@ int vloc_get_info(vloc_plan p, vloc_info* info) {
     info->npw = p->npw_user;
     info->nsticks = p->S; info->nplanes = p->NP; info->nparts = p->P;
     info->lines_per_tile = kLinesPerTile;
-    info->path = (p->fast ? 1 : 0) | (p->gamma ? 4 : 0);
+    info->path = (p->fast ? 1 : 0) | (p->gamma ? 4 : 0) | (p->df ? 8 : 0);
     info->chunk_bands = p->chunk;
     info->workspace_bytes = (int64_t)p->ws_bytes;
     for (int a = 0; a < 3; ++a) {

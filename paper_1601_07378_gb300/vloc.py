@@ -35,6 +35,7 @@ VLOC_GRAPH = 0x100
 VLOC_HOST_ONLY = 0x200
 VLOC_GENERIC_KERNELS = 0x400
 VLOC_GAMMA = 0x1000
+VLOC_DOUBLE_FLOAT = 0x2000
 
 # every exported symbol declared in include/vloc.h
 EXPORTS = [
@@ -154,6 +155,8 @@ class VlocPlan:
 
     ``glist`` is an int array [npw, 3] of Miller indices; ``dtype`` is
     ``torch.complex64`` (FP32 path) or ``torch.complex128`` (FP64 path).
+    ``double_float=True`` (with complex128) runs the apply in double-float
+    arithmetic on the FP32 pipes, FP64 data in and out.
     ``gamma=True`` selects the Gamma-point real mode (Sec. 4.3): ``glist`` is
     half of a G -> -G symmetric sphere, the bands are real in r-space
     (c(-G) = conj c(G) implied, c(0) taken real) and two of them share one
@@ -162,7 +165,7 @@ class VlocPlan:
 
     def __init__(self, grid, glist, dtype=None, *, partition: str = "greedy", chunk: int = 0,
                  graph: bool = False, host_only: bool = False, generic: bool = False, gamma: bool = False,
-                 stream=None):
+                 double_float: bool = False, stream=None):
         import torch
         dtype = dtype or torch.complex64
         if dtype not in (torch.complex64, torch.complex128):
@@ -186,6 +189,8 @@ class VlocPlan:
         self.gamma = bool(gamma)
         if gamma:
             flags |= VLOC_GAMMA
+        if double_float:
+            flags |= VLOC_DOUBLE_FLOAT
         h = ctypes.c_void_p()
         sp = ctypes.c_void_p(None) if host_only else _stream_ptr(stream)
         _check(self.lib.vloc_plan_create(ctypes.byref(h), *self.grid,
@@ -222,6 +227,7 @@ class VlocPlan:
             "radix": [[inf.radix[a][i] for i in range(inf.nstages[a])] for a in range(3)],
             "compile_time_kernels": bool(inf.path & 1),
             "gamma": bool(inf.path & 4),
+            "double_float": bool(inf.path & 8),
         }
 
     def set_schedule(self, axis: int, radices):
