@@ -87,13 +87,16 @@ template <typename T, int N> struct LaunchCT {
                    long long b_base, int pair, long long nreal, double* partial, cudaStream_t st);
 };
 
-// Double-float launchers (kernels_df.cuh) for the same lengths, FP64 data:
-// twiddle tables are TwDF [n], V is hi + lo pairs [N], the cylinder and slab
-// hold double-float complex values (16 bytes).
-template <int N> struct LaunchDF {
+// Compile-time-length launchers for FP64 data (kernels_df.cuh), one value
+// per lane slot, 16-line tiles, for the lengths of VLOC_CT_SIZES.  P = 0:
+// double-float arithmetic (twiddle tables TwDF [n], V as hi + lo pairs [N],
+// cylinder and slab of 16-byte double-float values); P = 1: native FP64
+// (twiddles and V as the plan's FP64 tables, double2 cylinder and slab, the
+// layout the runtime-radix FP64 kernels use).
+template <int P, int N> struct LaunchF64 {
     static int k1(const DevTables& t, const void* tw3, const void* coeffs, long long nb, void* cyl, cudaStream_t st);
     static int k2(int sign, const DevTables& t, const void* tw2, long long nb, void* cyl, void* slab, cudaStream_t st);
-    static int k3(const DevTables& t, const void* tw1, const void* Vdf, long long nb, void* slab, cudaStream_t st);
+    static int k3(const DevTables& t, const void* tw1, const void* V, long long nb, void* slab, cudaStream_t st);
     static int k4(const DevTables& t, const void* tw3, const void* cyl, long long nb, void* out, const void* diag,
                   const void* cin, cudaStream_t st);
 };
@@ -103,9 +106,9 @@ int launch_twiddles_df(const void* tw64, void* twdf, int n, cudaStream_t st);
 int launch_v_to_df(const void* V, void* Vdf, long long N, cudaStream_t st);
 
 // Precision dispatch (kernels.cu): dbl = 0 for float, 1 for double; `fast`
-// selects the compile-time-length kernels when one exists for the axis (FP32),
-// and fast = 2 with dbl = 1 the double-float kernels (every axis must have
-// them: the caller checks has_df).
+// selects the compile-time-length kernels when one exists for the axis (FP32
+// and native FP64), and fast = 2 with dbl = 1 the double-float kernels (every
+// axis must have them: the caller checks has_df).
 int launch_twiddles(int dbl, void* tw, int n, cudaStream_t st);
 int launch_k1_scatter_zpass(int dbl, int fast, const DevTables& t, const LaunchAxes& ax, const void* tw3, const void* coeffs,
                             long long nb, void* cyl, cudaStream_t st);

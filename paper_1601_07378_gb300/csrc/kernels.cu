@@ -138,10 +138,16 @@ bool has_ct(int n) {
 int launch_k1_scatter_zpass(int dbl, int fast, const DevTables& t, const LaunchAxes& ax, const void* tw3,
                             const void* coeffs, long long nb, void* cyl, cudaStream_t st) {
     if (dbl && fast == 2) switch (t.n3) {
-#define VLOC_CASE(N) case N: return LaunchDF<N>::k1(t, tw3, coeffs, nb, cyl, st);
+#define VLOC_CASE(N) case N: return LaunchF64<0, N>::k1(t, tw3, coeffs, nb, cyl, st);
         VLOC_CT_SIZES(VLOC_CASE)
 #undef VLOC_CASE
         default: return (int)cudaErrorInvalidValue;
+    }
+    if (dbl && fast == 1) switch (t.n3) {
+#define VLOC_CASE(N) case N: return LaunchF64<1, N>::k1(t, tw3, coeffs, nb, cyl, st);
+        VLOC_CT_SIZES(VLOC_CASE)
+#undef VLOC_CASE
+        default: break;
     }
     if (!dbl && fast) switch (t.n3) {
 #define VLOC_CASE(N) case N: return LaunchCT<float, N>::k1(t, tw3, coeffs, nb, cyl, st);
@@ -154,10 +160,16 @@ int launch_k1_scatter_zpass(int dbl, int fast, const DevTables& t, const LaunchA
 int launch_k2_ypass(int dbl, int fast, int sign, const DevTables& t, const LaunchAxes& ax, const void* tw2,
                     long long nb, void* cyl, void* slab, cudaStream_t st) {
     if (dbl && fast == 2) switch (t.n2) {
-#define VLOC_CASE(N) case N: return LaunchDF<N>::k2(sign, t, tw2, nb, cyl, slab, st);
+#define VLOC_CASE(N) case N: return LaunchF64<0, N>::k2(sign, t, tw2, nb, cyl, slab, st);
         VLOC_CT_SIZES(VLOC_CASE)
 #undef VLOC_CASE
         default: return (int)cudaErrorInvalidValue;
+    }
+    if (dbl && fast == 1) switch (t.n2) {
+#define VLOC_CASE(N) case N: return LaunchF64<1, N>::k2(sign, t, tw2, nb, cyl, slab, st);
+        VLOC_CT_SIZES(VLOC_CASE)
+#undef VLOC_CASE
+        default: break;
     }
     // the compile-time y- and x-passes move line pairs along z as 16-byte
     // vectors, which needs an even n3 (every pair then starts on an even
@@ -174,10 +186,16 @@ int launch_k2_ypass(int dbl, int fast, int sign, const DevTables& t, const Launc
 int launch_k3_xpass_v(int dbl, int fast, const DevTables& t, const LaunchAxes& ax, const void* tw1, const void* V,
                       long long nb, void* slab, cudaStream_t st) {
     if (dbl && fast == 2) switch (t.n1) {  // V: hi + lo pairs
-#define VLOC_CASE(N) case N: return LaunchDF<N>::k3(t, tw1, V, nb, slab, st);
+#define VLOC_CASE(N) case N: return LaunchF64<0, N>::k3(t, tw1, V, nb, slab, st);
         VLOC_CT_SIZES(VLOC_CASE)
 #undef VLOC_CASE
         default: return (int)cudaErrorInvalidValue;
+    }
+    if (dbl && fast == 1) switch (t.n1) {
+#define VLOC_CASE(N) case N: return LaunchF64<1, N>::k3(t, tw1, V, nb, slab, st);
+        VLOC_CT_SIZES(VLOC_CASE)
+#undef VLOC_CASE
+        default: break;
     }
     // the compile-time x-pass reads V two lines at a time (8-byte loads)
     if (!dbl && fast && (t.n3 & 1) == 0 && ((uintptr_t)V & 7) == 0) switch (t.n1) {
@@ -192,10 +210,16 @@ int launch_k4_zpass_gather(int dbl, int fast, const DevTables& t, const LaunchAx
                            const void* cyl, long long nb, void* out, const void* diag, const void* cin,
                            cudaStream_t st) {
     if (dbl && fast == 2) switch (t.n3) {
-#define VLOC_CASE(N) case N: return LaunchDF<N>::k4(t, tw3, cyl, nb, out, diag, cin, st);
+#define VLOC_CASE(N) case N: return LaunchF64<0, N>::k4(t, tw3, cyl, nb, out, diag, cin, st);
         VLOC_CT_SIZES(VLOC_CASE)
 #undef VLOC_CASE
         default: return (int)cudaErrorInvalidValue;
+    }
+    if (dbl && fast == 1) switch (t.n3) {
+#define VLOC_CASE(N) case N: return LaunchF64<1, N>::k4(t, tw3, cyl, nb, out, diag, cin, st);
+        VLOC_CT_SIZES(VLOC_CASE)
+#undef VLOC_CASE
+        default: break;
     }
     if (!dbl && fast) switch (t.n3) {
 #define VLOC_CASE(N) case N: return LaunchCT<float, N>::k4(t, tw3, cyl, nb, out, diag, cin, st);

@@ -1,5 +1,7 @@
-// kernels_df.cuh -- the chain for FP64 data computed in double-float
-// arithmetic on the FP32 pipes (the double-float plan option).
+// kernels_df.cuh -- compile-time-length chain kernels for FP64 data, one
+// 16-byte value per lane slot (16-line tiles), in two arithmetics:
+//  * PolNative: FP64 complex values (double2), FP64 instructions;
+//  * PolDF: double-float (the double-float plan option), below.
 //
 // GB300's FP64 rate is a small fraction of its FP32 rate, so an FP64 chain is
 // bound by its FP64 instructions.  Here the coefficients and the result stay
@@ -27,49 +29,74 @@ __device__ __forceinline__ int slot_of_df() { return threadIdx.x & 15; }
 __device__ __forceinline__ int sub_of_df() { return (threadIdx.x >> 4) & 1; }
 __device__ __forceinline__ int warp_of_df() { return threadIdx.x >> 5; }
 
-template <int N> __host__ __device__ constexpr size_t df_smem() {
-    return (size_t)N * kLdP * sizeof(float2) + (size_t)N * sizeof(TwDF) + (size_t)N * sizeof(int) + 16;
+// Arithmetic policies: value type V, twiddle type TW, the V(r) element type
+// VR, and the conversions at the scatter / gather / multiply by V.
+struct PolDF {
+    using V = DFc;
+    using TW = TwDF;
+    using VR = float2;  // V(r) as (hi, lo)
+    __device__ __forceinline__ static DFc from(double2 v) { return df_from(v); }
+    __device__ __forceinline__ static double2 out(DFc v, double scale) {
+        const float2 sc = df_split(scale);
+        return df_to(df2_mul(v, make_float2(sc.x, sc.x), make_float2(sc.y, sc.y)));
+    }
+    __device__ __forceinline__ static DFc mul_v(DFc h, float2 w) {
+        return df2_mul(h, make_float2(w.x, w.x), make_float2(w.y, w.y));
+    }
+};
+struct PolNative {
+    using V = double2;
+    using TW = double2;
+    using VR = double;
+    __device__ __forceinline__ static double2 from(double2 v) { return v; }
+    __device__ __forceinline__ static double2 out(double2 v, double scale) { return cscale(v, scale); }
+    __device__ __forceinline__ static double2 mul_v(double2 h, double w) { return cscale(h, w); }
+};
+template <int P> using PolOf = std::conditional_t<P == 0, PolDF, PolNative>;
+
+template <class Pol, int N> __host__ __device__ constexpr size_t w_smem() {
+    return (size_t)N * kLdP * sizeof(float2) + (size_t)N * sizeof(typename Pol::TW) + (size_t)N * sizeof(int) + 16;
 }
 
 
 // element (row e, line l) of a tile buffer
-__device__ __forceinline__ DFc& df_at(float2* buf, int e, int l) {
-    return *reinterpret_cast<DFc*>(buf + e * kLdP + 2 * l);
+template <class V> __device__ __forceinline__ V& w_at(float2* buf, int e, int l) {
+    return *reinterpret_cast<V*>(buf + e * kLdP + 2 * l);
 }
 
-__device__ __forceinline__ void load_twdf(TwDF* stw, const TwDF* __restrict__ tw, int n) {
+template <class TW> __device__ __forceinline__ void load_tww(TW* stw, const TW* __restrict__ tw, int n) {
     for (int j = threadIdx.x; j < n; j += kThreads) stw[j] = tw[j];
 }
 
 // Global row accessors (one DFc per slot)
-struct CylRowsD {  // rows = the plane's sticks (via rowmap), -1 = absent row
-    DFc* cb;
+template <class V> struct CylRowsD {  // rows = the plane's sticks (via rowmap), -1 = absent row
+    V* cb;
     const int* rowmap;
     int n3, z0;
-    __device__ __forceinline__ DFc operator()(int e, int slot) const {
+    __device__ __forceinline__ V operator()(int e, int slot) const {
         const int s = rowmap[e];
-        return s >= 0 ? cb[s * n3 + z0 + slot] : czero<DFc>();
+        return s >= 0 ? cb[s * n3 + z0 + slot] : czero<V>();
     }
-    __device__ __forceinline__ void operator()(int e, int slot, DFc v) const {
+    __device__ __forceinline__ void operator()(int e, int slot, V v) const {
         const int s = rowmap[e];
         if (s >= 0) cb[s * n3 + z0 + slot] = v;
     }
 };
-struct SlabRowsD {  // every y row of one plane's tile
-    DFc* p;         // slab[b][plane][0][z0]
+template <class V> struct SlabRowsD {  // every y row of one plane's tile
+    V* p;           // slab[b][plane][0][z0]
     int n3;
-    __device__ __forceinline__ DFc operator()(int e, int slot) const { return p[e * n3 + slot]; }
-    __device__ __forceinline__ void operator()(int e, int slot, DFc v) const { p[e * n3 + slot] = v; }
+    __device__ __forceinline__ V operator()(int e, int slot) const { return p[e * n3 + slot]; }
+    __device__ __forceinline__ void operator()(int e, int slot, V v) const { p[e * n3 + slot] = v; }
 };
-struct XRowsD {  // x rows at fixed y: the occupied planes
-    DFc* sb;     // slab[b][0][y][z0]
+template <class V> struct XRowsD {  // x rows at fixed y: the occupied planes
+    V* sb;       // slab[b][0][y][z0]
     const int* xrow;
     int pstride;
-    __device__ __forceinline__ DFc operator()(int e, int slot) const {
+    __device__ __forceinline__ V operator()(int e, int slot) const {
         const int p = xrow[e];
-        return p >= 0 ? sb[p * pstride + slot] : czero<DFc>();
+        return p >= 0 ? sb[p * pstride + slot] : czero<V>();
     }
-    __device__ __forceinline__ void operator()(int e, int slot, DFc v) const {
+    __device__ __forceinline__ void operator()(int e, int slot, V v) const {
         const int p = xrow[e];
         if (p >= 0) sb[p * pstride + slot] = v;
     }
@@ -77,19 +104,21 @@ struct XRowsD {  // x rows at fixed y: the occupied planes
 
 // ------------------------------------------------------------------ K1
 // CTA (tile, band, half): lines [16 half, 16 half + 16) of the plan tile.
-template <int N>
-__global__ void __launch_bounds__(kThreads) k1_df(DevTables t, const TwDF* __restrict__ tw3,
-                                                 const double2* __restrict__ coeffs, DFc* __restrict__ cyl) {
+template <class Pol, int N>
+__global__ void __launch_bounds__(kThreads) k1_w(DevTables t, const typename Pol::TW* __restrict__ tw3,
+                                                const double2* __restrict__ coeffs, typename Pol::V* __restrict__ cyl) {
+    using V = typename Pol::V;
+    using TW = typename Pol::TW;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float2* buf = reinterpret_cast<float2*>(smem_raw);
-    TwDF* stw = reinterpret_cast<TwDF*>(buf + N * kLdP);
+    TW* stw = reinterpret_cast<TW*>(buf + N * kLdP);
     const int tile = blockIdx.x;
     const long long b = blockIdx.y;
     const int l0 = kLinesDF * (int)blockIdx.z;
     const int s0 = t.tile_ptr[tile] + l0;
     const int lines = min(kLinesDF, t.tile_ptr[tile + 1] - s0);
     if (lines <= 0) return;  // uniform over the CTA
-    load_twdf(stw, tw3, N);
+    load_tww(stw, tw3, N);
     for (int i = threadIdx.x; i < N * kLdP / 2; i += kThreads)
         reinterpret_cast<float4*>(buf)[i] = make_float4(0.f, 0.f, 0.f, 0.f);
     __syncthreads();
@@ -97,60 +126,65 @@ __global__ void __launch_bounds__(kThreads) k1_df(DevTables t, const TwDF* __res
     for (int e = t.tile_pw_ptr[tile] + (int)threadIdx.x; e < t.tile_pw_ptr[tile + 1]; e += kThreads) {
         const int2 en = t.tile_pw[e];
         const int l = (en.y >> 16) - l0;
-        if (l >= 0 && l < kLinesDF) df_at(buf, en.y & 0xffff, l) = df_from(c[en.x]);
+        if (l >= 0 && l < kLinesDF) w_at<V>(buf, en.y & 0xffff, l) = Pol::from(c[en.x]);
     }
     __syncthreads();
-    fft_ct<N, +1, kWarps, false, true, true, DFc, TwDF>(stw, SmemT<DFc>{buf}, SmemT<DFc>{buf}, buf, slot_of_df(),
+    fft_ct<N, +1, kWarps, false, true, true, V, TW>(stw, SmemT<V>{buf}, SmemT<V>{buf}, buf, slot_of_df(),
                                                        sub_of_df(), warp_of_df(), slot_of_df() < lines);
     __syncthreads();
     const int lane = threadIdx.x & 31;
     for (int l = threadIdx.x >> 5; l < lines; l += kWarps) {
-        DFc* row = cyl + (b * t.S + t.tile_sticks[s0 + l]) * (long long)N;
-        for (int z = lane; z < N; z += 32) row[z] = df_at(buf, z, l);
+        V* row = cyl + (b * t.S + t.tile_sticks[s0 + l]) * (long long)N;
+        for (int z = lane; z < N; z += 32) row[z] = w_at<V>(buf, z, l);
     }
 }
 
 // ------------------------------------------------------------------ K2
-template <int S, int N>
-__global__ void __launch_bounds__(kThreads) k2_df(DevTables t, const TwDF* __restrict__ tw2, DFc* cyl, DFc* slab) {
+template <class Pol, int S, int N>
+__global__ void __launch_bounds__(kThreads) k2_w(DevTables t, const typename Pol::TW* __restrict__ tw2,
+                                                typename Pol::V* cyl, typename Pol::V* slab) {
+    using V = typename Pol::V;
+    using TW = typename Pol::TW;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int n3 = t.n3;
     float2* buf = reinterpret_cast<float2*>(smem_raw);
-    TwDF* stw = reinterpret_cast<TwDF*>(buf + N * kLdP);
+    TW* stw = reinterpret_cast<TW*>(buf + N * kLdP);
     int* rowmap = reinterpret_cast<int*>(stw + N);
     const int plane = blockIdx.x;
     const int z0 = blockIdx.y * kLinesDF;
     const long long b = blockIdx.z;
     const int lines = min(kLinesDF, n3 - z0);
-    load_twdf(stw, tw2, N);
+    load_tww(stw, tw2, N);
     for (int e = threadIdx.x; e < N; e += kThreads) rowmap[e] = -1;
     __syncthreads();
     for (int s = t.plane_ptr[plane] + threadIdx.x; s < t.plane_ptr[plane + 1]; s += kThreads) rowmap[t.stick_row[s]] = s;
     __syncthreads();
-    CylRowsD cr{cyl + b * (long long)t.S * n3, rowmap, n3, z0};
-    SlabRowsD sr{slab + ((b * t.NP + plane) * (long long)N) * n3 + z0, n3};
+    CylRowsD<V> cr{cyl + b * (long long)t.S * n3, rowmap, n3, z0};
+    SlabRowsD<V> sr{slab + ((b * t.NP + plane) * (long long)N) * n3 + z0, n3};
     const bool act = slot_of_df() < lines;
     if constexpr (S > 0)
-        fft_ct<N, +1, kWarps, false, false, false, DFc, TwDF>(stw, cr, sr, buf, slot_of_df(), sub_of_df(), warp_of_df(),
+        fft_ct<N, +1, kWarps, false, false, false, V, TW>(stw, cr, sr, buf, slot_of_df(), sub_of_df(), warp_of_df(),
                                                              act);
     else
-        fft_ct<N, -1, kWarps, false, false, false, DFc, TwDF>(stw, sr, cr, buf, slot_of_df(), sub_of_df(), warp_of_df(),
+        fft_ct<N, -1, kWarps, false, false, false, V, TW>(stw, sr, cr, buf, slot_of_df(), sub_of_df(), warp_of_df(),
                                                              act);
 }
 
 // ------------------------------------------------------------------ K3
 // x-pass, x V(r) (V as hi + lo pairs), x-return; the last inverse stage, the
 // multiply and the first forward stage of the reversed schedule in registers.
-template <int N>
-__global__ void __launch_bounds__(kThreads) k3_df(DevTables t, const TwDF* __restrict__ tw1,
-                                                 const float2* __restrict__ Vdf, DFc* slab) {
+template <class Pol, int N>
+__global__ void __launch_bounds__(kThreads) k3_w(DevTables t, const typename Pol::TW* __restrict__ tw1,
+                                                const typename Pol::VR* __restrict__ Vr, typename Pol::V* slab) {
+    using V = typename Pol::V;
+    using TW = typename Pol::TW;
     using SC = Sched<N>;
     constexpr int nst = SC::nst;
     static_assert(nst >= 2, "compile-time x-pass needs at least two stages");
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int n2 = t.n2, n3 = t.n3;
     float2* buf = reinterpret_cast<float2*>(smem_raw);
-    TwDF* stw = reinterpret_cast<TwDF*>(buf + N * kLdP);
+    TW* stw = reinterpret_cast<TW*>(buf + N * kLdP);
     int* xrow = reinterpret_cast<int*>(stw + N);
     const int slot = slot_of_df(), sub = sub_of_df(), warp = warp_of_df();
     const int y = blockIdx.x;
@@ -158,29 +192,29 @@ __global__ void __launch_bounds__(kThreads) k3_df(DevTables t, const TwDF* __res
     const long long b = blockIdx.z;
     const int lines = min(kLinesDF, n3 - z0);
     const bool act = slot < lines;
-    load_twdf(stw, tw1, N);
+    load_tww(stw, tw1, N);
     for (int e = threadIdx.x; e < N; e += kThreads) xrow[e] = t.xrow_plane[e];
     __syncthreads();
     const int pstride = n2 * n3;
-    XRowsD xr{slab + b * t.NP * (long long)pstride + y * n3 + z0, xrow, pstride};
-    const float2* vrow = Vdf + (long long)y * n3 + z0 + slot;
-    SmemT<DFc> sb{buf};
+    XRowsD<V> xr{slab + b * t.NP * (long long)pstride + y * n3 + z0, xrow, pstride};
+    const typename Pol::VR* vrow = Vr + (long long)y * n3 + z0 + slot;
+    SmemT<V> sb{buf};
 
-    NatStage<N, +1, kWarps, 0, DFc, TwDF>::template run<false>(stw, xr, sb, slot, sub, warp, act);
+    NatStage<N, +1, kWarps, 0, V, TW>::template run<false>(stw, xr, sb, slot, sub, warp, act);
     __syncthreads();
     if constexpr (nst >= 3) {
-        NatStage<N, +1, kWarps, 1, DFc, TwDF>::template run<true>(stw, sb, sb, slot, sub, warp, act);
+        NatStage<N, +1, kWarps, 1, V, TW>::template run<true>(stw, sb, sb, slot, sub, warp, act);
         __syncthreads();
     }
     if constexpr (nst >= 4) {
-        NatStage<N, +1, kWarps, 2, DFc, TwDF>::template run<true>(stw, sb, sb, slot, sub, warp, act);
+        NatStage<N, +1, kWarps, 2, V, TW>::template run<true>(stw, sb, sb, slot, sub, warp, act);
         __syncthreads();
     }
-    using L = NatStage<N, +1, kWarps, nst - 1, DFc, TwDF>;
-    using F = RevStage<N, -1, kWarps, 0, DFc, TwDF>;
+    using L = NatStage<N, +1, kWarps, nst - 1, V, TW>;
+    using F = RevStage<N, -1, kWarps, 0, V, TW>;
     constexpr int R = SC::R(nst - 1);
     static_assert(F::NI == L::NI && SC::RR(0) == R, "chained stages must share units");
-    DFc h[L::U][R];
+    V h[L::U][R];
     if (act) {
         L::compute(h, stw, sb, slot, sub, warp);
 #pragma unroll
@@ -189,8 +223,7 @@ __global__ void __launch_bounds__(kThreads) k3_df(DevTables t, const TwDF* __res
             if (L::NI % (2 * kWarps) == 0 || i < L::NI) {
 #pragma unroll
                 for (int r = 0; r < R; ++r) {
-                    const float2 w = vrow[(i + r * L::NI) * pstride];  // V as (hi, lo)
-                    h[u][r] = df2_mul(h[u][r], make_float2(w.x, w.x), make_float2(w.y, w.y));
+                    h[u][r] = Pol::mul_v(h[u][r], vrow[(i + r * L::NI) * pstride]);
                 }
                 Dft<R, -1>::run(h[u]);
             }
@@ -200,49 +233,49 @@ __global__ void __launch_bounds__(kThreads) k3_df(DevTables t, const TwDF* __res
     if (act) F::store(h, sb, slot, sub, warp);
     __syncthreads();
     if constexpr (nst >= 3) {
-        RevStage<N, -1, kWarps, 1, DFc, TwDF>::template run<true>(stw, sb, sb, slot, sub, warp, act);
+        RevStage<N, -1, kWarps, 1, V, TW>::template run<true>(stw, sb, sb, slot, sub, warp, act);
         __syncthreads();
     }
     if constexpr (nst >= 4) {
-        RevStage<N, -1, kWarps, 2, DFc, TwDF>::template run<true>(stw, sb, sb, slot, sub, warp, act);
+        RevStage<N, -1, kWarps, 2, V, TW>::template run<true>(stw, sb, sb, slot, sub, warp, act);
         __syncthreads();
     }
-    RevStage<N, -1, kWarps, nst - 1, DFc, TwDF>::template run<false>(stw, sb, xr, slot, sub, warp, act);
+    RevStage<N, -1, kWarps, nst - 1, V, TW>::template run<false>(stw, sb, xr, slot, sub, warp, act);
 }
 
 // ------------------------------------------------------------------ K4
-template <int N>
-__global__ void __launch_bounds__(kThreads) k4_df(DevTables t, const TwDF* __restrict__ tw3,
-                                                 const DFc* __restrict__ cyl, double2* out, double scale,
-                                                 const double* __restrict__ diag, const double2* cin) {
+template <class Pol, int N>
+__global__ void __launch_bounds__(kThreads) k4_w(DevTables t, const typename Pol::TW* __restrict__ tw3,
+                                                const typename Pol::V* __restrict__ cyl, double2* out, double scale,
+                                                const double* __restrict__ diag, const double2* cin) {
+    using V = typename Pol::V;
+    using TW = typename Pol::TW;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float2* buf = reinterpret_cast<float2*>(smem_raw);
-    TwDF* stw = reinterpret_cast<TwDF*>(buf + N * kLdP);
+    TW* stw = reinterpret_cast<TW*>(buf + N * kLdP);
     const int tile = blockIdx.x;
     const long long b = blockIdx.y;
     const int l0 = kLinesDF * (int)blockIdx.z;
     const int s0 = t.tile_ptr[tile] + l0;
     const int lines = min(kLinesDF, t.tile_ptr[tile + 1] - s0);
     if (lines <= 0) return;  // uniform over the CTA
-    load_twdf(stw, tw3, N);
+    load_tww(stw, tw3, N);
     const int lane = threadIdx.x & 31;
     for (int l = threadIdx.x >> 5; l < lines; l += kWarps) {
-        const DFc* row = cyl + (b * t.S + t.tile_sticks[s0 + l]) * (long long)N;
-        for (int z = lane; z < N; z += 32) df_at(buf, z, l) = row[z];
+        const V* row = cyl + (b * t.S + t.tile_sticks[s0 + l]) * (long long)N;
+        for (int z = lane; z < N; z += 32) w_at<V>(buf, z, l) = row[z];
     }
     __syncthreads();
-    fft_ct<N, -1, kWarps, false, true, true, DFc, TwDF>(stw, SmemT<DFc>{buf}, SmemT<DFc>{buf}, buf, slot_of_df(),
+    fft_ct<N, -1, kWarps, false, true, true, V, TW>(stw, SmemT<V>{buf}, SmemT<V>{buf}, buf, slot_of_df(),
                                                        sub_of_df(), warp_of_df(), slot_of_df() < lines);
     __syncthreads();
-    const float2 sc = df_split(scale);
     double2* o = out + b * t.npw;
     const double2* ci = diag ? cin + b * t.npw : cin;
     for (int e = t.tile_pw_ptr[tile] + (int)threadIdx.x; e < t.tile_pw_ptr[tile + 1]; e += kThreads) {
         const int2 en = t.tile_pw[e];
         const int l = (en.y >> 16) - l0;
         if (l < 0 || l >= kLinesDF) continue;
-        const DFc v = df_at(buf, en.y & 0xffff, l);
-        double2 r = df_to(df2_mul(v, make_float2(sc.x, sc.x), make_float2(sc.y, sc.y)));
+        double2 r = Pol::out(w_at<V>(buf, en.y & 0xffff, l), scale);
         if (diag) {  // H = diag + A (c is read before out is written: they may alias)
             const double d = diag[en.x];
             const double2 cc = ci[en.x];
@@ -254,53 +287,62 @@ __global__ void __launch_bounds__(kThreads) k4_df(DevTables t, const TwDF* __res
 }
 
 // ------------------------------------------------------------ launchers
-template <int N> struct DfSmem {
-    static constexpr size_t sm = df_smem<N>();
+template <class Pol, int N> struct WSmem {
+    static constexpr size_t sm = w_smem<Pol, N>();
     template <class K> static cudaError_t ensure(K kernel) {
         if (sm <= 48 * 1024) return cudaSuccess;
         return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     }
 };
 
-template <int N>
-int LaunchDF<N>::k1(const DevTables& t, const void* tw3, const void* coeffs, long long nb, void* cyl, cudaStream_t st) {
-    static const cudaError_t once = DfSmem<N>::ensure(k1_df<N>);
+template <int P, int N>
+int LaunchF64<P, N>::k1(const DevTables& t, const void* tw3, const void* coeffs, long long nb, void* cyl,
+                        cudaStream_t st) {
+    using Pol = PolOf<P>;
+    static const cudaError_t once = WSmem<Pol, N>::ensure(k1_w<Pol, N>);
     if (once) return (int)once;
-    k1_df<N><<<dim3(t.T, (unsigned)nb, 2), kThreads, DfSmem<N>::sm, st>>>(t, (const TwDF*)tw3, (const double2*)coeffs,
-                                                                          (DFc*)cyl);
+    k1_w<Pol, N><<<dim3(t.T, (unsigned)nb, 2), kThreads, WSmem<Pol, N>::sm, st>>>(
+        t, (const typename Pol::TW*)tw3, (const double2*)coeffs, (typename Pol::V*)cyl);
     return (int)cudaGetLastError();
 }
-template <int N>
-int LaunchDF<N>::k2(int sign, const DevTables& t, const void* tw2, long long nb, void* cyl, void* slab,
-                    cudaStream_t st) {
+template <int P, int N>
+int LaunchF64<P, N>::k2(int sign, const DevTables& t, const void* tw2, long long nb, void* cyl, void* slab,
+                        cudaStream_t st) {
+    using Pol = PolOf<P>;
+    using V = typename Pol::V;
     const dim3 grid(t.NP, (t.n3 + kLinesDF - 1) / kLinesDF, (unsigned)nb);
     if (sign > 0) {
-        static const cudaError_t once = DfSmem<N>::ensure(k2_df<+1, N>);
+        static const cudaError_t once = WSmem<Pol, N>::ensure(k2_w<Pol, +1, N>);
         if (once) return (int)once;
-        k2_df<+1, N><<<grid, kThreads, DfSmem<N>::sm, st>>>(t, (const TwDF*)tw2, (DFc*)cyl, (DFc*)slab);
+        k2_w<Pol, +1, N><<<grid, kThreads, WSmem<Pol, N>::sm, st>>>(t, (const typename Pol::TW*)tw2, (V*)cyl, (V*)slab);
     } else {
-        static const cudaError_t once = DfSmem<N>::ensure(k2_df<-1, N>);
+        static const cudaError_t once = WSmem<Pol, N>::ensure(k2_w<Pol, -1, N>);
         if (once) return (int)once;
-        k2_df<-1, N><<<grid, kThreads, DfSmem<N>::sm, st>>>(t, (const TwDF*)tw2, (DFc*)cyl, (DFc*)slab);
+        k2_w<Pol, -1, N><<<grid, kThreads, WSmem<Pol, N>::sm, st>>>(t, (const typename Pol::TW*)tw2, (V*)cyl, (V*)slab);
     }
     return (int)cudaGetLastError();
 }
-template <int N>
-int LaunchDF<N>::k3(const DevTables& t, const void* tw1, const void* Vdf, long long nb, void* slab, cudaStream_t st) {
-    static const cudaError_t once = DfSmem<N>::ensure(k3_df<N>);
+template <int P, int N>
+int LaunchF64<P, N>::k3(const DevTables& t, const void* tw1, const void* V, long long nb, void* slab,
+                        cudaStream_t st) {
+    using Pol = PolOf<P>;
+    static const cudaError_t once = WSmem<Pol, N>::ensure(k3_w<Pol, N>);
     if (once) return (int)once;
     const dim3 grid(t.n2, (t.n3 + kLinesDF - 1) / kLinesDF, (unsigned)nb);
-    k3_df<N><<<grid, kThreads, DfSmem<N>::sm, st>>>(t, (const TwDF*)tw1, (const float2*)Vdf, (DFc*)slab);
+    k3_w<Pol, N><<<grid, kThreads, WSmem<Pol, N>::sm, st>>>(t, (const typename Pol::TW*)tw1,
+                                                           (const typename Pol::VR*)V, (typename Pol::V*)slab);
     return (int)cudaGetLastError();
 }
-template <int N>
-int LaunchDF<N>::k4(const DevTables& t, const void* tw3, const void* cyl, long long nb, void* out, const void* diag,
-                    const void* cin, cudaStream_t st) {
-    static const cudaError_t once = DfSmem<N>::ensure(k4_df<N>);
+template <int P, int N>
+int LaunchF64<P, N>::k4(const DevTables& t, const void* tw3, const void* cyl, long long nb, void* out,
+                        const void* diag, const void* cin, cudaStream_t st) {
+    using Pol = PolOf<P>;
+    static const cudaError_t once = WSmem<Pol, N>::ensure(k4_w<Pol, N>);
     if (once) return (int)once;
     const double scale = 1.0 / ((double)t.n1 * t.n2 * t.n3);
-    k4_df<N><<<dim3(t.T, (unsigned)nb, 2), kThreads, DfSmem<N>::sm, st>>>(
-        t, (const TwDF*)tw3, (const DFc*)cyl, (double2*)out, scale, (const double*)diag, (const double2*)cin);
+    k4_w<Pol, N><<<dim3(t.T, (unsigned)nb, 2), kThreads, WSmem<Pol, N>::sm, st>>>(
+        t, (const typename Pol::TW*)tw3, (const typename Pol::V*)cyl, (double2*)out, scale, (const double*)diag,
+        (const double2*)cin);
     return (int)cudaGetLastError();
 }
 

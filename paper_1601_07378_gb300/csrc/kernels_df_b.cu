@@ -1,9 +1,13 @@
-// kernels_df_b.cu -- Double-float chain kernels, lengths 64, 72, 80, 96.
+// kernels_df_b.cu -- FP64-data chain kernels (double-float and native), lengths 64, 72, 80, 96.
 #include "kernels_df.cuh"
 
 namespace vloc {
-template struct LaunchDF<64>;
-template struct LaunchDF<72>;
-template struct LaunchDF<80>;
-template struct LaunchDF<96>;
+template struct LaunchF64<0, 64>;
+template struct LaunchF64<1, 64>;
+template struct LaunchF64<0, 72>;
+template struct LaunchF64<1, 72>;
+template struct LaunchF64<0, 80>;
+template struct LaunchF64<1, 80>;
+template struct LaunchF64<0, 96>;
+template struct LaunchF64<1, 96>;
 }  // namespace vloc
