@@ -142,26 +142,37 @@ __host__ __device__ __forceinline__ TwDF twdf_make(double c, double s) {
     return TwDF{make_float2(cc.x, cc.x), make_float2(cc.y, cc.y), make_float2(-ss.x, ss.x), make_float2(-ss.y, ss.y)};
 }
 __device__ __forceinline__ DFc df2_neg(DFc x) { return {fneg2_(x.hi), fneg2_(x.lo)}; }
-// paired double-float sum (two-sum of the high parts, then renormalise)
+// Paired double-float sum: the exact two-sum of the high parts, plus the
+// low parts.  The pair is left unnormalised (no final fast two-sum): the
+// next two-sum is exact whatever the size of the low part, and each low part
+// stays within a few ulps of its high part, so errors stay a few units of
+// 2^-48 relative to the operands (the norm-wise bound of an FFT).
 __device__ __forceinline__ DFc cadd(DFc x, DFc y) {
     const float2 s = __fadd2_rn(x.hi, y.hi);
     const float2 bb = __fadd2_rn(s, fneg2_(x.hi));
     const float2 e = __fadd2_rn(__fadd2_rn(__fadd2_rn(x.hi, fneg2_(__fadd2_rn(s, fneg2_(bb)))),
                                            __fadd2_rn(y.hi, fneg2_(bb))),
                                 __fadd2_rn(x.lo, y.lo));
-    const float2 hi = __fadd2_rn(s, e);
-    return {hi, __fadd2_rn(e, fneg2_(__fadd2_rn(hi, fneg2_(s))))};
+    return {s, e};
 }
 __device__ __forceinline__ DFc csub(DFc x, DFc y) { return cadd(x, df2_neg(y)); }
+// renormalise (fast two-sum; |lo| is a few ulps of hi at most): applied when a
+// value is written to global memory, so low parts do not grow over passes
+__device__ __forceinline__ DFc df2_norm(DFc x) {
+    const float2 hi = __fadd2_rn(x.hi, x.lo);
+    return {hi, __fadd2_rn(x.lo, fneg2_(__fadd2_rn(hi, fneg2_(x.hi))))};
+}
 __device__ __forceinline__ DFc cneg(DFc x) { return df2_neg(x); }
-// componentwise double-float product of x with the pair (bh + bl)
+// componentwise double-float product of x with the pair (bh + bl): the exact
+// product of the high parts (an FMA gives its rounding error) plus the cross
+// terms; the result (p, e) has |e| of a few ulps of p, so it needs no
+// renormalisation either
 __device__ __forceinline__ DFc df2_mul(DFc x, float2 bh, float2 bl) {
     const float2 p = __fmul2_rn(x.hi, bh);
     float2 e = __ffma2_rn(x.hi, bh, fneg2_(p));
     e = __ffma2_rn(x.hi, bl, e);
     e = __ffma2_rn(x.lo, bh, e);
-    const float2 hi = __fadd2_rn(p, e);
-    return {hi, __fadd2_rn(e, fneg2_(__fadd2_rn(hi, fneg2_(p))))};
+    return {p, e};
 }
 __device__ __forceinline__ DFc df2_swap(DFc x) {  // (re, im) -> (im, re)
     return {make_float2(x.hi.y, x.hi.x), make_float2(x.lo.y, x.lo.x)};

@@ -54,6 +54,10 @@ struct PolNative {
 };
 template <int P> using PolOf = std::conditional_t<P == 0, PolDF, PolNative>;
 
+// value as written to global memory (double-float values renormalised)
+__device__ __forceinline__ DFc w_store(DFc v) { return df2_norm(v); }
+__device__ __forceinline__ double2 w_store(double2 v) { return v; }
+
 template <class Pol, int N> __host__ __device__ constexpr size_t w_smem() {
     return (size_t)N * kLdP * sizeof(float2) + (size_t)N * sizeof(typename Pol::TW) + (size_t)N * sizeof(int) + 16;
 }
@@ -79,14 +83,14 @@ template <class V> struct CylRowsD {  // rows = the plane's sticks (via rowmap),
     }
     __device__ __forceinline__ void operator()(int e, int slot, V v) const {
         const int s = rowmap[e];
-        if (s >= 0) cb[s * n3 + z0 + slot] = v;
+        if (s >= 0) cb[s * n3 + z0 + slot] = w_store(v);
     }
 };
 template <class V> struct SlabRowsD {  // every y row of one plane's tile
     V* p;           // slab[b][plane][0][z0]
     int n3;
     __device__ __forceinline__ V operator()(int e, int slot) const { return p[e * n3 + slot]; }
-    __device__ __forceinline__ void operator()(int e, int slot, V v) const { p[e * n3 + slot] = v; }
+    __device__ __forceinline__ void operator()(int e, int slot, V v) const { p[e * n3 + slot] = w_store(v); }
 };
 template <class V> struct XRowsD {  // x rows at fixed y: the occupied planes
     V* sb;       // slab[b][0][y][z0]
@@ -98,7 +102,7 @@ template <class V> struct XRowsD {  // x rows at fixed y: the occupied planes
     }
     __device__ __forceinline__ void operator()(int e, int slot, V v) const {
         const int p = xrow[e];
-        if (p >= 0) sb[p * pstride + slot] = v;
+        if (p >= 0) sb[p * pstride + slot] = w_store(v);
     }
 };
 
@@ -135,7 +139,7 @@ __global__ void __launch_bounds__(kThreads) k1_w(DevTables t, const typename Pol
     const int lane = threadIdx.x & 31;
     for (int l = threadIdx.x >> 5; l < lines; l += kWarps) {
         V* row = cyl + (b * t.S + t.tile_sticks[s0 + l]) * (long long)N;
-        for (int z = lane; z < N; z += 32) row[z] = w_at<V>(buf, z, l);
+        for (int z = lane; z < N; z += 32) row[z] = w_store(w_at<V>(buf, z, l));
     }
 }
 
