@@ -761,8 +761,17 @@ int vloc_backward(vloc_plan p, const void* c, const void* gout, const void* V, i
             double* partial = p->d_acc + p->N;
             if ((rc = launch(p, KK_GRAD_V, st, [&] { return launch_k3b_grad_v(dbl, p->fast, t, ax, p->d_tw[0], slabC, slabG, cb, (int)kGradBandsPerGroup, partial, &used, st); }))) return rc;
             if ((rc = launch(p, KK_AUX, st, [&] { return launch_reduce_partials(partial, used, p->N, p->d_acc, st); }))) return rc;
+            if (gc) {
+                // dL/dc = A g continues from g's slab (its z- and y-passes are
+                // already done): x-pass with V, forward y-pass, z-pass + gather
+                void* gg_out = (char*)gc + b0 * bstride;
+                if ((rc = launch(p, KK_X_V, st, [&] { return launch_k3_xpass_v(dbl, p->fast, t, ax, p->d_tw[0], V, cb, slabG, st); }))) return rc;
+                if ((rc = launch(p, KK_Y_FWD, st, [&] { return launch_k2_ypass(dbl, p->fast, -1, t, ax, p->d_tw[1], cb, cylG, slabG, st); }))) return rc;
+                if ((rc = launch(p, KK_Z_GATHER, st, [&] { return launch_k4_zpass_gather(dbl, p->fast, t, ax, p->d_tw[2], cylG, cb, gg_out, nullptr, nullptr, st); }))) return rc;
+            }
         }
         if ((rc = launch(p, KK_AUX, st, [&] { return launch_finish_grad_v(dbl, p->d_acc, gV, p->N, st); }))) return rc;
+        return VLOC_OK;
     }
     if (gc && nb > 0) {
         int rc = apply_impl(p, gout, V, nb, gc, st);
