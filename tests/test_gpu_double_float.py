@@ -93,3 +93,19 @@ def test_double_float_flag_needs_fp64():
     g = synth.sphere_glist(24, 24, 24, 6)
     with pytest.raises(vloc.VlocError):
         vloc.VlocPlan((24, 24, 24), g, torch.complex64, double_float=True)
+
+
+def test_double_float_batched_graph():
+    # two double-float plans of different grids in one graph-captured batch
+    n1, n2 = (24, 24, 24), (48, 60, 72)
+    g1, c1, V1 = make_case(n1, 6, 3, seed=7, prec="f64")
+    g2, c2, V2 = make_case(n2, 11, 2, seed=8, prec="f64")
+    p1 = vloc.VlocPlan(n1, g1, torch.complex128, double_float=True, graph=True)
+    p2 = vloc.VlocPlan(n2, g2, torch.complex128, double_float=True, graph=True)
+    cs = [torch.from_numpy(c1).cuda(), torch.from_numpy(c2).cuda()]
+    Vs = [torch.from_numpy(V1).cuda(), torch.from_numpy(V2).cuda()]
+    for _ in range(2):
+        outs = vloc.apply_batched([p1, p2], cs, Vs)
+        torch.cuda.synchronize()
+        assert rel_l2_per_band(outs[0].cpu().numpy(), oracle_apply(n1, g1, c1, V1)).max() < TOL["f64"]
+        assert rel_l2_per_band(outs[1].cpu().numpy(), oracle_apply(n2, g2, c2, V2)).max() < TOL["f64"]
