@@ -49,42 +49,49 @@ __device__ __forceinline__ int sub_of() { return (threadIdx.x >> 4) & 1; }
 __device__ __forceinline__ int warp_of() { return threadIdx.x >> 5; }
 
 // ------------------------------------------------------------- tile I/O
-// One batch of a tile's plane-wave entries starting at `base` (stride
+// One batch of B of a tile's plane-wave entries starting at `base` (stride
 // kThreads): the entries and their coefficients into registers, then into
 // the tile buffer.
+template <int B>
 __device__ __forceinline__ void entries_load_p(const int2* __restrict__ ent, int base, int e1,
-                                               const float2* __restrict__ c, int2 (&en)[kBatch],
-                                               float2 (&val)[kBatch]) {
+                                               const float2* __restrict__ c, int2 (&en)[B], float2 (&val)[B]) {
 #pragma unroll
-    for (int u = 0; u < kBatch; ++u) {
+    for (int u = 0; u < B; ++u) {
         const int e = base + u * kThreads;
         en[u] = e < e1 ? ent[e] : make_int2(0, -1);
     }
 #pragma unroll
-    for (int u = 0; u < kBatch; ++u) val[u] = en[u].y >= 0 ? c[en[u].x] : make_float2(0.f, 0.f);
+    for (int u = 0; u < B; ++u) val[u] = en[u].y >= 0 ? c[en[u].x] : make_float2(0.f, 0.f);
 }
-__device__ __forceinline__ void entries_store_p(float2* buf, const int2 (&en)[kBatch], const float2 (&val)[kBatch]) {
+template <int B>
+__device__ __forceinline__ void entries_store_p(float2* buf, const int2 (&en)[B], const float2 (&val)[B]) {
 #pragma unroll
-    for (int u = 0; u < kBatch; ++u)
+    for (int u = 0; u < B; ++u)
         if (en[u].y >= 0) buf[(en[u].y & 0xffff) * kLdP + (en[u].y >> 16)] = val[u];
 }
 // Clear the tile buffer (N rows) and scatter the tile's plane waves into it;
 // the first batch's loads are issued before the clearing so their latency
-// hides behind it.  Ends with a barrier.
+// hides behind it.  Ends with a barrier.  Batches of VLOC_SCATTER_BATCH
+// entries per thread (a 32-stick tile holds about 1000 plane waves at 96^3,
+// 8 per thread).
+#ifndef VLOC_SCATTER_BATCH
+#define VLOC_SCATTER_BATCH 8
+#endif
 template <int N>
 __device__ __forceinline__ void scatter_tile_p(const int2* __restrict__ ent, int e0, int e1,
                                                const float2* __restrict__ c, float2* buf) {
-    int2 en[kBatch];
-    float2 val[kBatch];
+    constexpr int B = VLOC_SCATTER_BATCH;
+    int2 en[B];
+    float2 val[B];
     const int base0 = e0 + (int)threadIdx.x;
-    entries_load_p(ent, base0, e1, c, en, val);
+    entries_load_p<B>(ent, base0, e1, c, en, val);
     for (int i = threadIdx.x; i < N * kLdP / 2; i += kThreads)
         reinterpret_cast<float4*>(buf)[i] = make_float4(0.f, 0.f, 0.f, 0.f);
     __syncthreads();
-    entries_store_p(buf, en, val);
-    for (int base = base0 + kBatch * kThreads; base < e1; base += kBatch * kThreads) {
-        entries_load_p(ent, base, e1, c, en, val);
-        entries_store_p(buf, en, val);
+    entries_store_p<B>(buf, en, val);
+    for (int base = base0 + B * kThreads; base < e1; base += B * kThreads) {
+        entries_load_p<B>(ent, base, e1, c, en, val);
+        entries_store_p<B>(buf, en, val);
     }
     __syncthreads();
 }
