@@ -95,31 +95,35 @@ __device__ __forceinline__ void scatter_tile_p(const int2* __restrict__ ent, int
     }
     __syncthreads();
 }
+#ifndef VLOC_GATHER_BATCH
+#define VLOC_GATHER_BATCH 8
+#endif
 __device__ __forceinline__ void gather_entries_p(const int2* __restrict__ ent, int e0, int e1, const float2* buf,
                                                  float2* o, float scale, const float* __restrict__ diag,
                                                  const float2* cin) {
-    for (int base = e0 + (int)threadIdx.x; base < e1; base += kBatch * kThreads) {
-        int2 en[kBatch];
+    constexpr int GB = VLOC_GATHER_BATCH;
+    for (int base = e0 + (int)threadIdx.x; base < e1; base += GB * kThreads) {
+        int2 en[GB];
 #pragma unroll
-        for (int u = 0; u < kBatch; ++u) {
+        for (int u = 0; u < GB; ++u) {
             const int e = base + u * kThreads;
             en[u] = e < e1 ? ent[e] : make_int2(0, -1);
         }
         if (diag) {  // H = diag + A (c is read before out is written: they may alias)
-            float d[kBatch];
-            float2 ci[kBatch];
+            float d[GB];
+            float2 ci[GB];
 #pragma unroll
-            for (int u = 0; u < kBatch; ++u)
+            for (int u = 0; u < GB; ++u)
                 if (en[u].y >= 0) { d[u] = diag[en[u].x]; ci[u] = cin[en[u].x]; }
 #pragma unroll
-            for (int u = 0; u < kBatch; ++u)
+            for (int u = 0; u < GB; ++u)
                 if (en[u].y >= 0) {
                     const float2 v = cscale(buf[(en[u].y & 0xffff) * kLdP + (en[u].y >> 16)], scale);
                     o[en[u].x] = make_float2(v.x + d[u] * ci[u].x, v.y + d[u] * ci[u].y);
                 }
         } else {
 #pragma unroll
-            for (int u = 0; u < kBatch; ++u)
+            for (int u = 0; u < GB; ++u)
                 if (en[u].y >= 0) o[en[u].x] = cscale(buf[(en[u].y & 0xffff) * kLdP + (en[u].y >> 16)], scale);
         }
     }
