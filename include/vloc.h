@@ -84,6 +84,14 @@ extern "C" {
                                        /* Used when every axis length has compiled   */
                                        /* kernels (info.path bit 3), else native FP64*/
                                        /* (apply / adjoint / H / batched only).      */
+#define VLOC_X_TMA              0x4000 /* FP32: x-pass by a persistent kernel whose  */
+                                       /* slab tiles move by TMA tensor copies,      */
+                                       /* double-buffered on mbarriers (compiled x   */
+                                       /* length, even n3; info.path bit 4).  Same   */
+                                       /* results bit for bit; measured slower than  */
+                                       /* the default x-pass at 96^3, kept opt-in.   */
+                                       /* Its waits are bounded: see                 */
+                                       /* vloc_device_status.                        */
 #define VLOC_HOST_ONLY          0x200  /* build host tables only (no device memory, */
                                        /* no CUDA call); for introspection: the     */
                                        /* device calls then return VLOC_ERR_STATE   */
@@ -105,7 +113,8 @@ typedef struct vloc_info {
     int32_t nstages[3];
     int32_t path;                /* bit 0: compile-time-length kernels enabled;   */
                                  /* bit 2: Gamma-point real mode;                 */
-                                 /* bit 3: double-float FP64 apply in use         */
+                                 /* bit 3: double-float FP64 apply in use;        */
+                                 /* bit 4: TMA x-pass in use                      */
 } vloc_info;
 
 /*
@@ -122,8 +131,8 @@ typedef struct vloc_info {
  *   npw        : number of plane waves, >= 1.
  *   flags      : exactly one of VLOC_F32 / VLOC_F64, optionally one
  *                partition flag, VLOC_GRAPH, VLOC_HOST_ONLY,
- *                VLOC_GENERIC_KERNELS, VLOC_GAMMA and VLOC_DOUBLE_FLOAT (with
- *                VLOC_F64 only, else VLOC_ERR_ARG).  With VLOC_GAMMA every
+ *                VLOC_GENERIC_KERNELS, VLOC_GAMMA, VLOC_DOUBLE_FLOAT (with
+ *                VLOC_F64 only, else VLOC_ERR_ARG) and VLOC_X_TMA.  With VLOC_GAMMA every
  *                -G must be a valid index too (else VLOC_ERR_GLIST), and
  *                npw counts the half list (the caller's arrays).
  *   max_bands_per_chunk : bands per workspace chunk (<= 0: automatic, a
@@ -328,6 +337,12 @@ int vloc_get_profile(vloc_plan plan, vloc_kernel_stat* stats);
 /* vloc_get_launch_count -- kernels launched by this plan since creation
  * (always counted, profiling or not). */
 int vloc_get_launch_count(vloc_plan plan, int64_t* count);
+
+/* vloc_device_status -- synchronise the device and report whether a kernel
+ * of this plan gave up a bounded wait since the last call (a bulk copy that
+ * did not land within about a second): VLOC_ERR_TIMEOUT (and the flag is
+ * cleared), else VLOC_OK.  Results of the affected calls are undefined. */
+int vloc_device_status(vloc_plan plan);
 
 /* vloc_strerror -- static string for a return code (never NULL). */
 const char* vloc_strerror(int code);

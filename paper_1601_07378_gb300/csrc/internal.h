@@ -2,6 +2,7 @@
 // CUDA kernels (kernels.cu).  Not part of the public ABI.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -31,6 +32,16 @@ struct LaunchAxes {
     int n[3];
     int nst[3];
     int radix[3][4];
+};
+
+// Tensor map over a plan's slab workspace [ws_bands][NP][n2][2 n3] FP32, box
+// {64, 1, NP, 1} (one 32-z tile of every occupied plane at one y), for the
+// x-pass kernel's TMA loads and stores; err is the plan's device error flag.
+struct K3Tma {
+    CUtensorMap map;
+    const void* base;   // slab workspace start (band 0 of the map)
+    size_t band_bytes;  // NP * n2 * n3 * 8
+    int* err;
 };
 
 // Kernel kinds (profiling slots).
@@ -77,7 +88,9 @@ extern template struct Launch<double>;
 template <typename T, int N> struct LaunchCT {
     static int k1(const DevTables& t, const void* tw3, const void* coeffs, long long nb, void* cyl, cudaStream_t st);
     static int k2(int sign, const DevTables& t, const void* tw2, long long nb, void* cyl, void* slab, cudaStream_t st);
-    static int k3(const DevTables& t, const void* tw1, const void* V, long long nb, void* slab, cudaStream_t st);
+    // tma: the plan's slab tensor map for the persistent TMA form, or null
+    static int k3(const DevTables& t, const void* tw1, const void* V, long long nb, void* slab, const K3Tma* tma,
+                  cudaStream_t st);
     static int k4(const DevTables& t, const void* tw3, const void* cyl, long long nb, void* out, const void* diag,
                   const void* cin, cudaStream_t st);
     static int k3b(const DevTables& t, const void* tw1, const void* sc, const void* sg, long long nb, int bpg,
@@ -101,6 +114,7 @@ template <int P, int N> struct LaunchF64 {
                   const void* cin, cudaStream_t st);
 };
 bool has_df(int n);
+bool has_ct(int n);
 // TwDF table [n] from an FP64 twiddle table; V [N] FP64 -> hi + lo pairs
 int launch_twiddles_df(const void* tw64, void* twdf, int n, cudaStream_t st);
 int launch_v_to_df(const void* V, void* Vdf, long long N, cudaStream_t st);
@@ -115,7 +129,7 @@ int launch_k1_scatter_zpass(int dbl, int fast, const DevTables& t, const LaunchA
 int launch_k2_ypass(int dbl, int fast, int sign, const DevTables& t, const LaunchAxes& ax, const void* tw2, long long nb,
                     void* cyl, void* slab, cudaStream_t st);
 int launch_k3_xpass_v(int dbl, int fast, const DevTables& t, const LaunchAxes& ax, const void* tw1, const void* V,
-                      long long nb, void* slab, cudaStream_t st);
+                      long long nb, void* slab, cudaStream_t st, const K3Tma* tma = nullptr);
 int launch_k4_zpass_gather(int dbl, int fast, const DevTables& t, const LaunchAxes& ax, const void* tw3, const void* cyl,
                            long long nb, void* out, const void* diag, const void* cin, cudaStream_t st);
 // dL/dV x-pass over nb bands in groups of at most `bpg` bands; each group's

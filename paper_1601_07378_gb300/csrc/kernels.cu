@@ -184,7 +184,7 @@ int launch_k2_ypass(int dbl, int fast, int sign, const DevTables& t, const Launc
                : Launch<float>::k2(sign, t, ax, tw2, nb, cyl, slab, st);
 }
 int launch_k3_xpass_v(int dbl, int fast, const DevTables& t, const LaunchAxes& ax, const void* tw1, const void* V,
-                      long long nb, void* slab, cudaStream_t st) {
+                      long long nb, void* slab, cudaStream_t st, const K3Tma* tma) {
     if (dbl && fast == 2) switch (t.n1) {  // V: hi + lo pairs
 #define VLOC_CASE(N) case N: return LaunchF64<0, N>::k3(t, tw1, V, nb, slab, st);
         VLOC_CT_SIZES(VLOC_CASE)
@@ -199,7 +199,7 @@ int launch_k3_xpass_v(int dbl, int fast, const DevTables& t, const LaunchAxes& a
     }
     // the compile-time x-pass reads V two lines at a time (8-byte loads)
     if (!dbl && fast && (t.n3 & 1) == 0 && ((uintptr_t)V & 7) == 0) switch (t.n1) {
-#define VLOC_CASE(N) case N: return LaunchCT<float, N>::k3(t, tw1, V, nb, slab, st);
+#define VLOC_CASE(N) case N: return LaunchCT<float, N>::k3(t, tw1, V, nb, slab, tma, st);
         VLOC_CT_SIZES(VLOC_CASE)
 #undef VLOC_CASE
         default: break;

@@ -595,8 +595,13 @@ int LaunchCT<T, N>::k2(int sign, const DevTables& t, const void* tw2, long long 
     }
     return (int)cudaGetLastError();
 }
+// defined in k3_tma.cuh (included by the instantiating files)
+template <int N> int launch_k3_tma(const DevTables& t, const void* tw1, const void* V, long long nb, void* slab,
+                                   const K3Tma& tma, cudaStream_t st);
 template <typename T, int N>
-int LaunchCT<T, N>::k3(const DevTables& t, const void* tw1, const void* V, long long nb, void* slab, cudaStream_t st) {
+int LaunchCT<T, N>::k3(const DevTables& t, const void* tw1, const void* V, long long nb, void* slab, const K3Tma* tma,
+                       cudaStream_t st) {
+    if (tma) return launch_k3_tma<N>(t, tw1, V, nb, slab, *tma, st);
     static const cudaError_t once = CtSmem<N>::ensure(k3_ct<N, VLOC_K3_WARPS>);
     if (once) return (int)once;
     const dim3 grid(t.n2, (t.n3 + kLines - 1) / kLines, (unsigned)nb);

@@ -8,6 +8,7 @@
 // (Sec. 4.1, 4.2), makes the twiddles on the device in FP64 and owns the
 // workspace that replaces the distributed FFT's transposes.
 #include <cuda_runtime.h>
+#include <cudaTypedefs.h>
 
 #include <algorithm>
 #include <cmath>
@@ -41,6 +42,7 @@ int cuda_fail(cudaError_t e, const char* what) {
 
 const int kRadices[] = {16, 15, 12, 10, 9, 8, 6, 5, 4, 3, 2};
 constexpr long long kGradBandsPerGroup = 16;
+
 // Host-buffer apply: bands per staging chunk, and the growth (x2) of the
 // ramps of smaller chunks at both ends (4: doubling; 2 or less: no ramp).
 #ifndef VLOC_STAGE_BANDS
@@ -114,6 +116,9 @@ struct vloc_plan_s {
     bool df = false;            // FP64 apply in double-float arithmetic
     void* d_twdf[3] = {nullptr, nullptr, nullptr};  // TwDF tables per axis
     void* d_vdf = nullptr;      // V as hi + lo pairs [N]
+    int* d_err = nullptr;       // set by a kernel whose bounded wait ran out
+    bool k3tma_on = false;      // x-pass through the persistent TMA kernel
+    vloc::K3Tma k3tma{};
     bool gamma = false;       // Gamma-point real mode (half-sphere coefficients)
     long long npw_user = 0;   // plane waves per band in the caller's arrays
     int* d_gamma_neg = nullptr;  // full-list index of -G for each caller G
@@ -194,6 +199,7 @@ static void free_plan(vloc_plan p) {
     cudaFree(p->d_gamma_neg);
     for (int a = 0; a < 3; ++a) cudaFree(p->d_twdf[a]);
     cudaFree(p->d_vdf);
+    cudaFree(p->d_err);
     cudaFree(p->d_gamma_buf);
     cudaFree(p->d_stage);
     for (cudaEvent_t e : p->prof_pool) cudaEventDestroy(e);
@@ -220,7 +226,8 @@ int vloc_plan_create(vloc_plan* out, int n1, int n2, int n3, const int32_t* g, i
     const int part_flag = flags & 0x0F0;
     if (part_flag != VLOC_PARTITION_GREEDY && part_flag != VLOC_PARTITION_BASIC && part_flag != VLOC_PARTITION_IMPROVED)
         return VLOC_ERR_ARG;
-    if (flags & ~(0x003 | 0x0F0 | VLOC_GRAPH | VLOC_HOST_ONLY | VLOC_GENERIC_KERNELS | VLOC_GAMMA | VLOC_DOUBLE_FLOAT))
+    if (flags & ~(0x003 | 0x0F0 | VLOC_GRAPH | VLOC_HOST_ONLY | VLOC_GENERIC_KERNELS | VLOC_GAMMA | VLOC_DOUBLE_FLOAT |
+                  VLOC_X_TMA))
         return VLOC_ERR_ARG;
     if ((flags & VLOC_DOUBLE_FLOAT) && prec != VLOC_F64) return VLOC_ERR_ARG;
     const bool host_only = (flags & VLOC_HOST_ONLY) != 0;
@@ -433,6 +440,9 @@ int vloc_plan_create(vloc_plan* out, int n1, int n2, int n3, const int32_t* g, i
         if (launch_twiddles(dbl, p->d_tw[a], ns[a], st)) { free_plan(p); return cuda_fail(cudaGetLastError(), "twiddles"); }
     }
     if ((e = (cudaError_t)set_smem_limits(dbl, nmax, maxopt))) { free_plan(p); return cuda_fail(e, "cudaFuncSetAttribute"); }
+    if ((e = cudaMalloc(&p->d_err, sizeof(int)))) { free_plan(p); return cuda_fail(e, "cudaMalloc(error flag)"); }
+
+    if ((e = cudaMemsetAsync(p->d_err, 0, sizeof(int), st))) { free_plan(p); return cuda_fail(e, "clear error flag"); }
     if (p->df) {
         for (int a = 0; a < 3; ++a) {
             if ((e = cudaMalloc(&p->d_twdf[a], (size_t)ns[a] * 32))) { free_plan(p); return cuda_fail(e, "cudaMalloc(df twiddles)"); }
@@ -469,6 +479,33 @@ int vloc_plan_create(vloc_plan* out, int n1, int n2, int n3, const int32_t* g, i
         if ((e = cudaMalloc(&p->d_gamma_buf, 2 * (size_t)p->chunk * npw * elem))) { free_plan(p); return cuda_fail(e, "cudaMalloc(gamma buffers)"); }
         p->ws_bytes += 2 * (size_t)p->chunk * npw * elem;
     }
+    // tensor map over the slab workspace for the persistent TMA x-pass (FP32,
+    // compile-time x length, even n3 so rows are 16-byte multiples)
+    if ((flags & VLOC_X_TMA) && !dbl && p->fast && has_ct(n1) && (n3 % 2) == 0 && NP <= 256) {
+        static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+        if (!encode) {
+            cudaDriverEntryPointQueryResult q;
+            void* fn = nullptr;
+            if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) ==
+                    cudaSuccess && q == cudaDriverEntryPointSuccess)
+                encode = (PFN_cuTensorMapEncodeTiled_v12000)fn;
+        }
+        if (encode) {
+            const cuuint64_t dims[4] = {(cuuint64_t)2 * n3, (cuuint64_t)n2, (cuuint64_t)NP, (cuuint64_t)p->ws_bands};
+            const cuuint64_t strides[3] = {(cuuint64_t)n3 * 8, (cuuint64_t)n2 * n3 * 8, (cuuint64_t)NP * n2 * n3 * 8};
+            const cuuint32_t box[4] = {64, 1, (cuuint32_t)NP, 1};
+            const cuuint32_t estr[4] = {1, 1, 1, 1};
+            if (encode(&p->k3tma.map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, p->d_slab, dims, strides, box, estr,
+                       CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                       CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS) {
+                p->k3tma.base = p->d_slab;
+                p->k3tma.band_bytes = (size_t)NP * n2 * n3 * 8;
+                p->k3tma.err = p->d_err;
+                p->k3tma_on = true;
+            }
+        }
+    }
+
     // dL/dV accumulator [N] followed by the band groups' partial sums [ngroups][N]
     if ((e = cudaMalloc(&p->d_acc, (size_t)N * sizeof(double) * (1 + p->ngroups)))) { free_plan(p); return cuda_fail(e, "cudaMalloc(acc)"); }
     if ((e = cudaStreamSynchronize(st))) { free_plan(p); return cuda_fail(e, "plan create sync"); }
@@ -490,6 +527,7 @@ int vloc_plan_set_schedule(vloc_plan p, int axis, int nst, const int32_t* radix)
     for (int i = 0; i < 4; ++i) p->ax.radix[axis][i] = i < nst ? radix[i] : 0;
     p->fast = 0;
     p->df = false;
+    p->k3tma_on = false;
     for (auto& g : p->graphs)
         if (g.exec) cudaGraphExecDestroy(g.exec);
     p->graphs.clear();
@@ -582,7 +620,7 @@ static int apply_impl(vloc_plan p, const void* c, const void* V, int64_t nb, voi
         int rc;
         if ((rc = launch(p, KK_SCATTER_Z, st, [&] { return launch_k1_scatter_zpass(dbl, p->fast, t, ax, p->d_tw[2], cc, cb, p->d_cyl, st); }))) return rc;
         if ((rc = launch(p, KK_Y_INV, st, [&] { return launch_k2_ypass(dbl, p->fast, +1, t, ax, p->d_tw[1], cb, p->d_cyl, p->d_slab, st); }))) return rc;
-        if ((rc = launch(p, KK_X_V, st, [&] { return launch_k3_xpass_v(dbl, p->fast, t, ax, p->d_tw[0], V, cb, p->d_slab, st); }))) return rc;
+        if ((rc = launch(p, KK_X_V, st, [&] { return launch_k3_xpass_v(dbl, p->fast, t, ax, p->d_tw[0], V, cb, p->d_slab, st, p->k3tma_on ? &p->k3tma : nullptr); }))) return rc;
         if ((rc = launch(p, KK_Y_FWD, st, [&] { return launch_k2_ypass(dbl, p->fast, -1, t, ax, p->d_tw[1], cb, p->d_cyl, p->d_slab, st); }))) return rc;
         if ((rc = launch(p, KK_Z_GATHER, st, [&] { return launch_k4_zpass_gather(dbl, p->fast, t, ax, p->d_tw[2], p->d_cyl, cb, oo, diag, cc, st); }))) return rc;
     }
@@ -765,7 +803,7 @@ int vloc_backward(vloc_plan p, const void* c, const void* gout, const void* V, i
                 // dL/dc = A g continues from g's slab (its z- and y-passes are
                 // already done): x-pass with V, forward y-pass, z-pass + gather
                 void* gg_out = (char*)gc + b0 * bstride;
-                if ((rc = launch(p, KK_X_V, st, [&] { return launch_k3_xpass_v(dbl, p->fast, t, ax, p->d_tw[0], V, cb, slabG, st); }))) return rc;
+                if ((rc = launch(p, KK_X_V, st, [&] { return launch_k3_xpass_v(dbl, p->fast, t, ax, p->d_tw[0], V, cb, slabG, st, p->k3tma_on ? &p->k3tma : nullptr); }))) return rc;
                 if ((rc = launch(p, KK_Y_FWD, st, [&] { return launch_k2_ypass(dbl, p->fast, -1, t, ax, p->d_tw[1], cb, cylG, slabG, st); }))) return rc;
                 if ((rc = launch(p, KK_Z_GATHER, st, [&] { return launch_k4_zpass_gather(dbl, p->fast, t, ax, p->d_tw[2], cylG, cb, gg_out, nullptr, nullptr, st); }))) return rc;
             }
@@ -1041,6 +1079,17 @@ int vloc_apply_host(vloc_plan p, const void* ch, const void* Vh, int64_t nb, voi
     return VLOC_OK;
 }
 
+int vloc_device_status(vloc_plan p) {
+    if (!p) return VLOC_ERR_ARG;
+    if (p->flags & VLOC_HOST_ONLY) return VLOC_OK;
+    int h = 0;
+    cudaError_t e = cudaMemcpy(&h, p->d_err, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e) return cuda_fail(e, "read error flag");
+    if (!h) return VLOC_OK;
+    if ((e = cudaMemset(p->d_err, 0, sizeof(int)))) return cuda_fail(e, "clear error flag");
+    return VLOC_ERR_TIMEOUT;
+}
+
 int vloc_profile(vloc_plan p, int enable) {
     if (!p) return VLOC_ERR_ARG;
     if (p->flags & VLOC_HOST_ONLY) return VLOC_ERR_STATE;
@@ -1091,7 +1140,7 @@ int vloc_get_info(vloc_plan p, vloc_info* info) {
     info->npw = p->npw_user;
     info->nsticks = p->S; info->nplanes = p->NP; info->nparts = p->P;
     info->lines_per_tile = kLinesPerTile;
-    info->path = (p->fast ? 1 : 0) | (p->gamma ? 4 : 0) | (p->df ? 8 : 0);
+    info->path = (p->fast ? 1 : 0) | (p->gamma ? 4 : 0) | (p->df ? 8 : 0) | (p->k3tma_on ? 16 : 0);
     info->chunk_bands = p->chunk;
     info->workspace_bytes = (int64_t)p->ws_bytes;
     for (int a = 0; a < 3; ++a) {

@@ -36,6 +36,7 @@ VLOC_HOST_ONLY = 0x200
 VLOC_GENERIC_KERNELS = 0x400
 VLOC_GAMMA = 0x1000
 VLOC_DOUBLE_FLOAT = 0x2000
+VLOC_X_TMA = 0x4000
 
 # every exported symbol declared in include/vloc.h
 EXPORTS = [
@@ -44,7 +45,7 @@ EXPORTS = [
     "vloc_get_info", "vloc_strerror", "vloc_version", "vloc_last_cuda_error",
     "vloc_profile", "vloc_get_profile", "vloc_get_launch_count", "vloc_apply_noalloc",
     "vloc_plan_set_schedule", "vloc_to_real", "vloc_to_recip", "vloc_density",
-    "vloc_apply_h",
+    "vloc_apply_h", "vloc_device_status",
 ]
 
 KERNEL_NAMES = ["k1_scatter_zpass", "k2_ypass_inv", "k3_xpass_v", "k2_ypass_fwd", "k4_zpass_gather",
@@ -112,6 +113,7 @@ def load(path: str | None = None) -> ctypes.CDLL:
         lib.vloc_get_profile.argtypes = [vp, ctypes.POINTER(VlocKernelStat)]
         lib.vloc_get_launch_count.argtypes = [vp, ctypes.POINTER(i64)]
         lib.vloc_apply_h.argtypes = [vp, vp, vp, vp, i64, vp, vp]
+        lib.vloc_device_status.argtypes = [vp]
         lib.vloc_to_real.argtypes = [vp, vp, i64, vp, vp]
         lib.vloc_to_recip.argtypes = [vp, vp, i64, vp, vp]
         lib.vloc_density.argtypes = [vp, vp, vp, i64, vp, vp]
@@ -165,7 +167,7 @@ class VlocPlan:
 
     def __init__(self, grid, glist, dtype=None, *, partition: str = "greedy", chunk: int = 0,
                  graph: bool = False, host_only: bool = False, generic: bool = False, gamma: bool = False,
-                 double_float: bool = False, stream=None):
+                 double_float: bool = False, x_tma: bool = False, stream=None):
         import torch
         dtype = dtype or torch.complex64
         if dtype not in (torch.complex64, torch.complex128):
@@ -191,6 +193,8 @@ class VlocPlan:
             flags |= VLOC_GAMMA
         if double_float:
             flags |= VLOC_DOUBLE_FLOAT
+        if x_tma:
+            flags |= VLOC_X_TMA
         h = ctypes.c_void_p()
         sp = ctypes.c_void_p(None) if host_only else _stream_ptr(stream)
         _check(self.lib.vloc_plan_create(ctypes.byref(h), *self.grid,
@@ -228,6 +232,7 @@ class VlocPlan:
             "compile_time_kernels": bool(inf.path & 1),
             "gamma": bool(inf.path & 4),
             "double_float": bool(inf.path & 8),
+            "x_tma": bool(inf.path & 16),
         }
 
     def set_schedule(self, axis: int, radices):
@@ -243,6 +248,10 @@ class VlocPlan:
         arr = (VlocKernelStat * len(KERNEL_NAMES))()
         _check(self.lib.vloc_get_profile(self.handle, arr), "vloc_get_profile")
         return {KERNEL_NAMES[i]: (int(arr[i].launches), float(arr[i].total_ms)) for i in range(len(KERNEL_NAMES)) if arr[i].launches}
+
+    def device_status(self) -> int:
+        """Synchronise; VLOC_ERR_TIMEOUT if a bounded in-kernel wait gave up since the last call."""
+        return int(self.lib.vloc_device_status(self.handle))
 
     def launch_count(self) -> int:
         n = ctypes.c_int64()

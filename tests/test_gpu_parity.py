@@ -282,3 +282,28 @@ def test_graph_batched_matches_individual():
         torch.cuda.synchronize()
         for o, (_, _, _, ref) in zip(outs, cases):
             assert torch.equal(o, ref)
+
+
+@pytest.mark.parametrize("n,R,nb,chunk", [((96, 96, 96), 24, 300, 0), ((64, 64, 64), 16, 37, 5),
+                                          ((48, 60, 72), 11, 9, 0), ((32, 48, 96), 8, 20, 7)])
+def test_x_tma_option_is_bit_identical(n, R, nb, chunk):
+    # the persistent TMA x-pass (VLOC_X_TMA) runs the same arithmetic as the
+    # default x-pass: forward and backward results equal bit for bit
+    g, c, V = make_case(n, R, nb, seed=5, order="shuffled", prec="f32")
+    ref_plan, ct, Vt, ref = run(n, g, c, V, "f32", chunk=chunk)
+    plan = vloc.VlocPlan(n, g, torch.complex64, chunk=chunk, x_tma=True)
+    assert plan.info()["x_tma"]
+    out = plan.apply(ct, Vt)
+    gt = torch.from_numpy(synth.coefficients(g, nb, seed=6, dtype=np.complex64)).cuda()
+    gc0, gV0 = ref_plan.backward(ct, gt, Vt)
+    gc1, gV1 = plan.backward(ct, gt, Vt)
+    torch.cuda.synchronize()
+    assert plan.device_status() == 0
+    assert torch.equal(out, ref) and torch.equal(gc0, gc1) and torch.equal(gV0, gV1)
+
+
+def test_x_tma_option_falls_back_for_odd_z():
+    n = (48, 48, 25)
+    g, c, V = make_case(n, 6, 2, seed=5, prec="f32")
+    plan = vloc.VlocPlan(n, g, torch.complex64, x_tma=True)
+    assert not plan.info()["x_tma"]
