@@ -51,6 +51,10 @@ constexpr long long kGradBandsPerGroup = 16;
 #ifndef VLOC_STAGE_RAMP
 #define VLOC_STAGE_RAMP 4
 #endif
+// staging slots (chunks in flight between copy in, compute and copy out), <= 4
+#ifndef VLOC_STAGE_SLOTS
+#define VLOC_STAGE_SLOTS 2
+#endif
 constexpr long long kBatchBranches = 4;  // parallel branches of a batched graph  // bands per group of the dL/dV x-pass (FP32 sums)
 constexpr int kLinesPerTile = 32;
 
@@ -145,7 +149,7 @@ struct vloc_plan_s {
     long long stage_bands = 0;
     cudaStream_t copy_stream = nullptr;  // host-to-device copies
     cudaStream_t d2h_stream = nullptr;   // device-to-host copies
-    cudaEvent_t ev[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+    cudaEvent_t ev[12] = {};  // host-buffer staging: 3 events per staging slot
     int device = 0;
     int smem_optin = 0;
     std::mutex mu;
@@ -1007,7 +1011,9 @@ int vloc_apply_host(vloc_plan p, const void* ch, const void* Vh, int64_t nb, voi
     const long long sb = std::min<long long>(p->chunk, VLOC_STAGE_BANDS);
     const size_t vbytes = (size_t)p->N * re;
     auto align = [](size_t x) { return (x + 255) & ~(size_t)255; };
-    const size_t need = align(vbytes) + 4 * align((size_t)sb * bstride);
+    constexpr int K = VLOC_STAGE_SLOTS;
+    static_assert(K >= 2 && K <= 4, "staging slots");
+    const size_t need = align(vbytes) + 2 * K * align((size_t)sb * bstride);
     cudaError_t e;
     if (p->stage_bytes < need) {
         cudaFree(p->d_stage);
@@ -1024,10 +1030,10 @@ int vloc_apply_host(vloc_plan p, const void* ch, const void* Vh, int64_t nb, voi
     }
     char* base = (char*)p->d_stage;
     char* dV = base;
-    char* slot_in[2];
-    char* slot_out[2];
+    char* slot_in[K];
+    char* slot_out[K];
     size_t off = align(vbytes);
-    for (int s = 0; s < 2; ++s) {
+    for (int s = 0; s < K; ++s) {
         slot_in[s] = base + off; off += align((size_t)sb * bstride);
         slot_out[s] = base + off; off += align((size_t)sb * bstride);
     }
@@ -1050,28 +1056,28 @@ int vloc_apply_host(vloc_plan p, const void* ch, const void* Vh, int64_t nb, voi
         for (long long k = 0; k < m; ++k) sizes.push_back(rest * (k + 1) / m - rest * k / m);
         sizes.insert(sizes.end(), front.rbegin(), front.rend());
     }
-    // per slot s: ev[s] input copied in, ev[2+s] result computed, ev[4+s]
+    // per slot s: ev[s] input copied in, ev[K+s] result computed, ev[2K+s]
     // result copied out.  A slot's input is overwritten only after the chunk
-    // two back has been computed, its output only after that chunk's result
+    // K back has been computed, its output only after that chunk's result
     // has been copied out.
     const int64_t nchunks = (int64_t)sizes.size();
     int64_t b0 = 0;
     for (int64_t i = 0; i < nchunks; b0 += sizes[i], ++i) {
-        const int s = (int)(i & 1);
+        const int s = (int)(i % K);
         const long long cb = sizes[i];
-        if (i >= 2 && (e = cudaStreamWaitEvent(p->copy_stream, p->ev[2 + s], 0))) return cuda_fail(e, "wait");
+        if (i >= K && (e = cudaStreamWaitEvent(p->copy_stream, p->ev[K + s], 0))) return cuda_fail(e, "wait");
         if ((e = cudaMemcpyAsync(slot_in[s], (const char*)ch + b0 * bstride, cb * bstride, cudaMemcpyHostToDevice, p->copy_stream)))
             return cuda_fail(e, "H2D coeffs");
         if ((e = cudaEventRecord(p->ev[s], p->copy_stream))) return cuda_fail(e, "record");
         if ((e = cudaStreamWaitEvent(st, p->ev[s], 0))) return cuda_fail(e, "wait");
-        if (i >= 2 && (e = cudaStreamWaitEvent(st, p->ev[4 + s], 0))) return cuda_fail(e, "wait");
+        if (i >= K && (e = cudaStreamWaitEvent(st, p->ev[2 * K + s], 0))) return cuda_fail(e, "wait");
         int rc = apply_impl(p, slot_in[s], dV, cb, slot_out[s], st);
         if (rc) return rc;
-        if ((e = cudaEventRecord(p->ev[2 + s], st))) return cuda_fail(e, "record");
-        if ((e = cudaStreamWaitEvent(p->d2h_stream, p->ev[2 + s], 0))) return cuda_fail(e, "wait");
+        if ((e = cudaEventRecord(p->ev[K + s], st))) return cuda_fail(e, "record");
+        if ((e = cudaStreamWaitEvent(p->d2h_stream, p->ev[K + s], 0))) return cuda_fail(e, "wait");
         if ((e = cudaMemcpyAsync((char*)oh + b0 * bstride, slot_out[s], cb * bstride, cudaMemcpyDeviceToHost, p->d2h_stream)))
             return cuda_fail(e, "D2H out");
-        if ((e = cudaEventRecord(p->ev[4 + s], p->d2h_stream))) return cuda_fail(e, "record");
+        if ((e = cudaEventRecord(p->ev[2 * K + s], p->d2h_stream))) return cuda_fail(e, "record");
     }
     if ((e = cudaStreamSynchronize(p->d2h_stream))) return cuda_fail(e, "sync copy");
     if ((e = cudaStreamSynchronize(p->copy_stream))) return cuda_fail(e, "sync copy");
