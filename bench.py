@@ -186,9 +186,9 @@ def cpu_oracle_rate(n, g, c, V, nbands_sample):
     cores = host_cores()
     sub = np.ascontiguousarray(c[:nbands_sample].astype(np.complex128))
     t0 = time.perf_counter()
-    O.apply(n, g, sub, V.astype(np.float64), nthreads=cores)
+    ref = O.apply(n, g, sub, V.astype(np.float64), nthreads=cores)
     dt = time.perf_counter() - t0
-    return nbands_sample / dt, cores, dt
+    return nbands_sample / dt, cores, dt, ref
 
 
 # ------------------------------------------------------------------ arms
@@ -332,12 +332,15 @@ def run_ours(args, rank, world, local_rank):
     k64 = max(2, args.steps // 5)
     ms64 = time_steps(lambda: plan64.apply(c128_d, V64_d, out=o128_d), k64, 1, stream, dist_on)
     f64_value = world * NBANDS / (ms64 / k64 / 1e3)
+    ms64a = time_steps(lambda: plan64.apply(c128_d, V64_d, out=o128_d, adjoint=True), k64, 1, stream, dist_on)
+    f64_adj = world * NBANDS / (ms64a / k64 / 1e3)
     plan64.profile(True)
     plan64.apply(c128_d, V64_d, out=o128_d)
     prof64 = plan64.get_profile()
     plan64.profile(False)
     dom64 = max(prof64, key=lambda k: prof64[k][1])
     f64 = {"value": f64_value, "unit": "bands/s", "ms_per_step": ms64 / k64, "steps": k64,
+           "adjoint": {"value": f64_adj, "unit": "bands/s"},
            "speedup_fp32_over_fp64": value / f64_value,
            "roofline": {"bound": "alu", "unit": "GFLOP/s", "achieved": f64_value / world * flops / 1e9,
                         "peak": FP64_NOMINAL_GFLOPS, "frac": f64_value / world * flops / 1e9 / FP64_NOMINAL_GFLOPS,
@@ -516,12 +519,26 @@ def run_ours(args, rank, world, local_rank):
 
     # ---- CPU oracle baseline (rank 0, N = 1 only)
     cpu = None
+    accuracy = None
     if rank == 0 and world == 1 and not args.no_cpu:
         cores = host_cores()
         sample = 2 * cores
-        rate, used, dt = cpu_oracle_rate(GRID, g, c64, V96.astype(np.float32), sample)
+        rate, used, dt, ref = cpu_oracle_rate(GRID, g, c64, V96.astype(np.float32), sample)
         cpu = {"value": rate, "unit": "bands/s", "cores": used, "kind": "oracle",
                "sample": f"{sample} of the 1024 bands (FP64 C oracle, OpenMP over bands), {dt:.1f} s wall"}
+        # accuracy of the timed paths on the same bands (relative L2 per band,
+        # max), next to the speeds
+        def rel(x):
+            x = x.detach().cpu().numpy().astype(np.complex128)
+            return float((np.linalg.norm(x - ref, axis=1) / np.linalg.norm(ref, axis=1)).max())
+        cs = c_d[:sample].contiguous()
+        acc_f32 = rel(plan.apply(cs, V_d))
+        c64s, V64s = cs.to(torch.complex128), V_d.to(torch.float64)
+        acc_f64 = rel(vloc.VlocPlan(GRID, g, torch.complex128).apply(c64s, V64s))
+        acc_df = rel(vloc.VlocPlan(GRID, g, torch.complex128, double_float=True).apply(c64s, V64s))
+        accuracy = {"bands": sample, "f32_max_rel_l2": acc_f32, "f64_max_rel_l2": acc_f64,
+                    "f64_double_float_max_rel_l2": acc_df, "gates": {"f32": 2e-6, "f64": 1e-12},
+                    "reference": "FP64 oracle on the same FP32-rounded inputs"}
 
     if rank == 0:
         line = {
@@ -534,6 +551,7 @@ def run_ours(args, rank, world, local_rank):
             "roofline": roofline, "path": path,
             "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clocks,
             "fp64": f64, "fp64_double_float": f64_df, "adjoint": {"value": adj, "unit": "bands/s"},
+            "accuracy": accuracy,
             "grid_96x96x120": {"value": c2_value, "unit": "bands/s"},
             "batched_uneven": batched, "autograd_512": autograd, "gamma_real": gamma, "half_transforms_density": halves, "eigensolve": eig,
             "cufft_comparison": cufft,
