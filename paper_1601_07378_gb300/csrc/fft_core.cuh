@@ -92,36 +92,17 @@ template <int S> __device__ __forceinline__ P2f mul_si(P2f x) { return {mul_si<S
 template <> __device__ __forceinline__ P2f czero<P2f>() { return {make_float2(0.f, 0.f), make_float2(0.f, 0.f)}; }
 
 // ---------------------------------------------- double-float arithmetic
-// A real value held as hi + lo, two FP32 with |lo| <= ulp(hi) / 2 (about 48
-// significant bits), in a float2 (x = hi, y = lo).  Sums use the two-sum
-// of Knuth / Moller, products an FMA for the rounding error of hi * hi
-// (Dekker's algorithm with a fused multiply-add); each result is
-// renormalised with a fast two-sum.  Errors stay within a few units of
-// 2^-48 relative to the operands' magnitudes, the bound an FFT's norm-wise
-// error analysis needs.
-__device__ __forceinline__ float2 df_add(float2 a, float2 b) {
-    const float s = a.x + b.x;
-    const float bb = s - a.x;
-    const float e = ((a.x - (s - bb)) + (b.x - bb)) + (a.y + b.y);
-    const float hi = s + e;
-    return make_float2(hi, e - (hi - s));
-}
-__device__ __forceinline__ float2 df_neg(float2 a) { return make_float2(-a.x, -a.y); }
+// A real value held as hi + lo, two FP32 (about 48 significant bits).  Sums
+// use the two-sum of Knuth / Moller, products an FMA for the rounding error
+// of hi * hi (Dekker's product with a fused multiply-add); errors stay within
+// a few units of 2^-48 relative to the operands' magnitudes, the bound an
+// FFT's norm-wise error analysis needs.
 __device__ __forceinline__ float2 fneg2_(float2 a) { return make_float2(-a.x, -a.y); }
-__device__ __forceinline__ float2 df_mul(float2 a, float2 b) {
-    const float p = a.x * b.x;
-    float e = fmaf(a.x, b.x, -p);
-    e = fmaf(a.x, b.y, e);
-    e = fmaf(a.y, b.x, e);
-    const float hi = p + e;
-    return make_float2(hi, e - (hi - p));
-}
 // hi + lo split of a double (hi = nearest FP32, lo = nearest FP32 of the rest)
 __host__ __device__ __forceinline__ float2 df_split(double v) {
     const float hi = (float)v;
     return make_float2(hi, (float)(v - (double)hi));
 }
-__device__ __forceinline__ double df_value(float2 a) { return (double)a.x + (double)a.y; }
 
 // Complex double-float value held as a pair of high parts and a pair of low
 // parts, hi = (re.hi, im.hi), lo = (re.lo, im.lo): the real and imaginary
