@@ -146,13 +146,12 @@ def chfsi(H: Hamiltonian, nev: int, *, nblock: int | None = None, degree: int = 
         raise ValueError("block larger than the basis")
     dev = H.V.device
     if X0 is None:
-        gen = torch.Generator(device="cpu").manual_seed(seed)
-        Xr = torch.randn(nb, npw, generator=gen, dtype=torch.float64)
-        Xi = torch.randn(nb, npw, generator=gen, dtype=torch.float64)
-        X = torch.complex(Xr, Xi)
-        # start from smooth bands: damp large |G|
-        X = X / (1.0 + H.T.double().cpu())[None, :]
-        X = X.to(device=dev, dtype=plan.dtype)
+        # seeded random start, drawn on the device; smooth bands (large |G| damped)
+        gen = torch.Generator(device=dev).manual_seed(seed)
+        rdt = plan.real_dtype
+        X = torch.complex(torch.randn(nb, npw, generator=gen, dtype=rdt, device=dev),
+                          torch.randn(nb, npw, generator=gen, dtype=rdt, device=dev))
+        X = (X / (1.0 + H.T)[None, :]).to(plan.dtype)
     else:
         X = X0.to(device=dev, dtype=plan.dtype).clone()
     if H.gamma:
