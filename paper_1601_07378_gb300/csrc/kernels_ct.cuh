@@ -32,6 +32,11 @@
 #ifndef VLOC_K3_WARPS
 #define VLOC_K3_WARPS 4
 #endif
+// Warps per x-pass CTA by length, measured on GB300 (cubic grids, 1024
+// bands): the units of a stage spread over 2 W slots, so 100 = 10 x 10 wants
+// 5 warps and 120 = 12 x 10, 144 = 12 x 12 want 6 (K3 2.97 / 4.47 / 7.94 ms
+// against 3.53 / 5.28 / 10.23 with 4); 96 and 128 keep 4.
+constexpr int k3_warps(int n) { return n == 100 ? 5 : (n == 120 || n == 144) ? 6 : VLOC_K3_WARPS; }
 #ifndef VLOC_MINB_K4
 #define VLOC_MINB_K4 6
 #endif
@@ -39,6 +44,19 @@
 namespace vloc {
 
 constexpr int minb(int n, int m) { return n <= 96 ? m : 1; }
+// Resident-CTA floors of the z/y-pass kernels above length 96, measured on
+// GB300 (cubic grids, R = n/4, 1024 bands; floors 1, 4 and 5 compared, ms):
+// K1 at 100: 0.57 with 5 against 0.64; K2 inverse at 100 / 120 / 128 / 144:
+// 1.30 (5) / 2.35 (4) / 1.83 (5) / 3.87 (4) against 1.40 / 2.49 / 2.03 / 4.95;
+// K2 forward at 100: 1.23 (5) against 1.45; K4 at 120: 1.07 (5) against 1.15.
+// Elsewhere a floor measured the same or slower (K4 at 128: 1.59 with 4).
+constexpr int minb_k1(int n) { return n <= 96 ? VLOC_MINB_K1 : n == 100 ? 5 : 1; }
+constexpr int minb_k2(int n, int s) {
+    return n <= 96 ? VLOC_MINB_K2
+           : s > 0 ? ((n == 100 || n == 128) ? 5 : (n == 120 || n == 144) ? 4 : 1)
+                   : (n == 100 ? 5 : 1);
+}
+constexpr int minb_k4(int n) { return n <= 96 ? VLOC_MINB_K4 : n == 120 ? 5 : 1; }
 
 template <int N> __host__ __device__ constexpr size_t ct_smem() {
     return (size_t)N * kLdP * sizeof(float2) + (size_t)N * sizeof(float2) + (size_t)N * sizeof(int) + 16;
@@ -211,7 +229,7 @@ struct XRowsP {  // x rows at fixed y: the occupied planes
 
 // ------------------------------------------------------------------ K1
 template <int N>
-__global__ void __launch_bounds__(kThreads, minb(N, VLOC_MINB_K1)) k1_ct(DevTables t, const float2* __restrict__ tw3,
+__global__ void __launch_bounds__(kThreads, minb_k1(N)) k1_ct(DevTables t, const float2* __restrict__ tw3,
                                                  const float2* __restrict__ coeffs, float2* __restrict__ cyl) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float2* buf = reinterpret_cast<float2*>(smem_raw);
@@ -229,7 +247,7 @@ __global__ void __launch_bounds__(kThreads, minb(N, VLOC_MINB_K1)) k1_ct(DevTabl
 
 // ------------------------------------------------------------------ K2
 template <int S, int N>
-__global__ void __launch_bounds__(kThreads, minb(N, VLOC_MINB_K2)) k2_ct(DevTables t, const float2* __restrict__ tw2, float2* cyl,
+__global__ void __launch_bounds__(kThreads, minb_k2(N, S)) k2_ct(DevTables t, const float2* __restrict__ tw2, float2* cyl,
                                                  float2* slab) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int n3 = t.n3;
@@ -332,7 +350,7 @@ __global__ void __launch_bounds__(32 * W, minb(N, VLOC_MINB_K3)) k3_ct(DevTables
 
 // ------------------------------------------------------------------ K4
 template <int N>
-__global__ void __launch_bounds__(kThreads, minb(N, VLOC_MINB_K4)) k4_ct(DevTables t, const float2* __restrict__ tw3,
+__global__ void __launch_bounds__(kThreads, minb_k4(N)) k4_ct(DevTables t, const float2* __restrict__ tw3,
                                                  const float2* __restrict__ cyl, float2* out, float scale,
                                                  const float* __restrict__ diag, const float2* cin) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -602,10 +620,11 @@ template <typename T, int N>
 int LaunchCT<T, N>::k3(const DevTables& t, const void* tw1, const void* V, long long nb, void* slab, const K3Tma* tma,
                        cudaStream_t st) {
     if (tma) return launch_k3_tma<N>(t, tw1, V, nb, slab, *tma, st);
-    static const cudaError_t once = CtSmem<N>::ensure(k3_ct<N, VLOC_K3_WARPS>);
+    constexpr int W = k3_warps(N);
+    static const cudaError_t once = CtSmem<N>::ensure(k3_ct<N, W>);
     if (once) return (int)once;
     const dim3 grid(t.n2, (t.n3 + kLines - 1) / kLines, (unsigned)nb);
-    k3_ct<N, VLOC_K3_WARPS><<<grid, 32 * VLOC_K3_WARPS, CtSmem<N>::sm, st>>>(t, (const float2*)tw1, (const float*)V,
+    k3_ct<N, W><<<grid, 32 * W, CtSmem<N>::sm, st>>>(t, (const float2*)tw1, (const float*)V,
                                                                            (float2*)slab);
     return (int)cudaGetLastError();
 }
