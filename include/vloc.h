@@ -136,8 +136,9 @@ typedef struct vloc_info {
  *                -G must be a valid index too (else VLOC_ERR_GLIST), and
  *                npw counts the half list (the caller's arrays).
  *   max_bands_per_chunk : bands per workspace chunk (<= 0: automatic, a
- *                2 GiB workspace capped at 1/8 of the free device memory;
- *                large chunks keep every kernel many waves deep).
+ *                6 GiB workspace capped at 1/16 of the free device memory
+ *                and at 2048 bands; large chunks keep every kernel many
+ *                waves deep).
  *   stream     : stream used for the one-time table uploads (synchronised
  *                before return).
  * Errors: VLOC_ERR_ARG, VLOC_ERR_SIZE, VLOC_ERR_GLIST, VLOC_ERR_ALLOC,

@@ -69,13 +69,15 @@ def test_config1_64cubed_256_bands_sampled(prec):
 
 
 @pytest.mark.parametrize("prec", ["f32", "f64"])
-@pytest.mark.parametrize("n", [(96, 96, 120), (96, 96, 96), (128, 128, 128), (144, 144, 144)])
-def test_full_size_1024_bands_sampled(prec, n):
-    # The bench's launch configuration (default plan, 1024 bands), sampled
-    # bands from the first, middle and last workspace chunks.
+@pytest.mark.parametrize("n,chunk", [((96, 96, 120), 0), ((96, 96, 96), 0), ((96, 96, 96), 430),
+                                     ((128, 128, 128), 0), ((144, 144, 144), 0)])
+def test_full_size_1024_bands_sampled(prec, n, chunk):
+    # The bench's launch configuration (default plan, 1024 bands; and 430-band
+    # chunks, three chunks per step), sampled bands from the first, middle and
+    # last workspace chunks.
     R, nb = n[0] // 4, (1024 if n[0] == 96 else 64)
     g, c, V = make_case(n, R, nb, seed=2, prec=prec)
-    plan, _, _, out = run(n, g, c, V, prec)
+    plan, _, _, out = run(n, g, c, V, prec, chunk=chunk)
     chunk = plan.info()["chunk_bands"]
     bands = sorted({b for b in (0, chunk - 1, chunk, nb // 2, nb - 1) if b < nb})
     err = rel_l2_per_band(out.cpu().numpy()[bands], oracle_apply(n, g, c, V, bands))
@@ -199,6 +201,29 @@ def test_batched_matches_individual():
     torch.cuda.synchronize()
     for o, (_, _, _, ref) in zip(outs, cases):
         assert torch.equal(o, ref)
+
+
+def test_uneven_batch_full_size_sampled():
+    # The uneven multi-instance workload at full size, as the bench launches
+    # it: 8 cubic grids 48..144, R = n/4, 64 (i + 1) bands each, FP32, one
+    # graph-captured batched launch (captured, then replayed); the first and
+    # last band of every instance against the oracle.
+    cases = []
+    for i, m in enumerate(synth.BATCH_GRIDS):
+        n = (m, m, m)
+        g, c, V = make_case(n, m / 4, 64 * (i + 1), seed=3 + i, prec="f32")
+        plan = vloc.VlocPlan(n, g, torch.complex64, graph=True, chunk=64 * (i + 1))
+        cases.append((n, g, c, V, plan, torch.from_numpy(c).cuda(), torch.from_numpy(V).cuda()))
+    outs = [torch.empty_like(ct) for *_, ct, _ in cases]
+    for _ in range(2):
+        for o in outs:
+            o.zero_()
+        vloc.apply_batched([p for *_, p, _, _ in cases], [ct for *_, ct, _ in cases], [Vt for *_, Vt in cases], outs)
+        torch.cuda.synchronize()
+    for (n, g, c, V, *_), o in zip(cases, outs):
+        bands = [0, c.shape[0] - 1]
+        err = rel_l2_per_band(o.cpu().numpy()[bands], oracle_apply(n, g, c, V, bands))
+        assert err.max() < TOL["f32"], (n, err.max())
 
 
 @pytest.mark.parametrize("prec", ["f32", "f64"])
