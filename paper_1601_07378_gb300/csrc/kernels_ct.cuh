@@ -37,6 +37,14 @@
 // 5 warps and 120 = 12 x 10, 144 = 12 x 12 want 6 (K3 2.97 / 4.47 / 7.94 ms
 // against 3.53 / 5.28 / 10.23 with 4); 96 and 128 keep 4.
 constexpr int k3_warps(int n) { return n == 100 ? 5 : (n == 120 || n == 144) ? 6 : VLOC_K3_WARPS; }
+// x-pass resident-CTA floors above length 96, measured on GB300 (cubic
+// grids, 1024 bands; K3 ms without a floor -> with it): 100 (6 CTAs of 5
+// warps) 2.96 -> 2.59, 120 (5 of 6) 4.44 -> 4.00, 128 (5 of 4) 4.16 -> 4.06,
+// 144 (4 of 6) 7.88 -> 6.89.  One CTA more per SM spilled and measured slower
+// at every length (144: 7.54).
+constexpr int minb_k3(int n) {
+    return n <= 96 ? VLOC_MINB_K3 : n == 100 ? 6 : n == 120 ? 5 : n == 128 ? 5 : n == 144 ? 4 : 1;
+}
 #ifndef VLOC_MINB_K4
 #define VLOC_MINB_K4 6
 #endif
@@ -273,7 +281,7 @@ __global__ void __launch_bounds__(kThreads, minb_k2(N, S)) k2_ct(DevTables t, co
 // ------------------------------------------------------------------ K3
 // W warps per CTA (the tile is always 32 lines; more warps split its units).
 template <int N, int W>
-__global__ void __launch_bounds__(32 * W, minb(N, VLOC_MINB_K3)) k3_ct(DevTables t, const float2* __restrict__ tw1,
+__global__ void __launch_bounds__(32 * W, minb_k3(N)) k3_ct(DevTables t, const float2* __restrict__ tw1,
                                                  const float* __restrict__ Vr, float2* slab) {
     using SC = Sched<N>;
     constexpr int nst = SC::nst;
