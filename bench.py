@@ -30,6 +30,7 @@ sys.path.insert(0, ROOT)
 METRIC = "V_loc|ψ⟩ bands/s at 96^3 (FP32 vs FP64), fraction of HBM roofline"
 GRID, R, NBANDS, SEED = (96, 96, 96), 24, 1024, 2
 GRID2 = (96, 96, 120)
+WORKLOAD = "96^3 grid, sphere h^2+k^2+l^2<=24^2 (57777 PWs), 1024 bands/GPU, FP32 forward apply"
 FALLBACK_HBM_GBS = 6800.0
 FP64_NOMINAL_GFLOPS = 1250.0   # 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz ~ 1.26 TF/s
 KERNEL_SOURCES = ["paper_1601_07378_gb300/csrc/fft_core.cuh", "paper_1601_07378_gb300/csrc/fft_ct.cuh",
@@ -241,7 +242,8 @@ def run_reference(args, rank):
         "impl": "reference", "metric": METRIC, "value": value, "unit": "bands/s", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": "96^3 grid, sphere R=24 (57777 PWs), CPU oracle sample", "bands_per_step": per},
+        "config": {"workload": WORKLOAD, "grid": list(GRID), "npw": len(g), "bands_per_gpu": NBANDS,
+                   "sample_bands_per_step": per, "parallelism": f"host cores x{cores}"},
         "cpu_baseline": {"value": value, "unit": "bands/s", "cores": cores, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": "bands/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
@@ -580,7 +582,7 @@ def run_ours(args, rank, world, local_rank):
             "metric": METRIC, "value": value, "unit": "bands/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": "96^3 grid, sphere h^2+k^2+l^2<=24^2 (57777 PWs), 1024 bands/GPU, FP32 forward apply",
+            "config": {"workload": WORKLOAD,
                        "grid": list(GRID), "npw": info["npw"], "bands_per_gpu": NBANDS, "chunk_bands": info["chunk_bands"],
                        "l2": "inputs larger than L2 (473 MB in + 473 MB out per step)", "parallelism": f"bands x{world}"},
             "roofline": roofline, "path": path,
