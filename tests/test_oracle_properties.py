@@ -1,0 +1,88 @@
+"""Property-based pins of the oracle on random small grids and arbitrary
+G-lists (hypothesis; skipped where it is not installed).
+
+Each example draws a grid (every axis 2..9, odd and even), a random subset of
+the valid Miller indices, random bands and a random real V, and checks the C
+oracle against what the mathematics fixes:
+- Eqs. 2-3 summed plane wave by plane wave (brute force, no FFT, no DFT
+  matrix): the action, the G -> r transform and the r -> G transform;
+- linearity and Hermiticity of the action for real V;
+- the G -> r -> G round trip is the identity;
+- Parseval for the density of Sec. 3.1.
+"""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+
+hyp = pytest.importorskip("hypothesis")
+st = pytest.importorskip("hypothesis.strategies")
+given, settings = hyp.given, hyp.settings
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    O.build()
+
+
+def _case(n, seed, frac, nb):
+    rng = np.random.default_rng(seed)
+    axes = [np.arange(-(m // 2), (m + 1) // 2) for m in n]          # valid index range per axis
+    cube = np.array(np.meshgrid(*axes, indexing="ij")).reshape(3, -1).T
+    keep = rng.random(len(cube)) < frac
+    keep[rng.integers(len(cube))] = True                             # never empty
+    g = np.ascontiguousarray(cube[keep][rng.permutation(int(keep.sum()))].astype(np.int32))
+    c = rng.standard_normal((nb, len(g))) + 1j * rng.standard_normal((nb, len(g)))
+    V = rng.standard_normal(n)
+    return g, c, V
+
+
+def _rel(a, b):
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+grids = st.tuples(st.integers(2, 9), st.integers(2, 9), st.integers(2, 9))
+common = dict(max_examples=25, deadline=None)
+
+
+@settings(**common)
+@given(n=grids, seed=st.integers(0, 2**31 - 1), frac=st.floats(0.05, 1.0))
+def test_action_equals_plane_wave_sums(n, seed, frac):
+    g, c, V = _case(n, seed, frac, 2)
+    assert _rel(O.apply(n, g, c, V), O.bf_apply(n, g, c, V)) < 1e-12
+
+
+@settings(**common)
+@given(n=grids, seed=st.integers(0, 2**31 - 1), frac=st.floats(0.05, 1.0))
+def test_half_transforms_equal_plane_wave_sums_and_round_trip(n, seed, frac):
+    g, c, _ = _case(n, seed, frac, 2)
+    psi = O.to_real(n, g, c)
+    assert _rel(psi, O.bf_to_real(n, g, c)) < 1e-12
+    rng = np.random.default_rng(seed + 1)
+    u = rng.standard_normal((2,) + tuple(n)) + 1j * rng.standard_normal((2,) + tuple(n))
+    assert _rel(O.to_recip(n, g, u), O.bf_to_recip(n, g, u)) < 1e-12
+    assert _rel(O.to_recip(n, g, psi), c) < 1e-12
+
+
+@settings(**common)
+@given(n=grids, seed=st.integers(0, 2**31 - 1), frac=st.floats(0.05, 1.0),
+       a=st.complex_numbers(max_magnitude=3, allow_nan=False, allow_infinity=False))
+def test_action_is_linear_and_hermitian(n, seed, frac, a):
+    g, c, V = _case(n, seed, frac, 2)
+    x, y = c[0:1], c[1:2]
+    Ax, Ay = O.apply(n, g, x, V), O.apply(n, g, y, V)
+    assert _rel(O.apply(n, g, a * x + y, V), a * Ax + Ay) < 1e-12
+    lhs, rhs = np.vdot(x, Ay), np.vdot(Ax, y)
+    assert abs(lhs - rhs) <= 1e-12 * max(1.0, abs(lhs))
+
+
+@settings(**common)
+@given(n=grids, seed=st.integers(0, 2**31 - 1), frac=st.floats(0.05, 1.0))
+def test_density_parseval(n, seed, frac):
+    g, c, _ = _case(n, seed, frac, 3)
+    occ = np.array([2.0, 1.0, 0.5])
+    rho = O.density(n, g, c, occ)
+    N = int(np.prod(n))
+    want = N * float((occ[:, None] * np.abs(c) ** 2).sum())
+    assert abs(rho.sum() - want) <= 1e-12 * want
+    assert rho.min() >= 0.0
