@@ -172,7 +172,8 @@ def grads(n, g, c, V, gout, nthreads: int = 0):
 
 def axis_dft(n, grids, axis: int, sign: int, nthreads: int = 0) -> np.ndarray:
     """One naive DFT pass along an axis of full grids (copy returned)."""
-    a = np.array(grids, dtype=np.complex128, copy=True).reshape(-1, n[0], n[1], n[2])
+    # C order whatever the input's strides: the C side reads the buffer as [nb][n1][n2][n3]
+    a = np.array(grids, dtype=np.complex128, order="C", copy=True).reshape(-1, n[0], n[1], n[2])
     _check(_load().oracle_axis_dft(n[0], n[1], n[2], _p(a.view(np.float64), ctypes.c_double),
                                    a.shape[0], axis, sign, nthreads))
     return a

@@ -150,3 +150,76 @@ def test_planted_gamma_mistake_is_caught(monkeypatch, bad):
     except O.OracleError:
         caught = True
     assert caught
+
+
+# ---- planted mistakes in the r -> G transform and the density (Python side)
+def _recip_no_norm(n, g, u, nthreads=0):
+    return O.to_recip(n, g, u, nthreads) * (n[0] * n[1] * n[2])
+
+
+def _recip_wrong_sign(n, g, u, nthreads=0):
+    N = n[0] * n[1] * n[2]
+    a = np.asarray(u, dtype=np.complex128).reshape(-1, *n)
+    for axis in range(3):
+        a = O.axis_dft(n, a, axis, +1, nthreads)
+    return a.reshape(a.shape[0], N)[:, O.index_map(n, g)] / N
+
+
+def _recip_gather_at_minus_G(n, g, u, nthreads=0):
+    N = n[0] * n[1] * n[2]
+    a = np.asarray(u, dtype=np.complex128).reshape(-1, *n)
+    for axis in range(3):
+        a = O.axis_dft(n, a, axis, -1, nthreads)
+    h, k, l = (-np.asarray(g, dtype=np.int64)).T
+    idx = ((h % n[0]) * n[1] + (k % n[1])) * n[2] + (l % n[2])
+    return a.reshape(a.shape[0], N)[:, idx] / N
+
+
+def _density_no_occ(n, g, c, occ=None, nthreads=0):
+    return O.density(n, g, c, None, nthreads)
+
+
+def _density_abs_not_squared(n, g, c, occ=None, nthreads=0):
+    psi = O.to_real(n, g, c, nthreads)
+    f = np.ones(psi.shape[0]) if occ is None else np.asarray(occ, dtype=np.float64)
+    return np.tensordot(f, np.abs(psi), axes=1)
+
+
+def _density_real_part_only(n, g, c, occ=None, nthreads=0):
+    psi = O.to_real(n, g, c, nthreads)
+    f = np.ones(psi.shape[0]) if occ is None else np.asarray(occ, dtype=np.float64)
+    return np.tensordot(f, psi.real ** 2, axes=1)
+
+
+def _half_pins_fail(to_recip, density):
+    """True when a pin of the r -> G transform or of the density (point-by-point
+    sums of Eqs. 2-3, the G -> r -> G round trip, Parseval) rejects them."""
+    n = (4, 6, 5)
+    g = synth.sphere_glist(*n, 2.2, order="shuffled", seed=1)
+    c = synth.coefficients(g, 3, seed=5)
+    rng = np.random.default_rng(9)
+    u = rng.standard_normal((2, *n)) + 1j * rng.standard_normal((2, *n))
+    fails = 0
+    fails += np.linalg.norm(to_recip(n, g, u) - O.bf_to_recip(n, g, u)) > 1e-10 * np.linalg.norm(O.bf_to_recip(n, g, u))
+    fails += np.linalg.norm(to_recip(n, g, O.bf_to_real(n, g, c)) - c) > 1e-10 * np.linalg.norm(c)
+    occ = np.array([2.0, 1.0, 0.5])
+    rho = density(n, g, c, occ)
+    want = np.tensordot(occ, np.abs(O.bf_to_real(n, g, c)) ** 2, axes=1)
+    fails += np.abs(rho - want).max() > 1e-10 * np.abs(want).max()
+    N = n[0] * n[1] * n[2]
+    fails += abs(rho.sum() - N * float((occ[:, None] * np.abs(c) ** 2).sum())) > 1e-10 * rho.sum()
+    return fails > 0
+
+
+def test_unmutated_half_transforms_pass():
+    assert not _half_pins_fail(O.to_recip, O.density)
+
+
+@pytest.mark.parametrize("bad", [_recip_no_norm, _recip_wrong_sign, _recip_gather_at_minus_G])
+def test_planted_to_recip_mistake_is_caught(bad):
+    assert _half_pins_fail(bad, O.density), bad.__name__
+
+
+@pytest.mark.parametrize("bad", [_density_no_occ, _density_abs_not_squared, _density_real_part_only])
+def test_planted_density_mistake_is_caught(bad):
+    assert _half_pins_fail(O.to_recip, bad), bad.__name__

@@ -86,3 +86,16 @@ def test_density_parseval(n, seed, frac):
     want = N * float((occ[:, None] * np.abs(c) ** 2).sum())
     assert abs(rho.sum() - want) <= 1e-12 * want
     assert rho.min() >= 0.0
+
+
+@settings(**common)
+@given(n=grids, seed=st.integers(0, 2**31 - 1), frac=st.floats(0.05, 1.0))
+def test_r_to_G_is_invariant_under_relabelled_axes(n, seed, frac):
+    # exchanging the first two grid axes of u and of every G is a relabelling:
+    # the transform must not change (the exchanged u is a strided view, so this
+    # also checks that the wrapper hands C-ordered memory to the C side)
+    g, _, _ = _case(n, seed, frac, 1)
+    rng = np.random.default_rng(seed + 2)
+    u = rng.standard_normal((2,) + tuple(n)) + 1j * rng.standard_normal((2,) + tuple(n))
+    swapped = O.to_recip((n[1], n[0], n[2]), g[:, [1, 0, 2]], u.transpose(0, 2, 1, 3))
+    assert _rel(swapped, O.to_recip(n, g, u)) < 1e-12
