@@ -284,6 +284,12 @@ class VlocPlan:
         if not V.is_cuda or V.dtype != self.real_dtype or not V.is_contiguous() or V.numel() != np.prod(self.grid):
             raise ValueError(f"V must be a contiguous CUDA {self.real_dtype} tensor with {np.prod(self.grid)} elements")
 
+    def _check_out(self, out, c, name="out"):
+        # the kernels write as many bands as they read: a smaller buffer would be overrun
+        self._check_c(out, name)
+        if out.numel() != c.numel():
+            raise ValueError(f"{name} must hold as many bands as the input ({c.numel() // self.npw})")
+
     # ---------------------------------------------------------------- calls
     def apply(self, c, V, out=None, *, adjoint: bool = False, stream=None):
         """out = A c (or A^H c) for c of shape [..., npw]."""
@@ -293,7 +299,7 @@ class VlocPlan:
         if out is None:
             out = torch.empty_like(c)
         else:
-            self._check_c(out, "out")
+            self._check_out(out, c)
         nb = c.numel() // self.npw
         fn = self.lib.vloc_apply_adjoint if adjoint else self.lib.vloc_apply
         _check(fn(self.handle, _ptr(c), _ptr(V), nb, _ptr(out), _stream_ptr(stream)),
@@ -310,7 +316,7 @@ class VlocPlan:
         if out is None:
             out = torch.empty_like(c)
         else:
-            self._check_c(out, "out")
+            self._check_out(out, c)
         nb = c.numel() // self.npw
         _check(self.lib.vloc_apply_h(self.handle, _ptr(c), _ptr(V), _ptr(diag), nb, _ptr(out), _stream_ptr(stream)),
                "vloc_apply_h")
@@ -354,6 +360,8 @@ class VlocPlan:
             out = torch.empty((nb, self.npw), dtype=self.dtype, device=u.device)
         else:
             self._check_c(out, "out")
+            if out.numel() != nb * self.npw:
+                raise ValueError(f"out must hold nb = {nb} bands of npw = {self.npw}")
         _check(self.lib.vloc_to_recip(self.handle, _ptr(u), nb, _ptr(out), _stream_ptr(stream)), "vloc_to_recip")
         return out
 
@@ -367,6 +375,9 @@ class VlocPlan:
             raise ValueError(f"occ must be a contiguous CUDA {self.real_dtype} tensor of nb weights")
         if rho is None:
             rho = torch.empty(self.grid, dtype=self.real_dtype, device=c.device)
+        elif not rho.is_cuda or rho.dtype != self.real_dtype or not rho.is_contiguous() or \
+                rho.numel() != int(np.prod(self.grid)):
+            raise ValueError(f"rho must be a contiguous CUDA {self.real_dtype} tensor with {np.prod(self.grid)} elements")
         _check(self.lib.vloc_density(self.handle, _ptr(c), _ptr(occ) if occ is not None else None, nb, _ptr(rho),
                                      _stream_ptr(stream)), "vloc_density")
         return rho
@@ -378,10 +389,13 @@ class VlocPlan:
             raise ValueError("apply_host takes CPU tensors")
         if c_host.dtype != self.dtype or not c_host.is_contiguous() or c_host.shape[-1] != self.npw:
             raise ValueError("bad host coefficients")
-        if V_host.dtype != self.real_dtype or not V_host.is_contiguous():
+        if V_host.dtype != self.real_dtype or not V_host.is_contiguous() or V_host.numel() != np.prod(self.grid):
             raise ValueError("bad host V")
         if out_host is None:
             out_host = torch.empty_like(c_host, pin_memory=c_host.is_pinned())
+        elif out_host.is_cuda or out_host.dtype != self.dtype or not out_host.is_contiguous() or \
+                out_host.numel() != c_host.numel():
+            raise ValueError("out_host must be a contiguous host tensor shaped like the coefficients")
         nb = c_host.numel() // self.npw
         _check(self.lib.vloc_apply_host(self.handle, _ptr(c_host), _ptr(V_host), nb, _ptr(out_host),
                                         _stream_ptr(stream)), "vloc_apply_host")
@@ -394,10 +408,12 @@ def apply_batched(plans, cs, Vs, outs=None, *, stream=None):
     n = len(plans)
     if outs is None:
         outs = [torch.empty_like(c) for c in cs]
+    if not (len(cs) == len(Vs) == len(outs) == n):
+        raise ValueError("plans, coefficients, potentials and outputs must have one entry per instance")
     for p, c, V, o in zip(plans, cs, Vs, outs):
         p._check_c(c)
         p._check_V(V)
-        p._check_c(o, "out")
+        p._check_out(o, c)
     arr = lambda xs: (ctypes.c_void_p * n)(*[ctypes.c_void_p(x) for x in xs])
     nbs = (ctypes.c_int64 * n)(*[c.numel() // p.npw for p, c in zip(plans, cs)])
     lib = load()

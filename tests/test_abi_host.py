@@ -83,6 +83,27 @@ def test_host_only_plan_refuses_device_calls(lib):
     assert lib.vloc_plan_destroy(h) == 0
 
 
+def test_host_buffer_entry_checks_sizes_before_the_call(lib):
+    # the binding rejects host buffers that the copies would overrun; valid
+    # buffers reach the C side, which refuses a host-only plan
+    torch = pytest.importorskip("torch")
+    n = (8, 8, 8)
+    g = synth.sphere_glist(*n, 2)
+    plan = vloc.VlocPlan(n, g, torch.complex64, host_only=True)
+    c = torch.zeros(3, len(g), dtype=torch.complex64)
+    V = torch.zeros(n, dtype=torch.float32)
+    with pytest.raises(ValueError):
+        plan.apply_host(c, V, torch.zeros(2, len(g), dtype=torch.complex64))       # one band short
+    with pytest.raises(ValueError):
+        plan.apply_host(c, V, torch.zeros(3, len(g), dtype=torch.complex128))      # wrong precision
+    with pytest.raises(ValueError):
+        plan.apply_host(c, torch.zeros(8 * 8 * 7, dtype=torch.float32))            # V too small
+    import types
+    with pytest.raises(vloc.VlocError) as ei:       # a null stream: no CUDA context is needed here
+        plan.apply_host(c, V, torch.zeros_like(c), stream=types.SimpleNamespace(cuda_stream=0))
+    assert ei.value.code == vloc.VLOC_ERR_STATE
+
+
 @pytest.mark.parametrize("n,R,order", [((24, 24, 24), 6, "canonical"), ((64, 64, 64), 16, "shuffled"),
                                        ((96, 96, 120), 24, "canonical"), ((6, 5, 4), 2.0, "shuffled"),
                                        ((96, 96, 96), 24, "shuffled")])
