@@ -92,6 +92,11 @@ extern "C" {
                                        /* the default x-pass at 96^3, kept opt-in.   */
                                        /* Its waits are bounded: see                 */
                                        /* vloc_device_status.                        */
+#define VLOC_POISON_WORKSPACE   0x10000 /* test aid: fill the plan's cylinder and   */
+                                       /* slab workspace with NaN bytes before every */
+                                       /* workspace chunk, so a pass that reads a    */
+                                       /* cell its chunk never wrote shows up as a   */
+                                       /* non-finite result (slower; not for use)    */
 #define VLOC_HOST_ONLY          0x200  /* build host tables only (no device memory, */
                                        /* no CUDA call); for introspection: the     */
                                        /* device calls then return VLOC_ERR_STATE   */
@@ -292,14 +297,21 @@ int vloc_get_info(vloc_plan plan, vloc_info* info);
  * Instead of the plan's workspace it uses one fixed scratch array compiled
  * into the library: 48 MiB of device memory per GPU that loads the library,
  * held until the process exits.  The index tables and twiddles are rebuilt
- * in that array from the plan's host-side data on every call, so `plan` may
- * be a VLOC_HOST_ONLY plan (which made no CUDA call at all); together the
- * two never allocate device memory.  The caller passes inputs and outputs as
+ * in that array on every call from the plan's host-side data (a block the
+ * plan keeps unchanged until it is destroyed), so `plan` may be a
+ * VLOC_HOST_ONLY plan (which made no CUDA call at all); together the two
+ * never allocate device memory.  The caller passes inputs and outputs as
  * for vloc_apply (same layouts, alignment, alias and overlap rules).
- *   Limit: the tables, twiddles and the workspace of at least one band must
- *   fit in the 48 MiB (index tables at most 8 MiB); otherwise the call
- *   returns VLOC_ERR_SIZE before doing any device work.  Bands are processed
- *   in chunks that fit.
+ *   Kernels: the plan's own choice -- compile-time-length or runtime-radix
+ *   kernels (VLOC_GENERIC_KERNELS, vloc_plan_set_schedule), and the
+ *   double-float kernels for a VLOC_DOUBLE_FLOAT plan.
+ *   Not for VLOC_GAMMA plans: they return VLOC_ERR_STATE before any CUDA
+ *   call is made.
+ *   Limit: the tables, twiddles (for a double-float plan also V as hi + lo
+ *   pairs, 8 bytes per grid point) and the workspace of at least one band
+ *   must fit in the 48 MiB (index tables at most 8 MiB); otherwise the call
+ *   returns VLOC_ERR_SIZE before doing any device work.  Bands are
+ *   processed in chunks that fit.
  *   Set-up: the first call on each device looks up the array's device
  *   address (with that device current); make that first call before any
  *   stream capture.
@@ -307,7 +319,8 @@ int vloc_get_info(vloc_plan plan, vloc_info* info);
  *   nothing in it needs to start at zero.  Calls that overlap on the GPU
  *   (different streams, or interleaved work from several host threads) race
  *   on the array and must be serialised by the caller.
- * Errors: VLOC_ERR_ARG, VLOC_ERR_SIZE, VLOC_ERR_CUDA.
+ * Errors: VLOC_ERR_ARG, VLOC_ERR_SIZE, VLOC_ERR_STATE (Gamma plan),
+ * VLOC_ERR_CUDA.
  */
 int vloc_apply_noalloc(vloc_plan plan, const void* coeffs, const void* V, int64_t nbands, void* out,
                        void* stream);
@@ -344,6 +357,29 @@ int vloc_get_launch_count(vloc_plan plan, int64_t* count);
  * did not land within about a second): VLOC_ERR_TIMEOUT (and the flag is
  * cleared), else VLOC_OK.  Results of the affected calls are undefined. */
 int vloc_device_status(vloc_plan plan);
+
+/* ---- measurement aids ----------------------------------------------------
+ * The paper has no counterpart.  The FP64 chain is bound by the GPU's FP64
+ * rate and the double-float chain by its FP32 pipe, so their roofline
+ * fractions divide by arithmetic ceilings measured with these probes rather
+ * than nominal figures. */
+#define VLOC_PEAK_DFMA   0  /* FP64 fused multiply-add (2 flops)               */
+#define VLOC_PEAK_DADD   1  /* FP64 add (1 flop)                               */
+#define VLOC_PEAK_FFMA   2  /* FP32 fused multiply-add (2 flops)               */
+#define VLOC_PEAK_FFMA2  3  /* paired FP32 fused multiply-add (4 flops)        */
+#define VLOC_PEAK_FADD2  4  /* paired FP32 add (2 flops)                       */
+#define VLOC_PEAK_NKINDS 5
+/*
+ * vloc_alu_peak -- run one probe kernel of `kind`: 8 blocks of 256 threads
+ * per SM, each thread 16 independent dependent chains of `iters` steps of
+ * that one instruction; timed with CUDA events on `stream` (synchronises).
+ *   sink  : device pointer to one double (never written in practice; keeps
+ *           the chains live).
+ *   flops : receives the floating-point operations the launch performed.
+ *   ms    : receives the launch's event time in milliseconds.
+ * Errors: VLOC_ERR_ARG (bad kind, iters <= 0, null pointer), VLOC_ERR_CUDA.
+ */
+int vloc_alu_peak(int kind, int64_t iters, void* sink, double* flops, double* ms, void* stream);
 
 /* vloc_strerror -- static string for a return code (never NULL). */
 const char* vloc_strerror(int code);

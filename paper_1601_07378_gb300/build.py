@@ -22,7 +22,7 @@ ROOT = os.path.dirname(HERE)
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 SOURCES = ["kernels_ct_a.cu", "kernels_ct_b.cu", "kernels_ct_c.cu", "kernels_df_a.cu", "kernels_df_b.cu",
-           "kernels_df_c.cu", "kernels_f32.cu", "kernels_f64.cu", "kernels.cu", "plan.cpp", "noalloc.cu"]
+           "kernels_df_c.cu", "kernels_f32.cu", "kernels_f64.cu", "kernels.cu", "plan.cpp", "noalloc.cu", "peaks.cu"]
 
 
 def _cuda_home() -> str:

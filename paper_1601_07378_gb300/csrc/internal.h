@@ -42,6 +42,7 @@ struct K3Tma {
     const void* base;   // slab workspace start (band 0 of the map)
     size_t band_bytes;  // NP * n2 * n3 * 8
     int* err;
+    int skip_first;     // test aid: block 0 never loads its first tile (its wait runs out)
 };
 
 // Kernel kinds (profiling slots).
@@ -178,9 +179,9 @@ struct HostTableLayout {
 // DevTables pointing into a device copy of the table block at `base`.
 DevTables device_tables(const int* base, const HostTableLayout& L, int n1, int n2, int n3, long long npw);
 
-// Copy a plan's index tables (kept on the host for any plan, including
-// host-only ones) into `blob` (capacity `cap` ints) without allocating.
-// Returns VLOC_OK, or VLOC_ERR_SIZE when `cap` is too small.
-int plan_host_tables(const vloc_plan_s* p, int* blob, size_t cap, HostTableLayout* lay);
+// A plan's index tables as kept on the host for any plan (host-only ones
+// included): *blob points into the plan and stays valid, unchanged, until
+// the plan is destroyed.  No allocation, no copy.
+int plan_host_tables(const vloc_plan_s* p, const int** blob, HostTableLayout* lay);
 
 }  // namespace vloc

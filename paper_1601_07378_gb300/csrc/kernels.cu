@@ -91,15 +91,19 @@ int launch_zero_f64(double* p, long long n, cudaStream_t st) {
 
 size_t smem_bytes_for(int dbl, int n) { return dbl ? Launch<double>::smem(n) : Launch<float>::smem(n); }
 size_t grad_smem_bytes(int dbl, int n) { return dbl ? Launch<double>::smem_grad(n) : Launch<float>::smem_grad(n); }
-// The dynamic shared-memory limit is a per-kernel attribute shared by every
-// plan in the process, so it only ever grows.
+// The dynamic shared-memory limit is a per-kernel attribute of the current
+// device's context, shared by every plan on that device, so it only ever
+// grows; the largest length set so far is kept per device.
 int set_smem_limits(int dbl, int nmax, int optin) {
+    constexpr int kMaxDevices = 64;
     static std::mutex mu;
-    static int cur[2] = {0, 0};
+    static int cur[kMaxDevices][2] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return (int)cudaErrorInvalidDevice;
     std::lock_guard<std::mutex> lock(mu);
-    if (nmax <= cur[dbl]) return 0;
+    if (dev >= 0 && dev < kMaxDevices && nmax <= cur[dev][dbl]) return 0;
     const int rc = dbl ? Launch<double>::set_limits(nmax, optin) : Launch<float>::set_limits(nmax, optin);
-    if (rc == 0) cur[dbl] = nmax;
+    if (rc == 0 && dev >= 0 && dev < kMaxDevices) cur[dev][dbl] = nmax;
     return rc;
 }
 int launch_twiddles(int dbl, void* tw, int n, cudaStream_t st) {

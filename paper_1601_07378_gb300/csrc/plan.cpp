@@ -110,6 +110,28 @@ void process_grid(int p, int* m, int* n) {
     *n = p / mm;
 }
 
+// Test aids, read from the environment variable VLOC_FAULT when a plan is
+// created (unset in normal use):
+//   "alloc" or "alloc:K" -- allocation K of vloc_plan_create (0 = the host
+//       plan object, 1, 2, ... = its device allocations in order) fails as
+//       if memory were exhausted, so every clean-up path can be exercised
+//       without exhausting a GPU;
+//   "tma_wait" -- the persistent TMA x-pass of the plan never issues the
+//       first tile load of its first thread block, so that block's bounded
+//       wait runs out and the kernel reports it through the error flag.
+struct FaultSpec {
+    int alloc_at = -1;
+    bool tma_wait = false;
+};
+FaultSpec fault_spec() {
+    FaultSpec f;
+    const char* v = std::getenv("VLOC_FAULT");
+    if (!v) return f;
+    if (std::strncmp(v, "alloc", 5) == 0) f.alloc_at = v[5] == ':' ? std::atoi(v + 6) : 0;
+    if (std::strcmp(v, "tma_wait") == 0) f.tma_wait = true;
+    return f;
+}
+
 }  // namespace
 
 struct vloc_plan_s {
@@ -122,6 +144,7 @@ struct vloc_plan_s {
     void* d_vdf = nullptr;      // V as hi + lo pairs [N]
     int* d_err = nullptr;       // set by a kernel whose bounded wait ran out
     bool k3tma_on = false;      // x-pass through the persistent TMA kernel
+    bool poison = false;        // VLOC_POISON_WORKSPACE: NaN-fill before every chunk
     vloc::K3Tma k3tma{};
     bool gamma = false;       // Gamma-point real mode (half-sphere coefficients)
     long long npw_user = 0;   // plane waves per band in the caller's arrays
@@ -231,7 +254,7 @@ int vloc_plan_create(vloc_plan* out, int n1, int n2, int n3, const int32_t* g, i
     if (part_flag != VLOC_PARTITION_GREEDY && part_flag != VLOC_PARTITION_BASIC && part_flag != VLOC_PARTITION_IMPROVED)
         return VLOC_ERR_ARG;
     if (flags & ~(0x003 | 0x0F0 | VLOC_GRAPH | VLOC_HOST_ONLY | VLOC_GENERIC_KERNELS | VLOC_GAMMA | VLOC_DOUBLE_FLOAT |
-                  VLOC_X_TMA))
+                  VLOC_X_TMA | VLOC_POISON_WORKSPACE))
         return VLOC_ERR_ARG;
     if ((flags & VLOC_DOUBLE_FLOAT) && prec != VLOC_F64) return VLOC_ERR_ARG;
     const bool host_only = (flags & VLOC_HOST_ONLY) != 0;
@@ -264,8 +287,15 @@ int vloc_plan_create(vloc_plan* out, int n1, int n2, int n3, const int32_t* g, i
     const size_t elem = dbl ? 16 : 8;
     const int nmax = std::max(n1, std::max(n2, n3));
 
-    vloc_plan p = new (std::nothrow) vloc_plan_s();
+    const FaultSpec fault = fault_spec();
+    int alloc_no = 0;  // allocations so far (fault injection counts them)
+    vloc_plan p = fault.alloc_at == alloc_no++ ? nullptr : new (std::nothrow) vloc_plan_s();
     if (!p) return VLOC_ERR_ALLOC;
+    auto dmalloc = [&](void** ptr, size_t bytes) -> cudaError_t {
+        if (fault.alloc_at == alloc_no++) return cudaErrorMemoryAllocation;
+        return cudaMalloc(ptr, bytes);
+    };
+    p->poison = (flags & VLOC_POISON_WORKSPACE) != 0;
     p->n1 = n1; p->n2 = n2; p->n3 = n3; p->dbl = dbl; p->flags = flags; p->npw = npw; p->N = N;
     p->npw_user = npw_user;
     p->gamma = (flags & VLOC_GAMMA) != 0;
@@ -432,7 +462,7 @@ int vloc_plan_create(vloc_plan* out, int n1, int n2, int n3, const int32_t* g, i
     // ---- device tables (one allocation)
     cudaStream_t st = (cudaStream_t)stream;
     const std::vector<int>& blob = p->host_tables;
-    if ((e = cudaMalloc(&p->d_tables, blob.size() * sizeof(int)))) { free_plan(p); return cuda_fail(e, "cudaMalloc(tables)"); }
+    if ((e = dmalloc((void**)&p->d_tables, blob.size() * sizeof(int)))) { free_plan(p); return cuda_fail(e, "cudaMalloc(tables)"); }
     if ((e = cudaMemcpyAsync(p->d_tables, blob.data(), blob.size() * sizeof(int), cudaMemcpyHostToDevice, st))) {
         free_plan(p); return cuda_fail(e, "upload tables");
     }
@@ -440,19 +470,19 @@ int vloc_plan_create(vloc_plan* out, int n1, int n2, int n3, const int32_t* g, i
 
     // ---- twiddles exp(+2 pi i j / n), FP64-made
     for (int a = 0; a < 3; ++a) {
-        if ((e = cudaMalloc(&p->d_tw[a], (size_t)ns[a] * elem))) { free_plan(p); return cuda_fail(e, "cudaMalloc(twiddles)"); }
+        if ((e = dmalloc((void**)&p->d_tw[a], (size_t)ns[a] * elem))) { free_plan(p); return cuda_fail(e, "cudaMalloc(twiddles)"); }
         if (launch_twiddles(dbl, p->d_tw[a], ns[a], st)) { free_plan(p); return cuda_fail(cudaGetLastError(), "twiddles"); }
     }
     if ((e = (cudaError_t)set_smem_limits(dbl, nmax, maxopt))) { free_plan(p); return cuda_fail(e, "cudaFuncSetAttribute"); }
-    if ((e = cudaMalloc(&p->d_err, sizeof(int)))) { free_plan(p); return cuda_fail(e, "cudaMalloc(error flag)"); }
+    if ((e = dmalloc((void**)&p->d_err, sizeof(int)))) { free_plan(p); return cuda_fail(e, "cudaMalloc(error flag)"); }
 
     if ((e = cudaMemsetAsync(p->d_err, 0, sizeof(int), st))) { free_plan(p); return cuda_fail(e, "clear error flag"); }
     if (p->df) {
         for (int a = 0; a < 3; ++a) {
-            if ((e = cudaMalloc(&p->d_twdf[a], (size_t)ns[a] * 32))) { free_plan(p); return cuda_fail(e, "cudaMalloc(df twiddles)"); }
+            if ((e = dmalloc((void**)&p->d_twdf[a], (size_t)ns[a] * 32))) { free_plan(p); return cuda_fail(e, "cudaMalloc(df twiddles)"); }
             if (launch_twiddles_df(p->d_tw[a], p->d_twdf[a], ns[a], st)) { free_plan(p); return cuda_fail(cudaGetLastError(), "df twiddles"); }
         }
-        if ((e = cudaMalloc(&p->d_vdf, (size_t)N * 8))) { free_plan(p); return cuda_fail(e, "cudaMalloc(df V)"); }
+        if ((e = dmalloc((void**)&p->d_vdf, (size_t)N * 8))) { free_plan(p); return cuda_fail(e, "cudaMalloc(df V)"); }
     }
 
     // ---- workspace: cylinder [chunk][S][n3] + slab [chunk][NP][n2][n3]
@@ -475,14 +505,14 @@ int vloc_plan_create(vloc_plan* out, int n1, int n2, int n3, const int32_t* g, i
     p->ws_bands = std::max<long long>(chunk, 2);
     p->ngroups = (int)((std::max<long long>(1, p->ws_bands / 2) + kGradBandsPerGroup - 1) / kGradBandsPerGroup);
     p->ws_bytes = per_band * (size_t)p->ws_bands + (size_t)N * sizeof(double) * (1 + p->ngroups);
-    if ((e = cudaMalloc(&p->d_cyl, (size_t)S * n3 * elem * p->ws_bands))) { free_plan(p); return cuda_fail(e, "cudaMalloc(cylinder)"); }
-    if ((e = cudaMalloc(&p->d_slab, (size_t)NP * n2 * n3 * elem * p->ws_bands))) { free_plan(p); return cuda_fail(e, "cudaMalloc(slab)"); }
+    if ((e = dmalloc((void**)&p->d_cyl, (size_t)S * n3 * elem * p->ws_bands))) { free_plan(p); return cuda_fail(e, "cudaMalloc(cylinder)"); }
+    if ((e = dmalloc((void**)&p->d_slab, (size_t)NP * n2 * n3 * elem * p->ws_bands))) { free_plan(p); return cuda_fail(e, "cudaMalloc(slab)"); }
     if (p->gamma) {
-        if ((e = cudaMalloc(&p->d_gamma_neg, sizeof(int) * (size_t)npw_user))) { free_plan(p); return cuda_fail(e, "cudaMalloc(gamma map)"); }
+        if ((e = dmalloc((void**)&p->d_gamma_neg, sizeof(int) * (size_t)npw_user))) { free_plan(p); return cuda_fail(e, "cudaMalloc(gamma map)"); }
         if ((e = cudaMemcpyAsync(p->d_gamma_neg, gamma_neg.data(), sizeof(int) * (size_t)npw_user, cudaMemcpyHostToDevice, st))) {
             free_plan(p); return cuda_fail(e, "upload gamma map");
         }
-        if ((e = cudaMalloc(&p->d_gamma_buf, 2 * (size_t)p->chunk * npw * elem))) { free_plan(p); return cuda_fail(e, "cudaMalloc(gamma buffers)"); }
+        if ((e = dmalloc((void**)&p->d_gamma_buf, 2 * (size_t)p->chunk * npw * elem))) { free_plan(p); return cuda_fail(e, "cudaMalloc(gamma buffers)"); }
         p->ws_bytes += 2 * (size_t)p->chunk * npw * elem;
     }
     // tensor map over the slab workspace for the persistent TMA x-pass (FP32,
@@ -507,13 +537,14 @@ int vloc_plan_create(vloc_plan* out, int n1, int n2, int n3, const int32_t* g, i
                 p->k3tma.base = p->d_slab;
                 p->k3tma.band_bytes = (size_t)NP * n2 * n3 * 8;
                 p->k3tma.err = p->d_err;
+                p->k3tma.skip_first = fault.tma_wait ? 1 : 0;
                 p->k3tma_on = true;
             }
         }
     }
 
     // dL/dV accumulator [N] followed by the band groups' partial sums [ngroups][N]
-    if ((e = cudaMalloc(&p->d_acc, (size_t)N * sizeof(double) * (1 + p->ngroups)))) { free_plan(p); return cuda_fail(e, "cudaMalloc(acc)"); }
+    if ((e = dmalloc((void**)&p->d_acc, (size_t)N * sizeof(double) * (1 + p->ngroups)))) { free_plan(p); return cuda_fail(e, "cudaMalloc(acc)"); }
     if ((e = cudaStreamSynchronize(st))) { free_plan(p); return cuda_fail(e, "plan create sync"); }
     *out = p;
     return VLOC_OK;
@@ -593,6 +624,20 @@ static int launch(vloc_plan p, int kind, cudaStream_t st, F&& f) {
     return VLOC_OK;
 }
 
+// VLOC_POISON_WORKSPACE (a test aid): fill the whole cylinder and slab
+// workspace with all-ones bytes -- a NaN in FP32, FP64 and double-float --
+// before each chunk, so that a pruned pass reading a cell no earlier pass of
+// the chunk wrote makes the result non-finite.
+static int poison(vloc_plan p, cudaStream_t st) {
+    if (!p->poison) return VLOC_OK;
+    const size_t cyl = (size_t)p->S * p->n3 * p->elem * p->ws_bands;
+    const size_t slab = (size_t)p->NP * p->n2 * p->n3 * p->elem * p->ws_bands;
+    cudaError_t e;
+    if ((e = cudaMemsetAsync(p->d_cyl, 0xFF, cyl, st))) return cuda_fail(e, "poison cylinder");
+    if ((e = cudaMemsetAsync(p->d_slab, 0xFF, slab, st))) return cuda_fail(e, "poison slab");
+    return VLOC_OK;
+}
+
 extern "C" {
 
 // out = A c over workspace chunks: K1, K2(+), K3, K2(-), K4 per chunk.
@@ -611,6 +656,7 @@ static int apply_impl(vloc_plan p, const void* c, const void* V, int64_t nb, voi
             const long long cb = std::min<long long>(p->chunk, nb - b0);
             const void* cc = (const char*)c + b0 * bstride;
             void* oo = (char*)out + b0 * bstride;
+            if ((rc = poison(p, st))) return rc;
             if ((rc = launch(p, KK_SCATTER_Z, st, [&] { return launch_k1_scatter_zpass(1, 2, t, ax, p->d_twdf[2], cc, cb, p->d_cyl, st); }))) return rc;
             if ((rc = launch(p, KK_Y_INV, st, [&] { return launch_k2_ypass(1, 2, +1, t, ax, p->d_twdf[1], cb, p->d_cyl, p->d_slab, st); }))) return rc;
             if ((rc = launch(p, KK_X_V, st, [&] { return launch_k3_xpass_v(1, 2, t, ax, p->d_twdf[0], p->d_vdf, cb, p->d_slab, st); }))) return rc;
@@ -624,6 +670,7 @@ static int apply_impl(vloc_plan p, const void* c, const void* V, int64_t nb, voi
         const void* cc = (const char*)c + b0 * bstride;
         void* oo = (char*)out + b0 * bstride;
         int rc;
+        if ((rc = poison(p, st))) return rc;
         if ((rc = launch(p, KK_SCATTER_Z, st, [&] { return launch_k1_scatter_zpass(dbl, p->fast, t, ax, p->d_tw[2], cc, cb, p->d_cyl, st); }))) return rc;
         if ((rc = launch(p, KK_Y_INV, st, [&] { return launch_k2_ypass(dbl, p->fast, +1, t, ax, p->d_tw[1], cb, p->d_cyl, p->d_slab, st); }))) return rc;
         if ((rc = launch(p, KK_X_V, st, [&] { return launch_k3_xpass_v(dbl, p->fast, t, ax, p->d_tw[0], V, cb, p->d_slab, st, p->k3tma_on ? &p->k3tma : nullptr); }))) return rc;
@@ -797,6 +844,7 @@ int vloc_backward(vloc_plan p, const void* c, const void* gout, const void* V, i
             const long long cb = std::min<long long>(half, nb - b0);
             const void* cc = (const char*)c + b0 * bstride;
             const void* gg = (const char*)gout + b0 * bstride;
+            if ((rc = poison(p, st))) return rc;
             if ((rc = launch(p, KK_SCATTER_Z, st, [&] { return launch_k1_scatter_zpass(dbl, p->fast, t, ax, p->d_tw[2], cc, cb, cylC, st); }))) return rc;
             if ((rc = launch(p, KK_Y_INV, st, [&] { return launch_k2_ypass(dbl, p->fast, +1, t, ax, p->d_tw[1], cb, cylC, slabC, st); }))) return rc;
             if ((rc = launch(p, KK_SCATTER_Z, st, [&] { return launch_k1_scatter_zpass(dbl, p->fast, t, ax, p->d_tw[2], gg, cb, cylG, st); }))) return rc;
@@ -841,6 +889,7 @@ int vloc_to_real(vloc_plan p, const void* c, int64_t nb, void* psi, void* stream
         const void* cc = (const char*)c + b0 * bstride;
         void* gg = (char*)psi + b0 * gstride;
         int rc;
+        if ((rc = poison(p, st))) return rc;
         if ((rc = launch(p, KK_SCATTER_Z, st, [&] { return launch_k1_scatter_zpass(dbl, p->fast, t, ax, p->d_tw[2], cc, cb, p->d_cyl, st); }))) return rc;
         if ((rc = launch(p, KK_Y_INV, st, [&] { return launch_k2_ypass(dbl, p->fast, +1, t, ax, p->d_tw[1], cb, p->d_cyl, p->d_slab, st); }))) return rc;
         if ((rc = launch(p, KK_X_TO_GRID, st, [&] { return launch_k3_grid(dbl, p->fast, +1, t, ax, p->d_tw[0], cb, p->d_slab, gg, st); }))) return rc;
@@ -864,6 +913,7 @@ int vloc_to_recip(vloc_plan p, const void* u, int64_t nb, void* out, void* strea
         void* gg = (char*)const_cast<void*>(u) + b0 * gstride;
         void* oo = (char*)out + b0 * bstride;
         int rc;
+        if ((rc = poison(p, st))) return rc;
         if ((rc = launch(p, KK_X_FROM_GRID, st, [&] { return launch_k3_grid(dbl, p->fast, -1, t, ax, p->d_tw[0], cb, p->d_slab, gg, st); }))) return rc;
         if ((rc = launch(p, KK_Y_FWD, st, [&] { return launch_k2_ypass(dbl, p->fast, -1, t, ax, p->d_tw[1], cb, p->d_cyl, p->d_slab, st); }))) return rc;
         if ((rc = launch(p, KK_Z_GATHER, st, [&] { return launch_k4_zpass_gather(dbl, p->fast, t, ax, p->d_tw[2], p->d_cyl, cb, oo, nullptr, nullptr, st); }))) return rc;
@@ -894,6 +944,7 @@ int vloc_density(vloc_plan p, const void* c, const void* occ, int64_t nb, void* 
     // x-pass; `base` is the global index of the chunk's first (pair) band.
     auto chunk_density = [&](const void* src, long long cb, long long base, int pair) -> int {
         int r;
+        if ((r = poison(p, st))) return r;
         if ((r = launch(p, KK_SCATTER_Z, st, [&] { return launch_k1_scatter_zpass(dbl, p->fast, t, ax, p->d_tw[2], src, cb, p->d_cyl, st); }))) return r;
         if ((r = launch(p, KK_Y_INV, st, [&] { return launch_k2_ypass(dbl, p->fast, +1, t, ax, p->d_tw[1], cb, p->d_cyl, p->d_slab, st); }))) return r;
         for (long long j0 = 0; j0 < cb; j0 += per_pass) {
@@ -1160,12 +1211,12 @@ int vloc_get_info(vloc_plan p, vloc_info* info) {
 
 }  // extern "C"
 
-// The plan's index tables (kept on the host for every plan, including
-// host-only ones) copied into caller memory, with no allocation.
-int vloc::plan_host_tables(const vloc_plan_s* p, int* blob, size_t cap, HostTableLayout* lay) {
+// The plan's index tables, kept on the host for every plan (host-only ones
+// included) and never changed after plan creation, so the block lives
+// exactly as long as the plan.
+int vloc::plan_host_tables(const vloc_plan_s* p, const int** blob, HostTableLayout* lay) {
     if (!p || !blob || !lay) return VLOC_ERR_ARG;
-    if (p->lay.total > cap) return VLOC_ERR_SIZE;
-    std::memcpy(blob, p->host_tables.data(), p->lay.total * sizeof(int));
+    *blob = p->host_tables.data();
     *lay = p->lay;
     return VLOC_OK;
 }

@@ -37,6 +37,7 @@ VLOC_GENERIC_KERNELS = 0x400
 VLOC_GAMMA = 0x1000
 VLOC_DOUBLE_FLOAT = 0x2000
 VLOC_X_TMA = 0x4000
+VLOC_POISON_WORKSPACE = 0x10000
 
 # every exported symbol declared in include/vloc.h
 EXPORTS = [
@@ -45,7 +46,7 @@ EXPORTS = [
     "vloc_get_info", "vloc_strerror", "vloc_version", "vloc_last_cuda_error",
     "vloc_profile", "vloc_get_profile", "vloc_get_launch_count", "vloc_apply_noalloc",
     "vloc_plan_set_schedule", "vloc_to_real", "vloc_to_recip", "vloc_density",
-    "vloc_apply_h", "vloc_device_status",
+    "vloc_apply_h", "vloc_device_status", "vloc_alu_peak",
 ]
 
 KERNEL_NAMES = ["k1_scatter_zpass", "k2_ypass_inv", "k3_xpass_v", "k2_ypass_fwd", "k4_zpass_gather",
@@ -117,6 +118,8 @@ def load(path: str | None = None) -> ctypes.CDLL:
         lib.vloc_to_real.argtypes = [vp, vp, i64, vp, vp]
         lib.vloc_to_recip.argtypes = [vp, vp, i64, vp, vp]
         lib.vloc_density.argtypes = [vp, vp, vp, i64, vp, vp]
+        lib.vloc_alu_peak.argtypes = [c_int, i64, vp, ctypes.POINTER(ctypes.c_double),
+                                      ctypes.POINTER(ctypes.c_double), vp]
         for name in EXPORTS:
             getattr(lib, name)
         _lib = lib
@@ -152,6 +155,21 @@ def _ptr(t) -> ctypes.c_void_p:
     return ctypes.c_void_p(t.data_ptr())
 
 
+PEAK_KINDS = {"dfma": 0, "dadd": 1, "ffma": 2, "ffma2": 3, "fadd2": 4}
+
+
+def alu_peak(kind: str, iters: int, *, stream=None) -> dict:
+    """Run one arithmetic-rate probe (vloc_alu_peak) on the current device;
+    returns the FLOPs of the launch, its event time and the GFLOP/s."""
+    import torch
+    lib = load()
+    sink = torch.zeros(1, dtype=torch.float64, device="cuda")
+    flops, ms = ctypes.c_double(), ctypes.c_double()
+    _check(lib.vloc_alu_peak(PEAK_KINDS[kind], int(iters), _ptr(sink), ctypes.byref(flops), ctypes.byref(ms),
+                             _stream_ptr(stream)), "vloc_alu_peak")
+    return {"flops": flops.value, "ms": ms.value, "gflops": flops.value / (ms.value * 1e6)}
+
+
 class VlocPlan:
     """Plan of the V_loc action for one grid (n1, n2, n3) and one G-list.
 
@@ -159,6 +177,9 @@ class VlocPlan:
     ``torch.complex64`` (FP32 path) or ``torch.complex128`` (FP64 path).
     ``double_float=True`` (with complex128) runs the apply in double-float
     arithmetic on the FP32 pipes, FP64 data in and out.
+    ``poison=True`` (a test aid) fills the workspace with NaN before every
+    chunk, so a pass that reads a cell its chunk never wrote shows up as a
+    non-finite result.
     ``gamma=True`` selects the Gamma-point real mode (Sec. 4.3): ``glist`` is
     half of a G -> -G symmetric sphere, the bands are real in r-space
     (c(-G) = conj c(G) implied, c(0) taken real) and two of them share one
@@ -167,7 +188,7 @@ class VlocPlan:
 
     def __init__(self, grid, glist, dtype=None, *, partition: str = "greedy", chunk: int = 0,
                  graph: bool = False, host_only: bool = False, generic: bool = False, gamma: bool = False,
-                 double_float: bool = False, x_tma: bool = False, stream=None):
+                 double_float: bool = False, x_tma: bool = False, poison: bool = False, stream=None):
         import torch
         dtype = dtype or torch.complex64
         if dtype not in (torch.complex64, torch.complex128):
@@ -195,6 +216,8 @@ class VlocPlan:
             flags |= VLOC_DOUBLE_FLOAT
         if x_tma:
             flags |= VLOC_X_TMA
+        if poison:
+            flags |= VLOC_POISON_WORKSPACE
         h = ctypes.c_void_p()
         sp = ctypes.c_void_p(None) if host_only else _stream_ptr(stream)
         _check(self.lib.vloc_plan_create(ctypes.byref(h), *self.grid,

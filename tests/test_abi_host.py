@@ -155,3 +155,43 @@ def test_gamma_host_plan_index_map_and_rejects():
     with pytest.raises(vloc.VlocError) as e:
         vloc.VlocPlan(n, np.array([[-8, 0, 0]], dtype=np.int32), torch.complex64, host_only=True, gamma=True)
     assert e.value.code == -3
+
+
+def test_noalloc_refuses_gamma_plans_before_any_device_call(lib):
+    # A Gamma-point plan's caller arrays hold the half list, while its index
+    # tables address the full G / -G list: the allocation-free apply must
+    # refuse it before touching any pointer or making a CUDA call (this runs
+    # without a GPU; the pointers are never dereferenced).
+    import torch  # noqa: F401
+    n = (16, 18, 20)
+    gh = synth.half_sphere(synth.sphere_glist(*n, 4.5, seed=3))
+    for dt in (torch.complex64, torch.complex128):
+        p = vloc.VlocPlan(n, gh, dt, host_only=True, gamma=True)
+        bogus = ctypes.c_void_p(256)
+        for nb in (0, 1, 5):
+            rc = lib.vloc_apply_noalloc(p.handle, bogus, bogus, nb, bogus, None)
+            assert rc == vloc.VLOC_ERR_STATE, (dt, nb, rc)
+
+
+def test_fault_injection_fails_plan_creation_cleanly(lib, monkeypatch):
+    # VLOC_FAULT=alloc makes the first allocation of vloc_plan_create (the
+    # host plan object) fail: the call returns VLOC_ERR_ALLOC and hands back
+    # no plan.  A host-only plan makes no CUDA call, so this runs without a GPU.
+    g = np.ascontiguousarray(synth.sphere_glist(8, 8, 8, 2), dtype=np.int32)
+    monkeypatch.setenv("VLOC_FAULT", "alloc")
+    rc, h = _create(lib, (8, 8, 8), g)
+    assert rc == vloc.VLOC_ERR_ALLOC and not h.value
+    monkeypatch.setenv("VLOC_FAULT", "alloc:0")
+    rc, h = _create(lib, (8, 8, 8), g)
+    assert rc == vloc.VLOC_ERR_ALLOC and not h.value
+    monkeypatch.delenv("VLOC_FAULT")
+    rc, h = _create(lib, (8, 8, 8), g)
+    assert rc == vloc.VLOC_OK and h.value
+    assert lib.vloc_plan_destroy(h) == 0
+
+
+def test_poison_flag_is_accepted_on_host_plans(lib):
+    g = synth.sphere_glist(8, 8, 8, 2)
+    rc, h = _create(lib, (8, 8, 8), g, flags=vloc.VLOC_F32 | vloc.VLOC_HOST_ONLY | vloc.VLOC_POISON_WORKSPACE)
+    assert rc == 0
+    assert lib.vloc_plan_destroy(h) == 0

@@ -244,6 +244,50 @@ def test_backward_matches_oracle(prec, n, R):
     assert np.linalg.norm(dV - dV_ref) / np.linalg.norm(dV_ref) < TOL[prec]
 
 
+_FULL_GRAD_CACHE = {}
+
+
+def _full_size_grad_case(prec):
+    # 96^3, R = 24 (57777 PWs), 48 bands: three 16-band groups of the dL/dV
+    # x-pass.  The oracle's dL/dV over all bands and its dL/dc on sampled
+    # bands are computed once per precision (same rounded inputs for every
+    # chunk setting).
+    if prec not in _FULL_GRAD_CACHE:
+        n, R, nb = (96, 96, 96), 24, 48
+        g, c, V = make_case(n, R, nb, seed=44, prec=prec)
+        rng = np.random.default_rng(45)
+        gout = (rng.standard_normal(c.shape) + 1j * rng.standard_normal(c.shape)).astype(c.dtype) * 0.01
+        sample = [0, 15, 16, 31, 47]
+        dc_ref = oracle_apply(n, g, gout, V, bands=sample)
+        dV_ref = O.grad_V(n, g, c.astype(np.complex128), gout.astype(np.complex128))
+        _FULL_GRAD_CACHE[prec] = (n, g, c, V, gout, sample, dc_ref, dV_ref)
+    return _FULL_GRAD_CACHE[prec]
+
+
+@pytest.mark.parametrize("prec", ["f32", "f64"])
+@pytest.mark.parametrize("chunk", [0, 40])
+def test_backward_full_size_matches_oracle(prec, chunk):
+    # The differentiable workload's grid (96^3, R = 24) with 48 bands.  The
+    # default chunk keeps all bands in one workspace chunk, so dL/dV merges
+    # three 16-band group sums in FP64; chunk = 40 splits the backward into
+    # chunks of 20, 20 and 8 bands (ragged), each with one full and one
+    # partial group.  dL/dc is compared per band on sampled bands, dL/dV over
+    # the whole grid.
+    n, g, c, V, gout, sample, dc_ref, dV_ref = _full_size_grad_case(prec)
+    cd, rd = DT[prec]
+    plan = vloc.VlocPlan(n, g, cd, chunk=chunk)
+    if chunk:
+        assert plan.info()["chunk_bands"] == chunk
+    ct = torch.from_numpy(c).to("cuda", cd)
+    Vt = torch.from_numpy(V).to("cuda", rd)
+    gt = torch.from_numpy(gout).to("cuda", cd)
+    gc, gV = plan.backward(ct, gt, Vt)
+    torch.cuda.synchronize()
+    assert rel_l2_per_band(gc.cpu().numpy()[sample], dc_ref).max() < TOL[prec]
+    dV = gV.cpu().numpy().astype(np.float64)
+    assert np.linalg.norm(dV - dV_ref) / np.linalg.norm(dV_ref) < TOL[prec]
+
+
 def test_autograd_finite_differences_fp64():
     # loss = sum_n <psi_n|V|psi_n> + ||V psi - t||^2 at 32^3 (R = 8), FP64.
     n, R, nb = (32, 32, 32), 8, 2
