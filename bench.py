@@ -298,6 +298,23 @@ def run_ours(args, rank, world, local_rank):
 
     stream = torch.cuda.current_stream()
     g = synth.sphere_glist(*GRID, R)
+    if args.only == "density":
+        # profiler driver: the charge density of --bands bands at 96^3, FP32
+        c_d = torch.from_numpy(synth.coefficients(g, NBANDS, seed=SEED)).to("cuda", torch.complex64)
+        rho_d = torch.empty(GRID, dtype=torch.float32, device="cuda")
+        plan = vloc.VlocPlan(GRID, g, torch.complex64, chunk=args.chunk, generic=args.generic)
+        ms = time_steps(lambda: plan.density(c_d, rho=rho_d), args.steps, args.warmup, stream, dist_on)
+        plan.profile(True)
+        for _ in range(args.steps):
+            plan.density(c_d, rho=rho_d)
+        prof = plan.get_profile()
+        plan.profile(False)
+        if rank == 0:
+            print(json.dumps({"only": "density", "bands": NBANDS, "steps": args.steps, "grid": list(GRID),
+                              "chunk": plan.info()["chunk_bands"], "ms_per_step": ms / args.steps,
+                              "bands_per_s": world * NBANDS * args.steps / ms * 1e3,
+                              "kernels": {k: [n // args.steps, round(t / args.steps, 4)] for k, (n, t) in prof.items()}}))
+        return
     if args.only == "headline":
         # profiler driver: the headline steps alone, nothing else
         cdt, rdt = (torch.complex64, torch.float32) if args.prec == "f32" else (torch.complex128, torch.float64)
@@ -310,7 +327,8 @@ def run_ours(args, rank, world, local_rank):
             c_d = torch.from_numpy(synth.coefficients(g, NBANDS, seed=SEED)).to("cuda", cdt)
             V_d = torch.from_numpy(synth.potential(*grid, "smooth", SEED + 1000)[0]).to("cuda", rdt)
             out_d = torch.empty_like(c_d)
-        plan = vloc.VlocPlan(grid, g, cdt, chunk=args.chunk, generic=args.generic)
+        plan = vloc.VlocPlan(grid, g, cdt, chunk=args.chunk, generic=args.generic,
+                             double_float=args.df and args.prec == "f64")
         ms = time_steps(lambda: plan.apply(c_d, V_d, out=out_d), args.steps, args.warmup, stream, dist_on)
         plan.profile(True)
         for _ in range(args.steps):
@@ -318,7 +336,8 @@ def run_ours(args, rank, world, local_rank):
         prof = plan.get_profile()
         plan.profile(False)
         if rank == 0:
-            print(json.dumps({"only": "headline", "prec": args.prec, "bands": NBANDS, "steps": args.steps,
+            print(json.dumps({"only": "headline", "prec": args.prec, "double_float": plan.info()["double_float"],
+                              "bands": NBANDS, "steps": args.steps,
                               "grid": list(grid),
                               "chunk": plan.info()["chunk_bands"], "generic": args.generic,
                               "ms_per_step": ms / args.steps, "bands_per_s": world * NBANDS * args.steps / ms * 1e3,
@@ -669,8 +688,10 @@ def main():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-cufft", action="store_true", help="skip the torch.fft comparison")
     ap.add_argument("--no-extra", action="store_true", help="skip the batched and autograd legs")
-    ap.add_argument("--only", choices=["all", "headline"], default="all",
-                    help="headline: only the FP32 forward steps (for profiler launch lists)")
+    ap.add_argument("--only", choices=["all", "headline", "density"], default="all",
+                    help="headline: only the forward apply steps; density: only the density steps "
+                         "(profiler drivers)")
+    ap.add_argument("--df", action="store_true", help="with --only headline --prec f64: double-float plan")
     ap.add_argument("--bands", type=int, default=NBANDS, help="bands per GPU per step (default 1024)")
     ap.add_argument("--prec", choices=["f32", "f64"], default="f32", help="precision of --only headline")
     ap.add_argument("--chunk", type=int, default=0, help="bands per workspace chunk (0: the plan's default)")

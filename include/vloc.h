@@ -119,7 +119,10 @@ typedef struct vloc_info {
     int32_t path;                /* bit 0: compile-time-length kernels enabled;   */
                                  /* bit 2: Gamma-point real mode;                 */
                                  /* bit 3: double-float FP64 apply in use;        */
-                                 /* bit 4: TMA x-pass in use                      */
+                                 /* bit 4: TMA x-pass in use;                     */
+                                 /* bit 5: the x-planes are the quarter-sphere    */
+                                 /* set x = 0..n1/4, n1 - n1/4 .. n1 - 1, and the */
+                                 /* x-pass kernels take them at compile time      */
 } vloc_info;
 
 /*

@@ -344,6 +344,175 @@ template <int S> struct Dft<12, S> : DftAB<4, 3, S> {};
 template <int S> struct Dft<15, S> : DftAB<3, 5, S> {};
 template <int S> struct Dft<16, S> : DftAB<4, 4, S> {};
 
+// ------------------------------------- small DFTs with known-zero inputs
+// A pruned stage (Sec. 4.3, Fig. 5: only the cuboid's planes hold data)
+// knows at compile time which inputs of a unit are zero.  ZV<Z, V> carries
+// that knowledge in its type: Z = true means "known zero", and the helpers
+// below skip every operation with a known-zero operand, so a DFT over such
+// inputs costs only the adds and products its nonzero inputs need.  Outputs
+// a caller never stores are left to dead-code elimination.
+template <bool Z, class V> struct ZV {
+    V v;
+};
+template <bool Z, class V> __device__ __forceinline__ V zget(const ZV<Z, V>& a) {
+    if constexpr (Z) return czero<V>();
+    else return a.v;
+}
+template <bool A, bool B, class V> __device__ __forceinline__ ZV<A && B, V> zadd(const ZV<A, V>& a, const ZV<B, V>& b) {
+    if constexpr (A && B) return {};
+    else if constexpr (A) return {b.v};
+    else if constexpr (B) return {a.v};
+    else return {cadd(a.v, b.v)};
+}
+template <bool A, bool B, class V> __device__ __forceinline__ ZV<A && B, V> zsub(const ZV<A, V>& a, const ZV<B, V>& b) {
+    if constexpr (A && B) return {};
+    else if constexpr (A) return {cneg(b.v)};
+    else if constexpr (B) return {a.v};
+    else return {csub(a.v, b.v)};
+}
+template <int S, bool A, class V> __device__ __forceinline__ ZV<A, V> zmul_si(const ZV<A, V>& a) {
+    if constexpr (A) return {};
+    else return {mul_si<S>(a.v)};
+}
+template <bool A, class V> __device__ __forceinline__ ZV<A, V> zscale(const ZV<A, V>& a, scalar_t<V> s) {
+    if constexpr (A) return {};
+    else return {cscale(a.v, s)};
+}
+// a + s b
+template <bool A, bool B, class V>
+__device__ __forceinline__ ZV<A && B, V> zfma(const ZV<A, V>& a, scalar_t<V> s, const ZV<B, V>& b) {
+    if constexpr (B) return {a.v};
+    else if constexpr (A) return {cscale(b.v, s)};
+    else return {cfma(a.v, s, b.v)};
+}
+
+constexpr bool zbit(unsigned m, int i) { return ((m >> i) & 1u) == 0; }  // true: input i known zero
+
+// X[k] = sum_n x[n] exp(S 2 pi i n k / R) where bit n of M is clear for the
+// inputs known to be zero (their values are ignored).  M = all ones is the
+// plain Dft.
+template <int R, int S, unsigned M> struct DftZ {
+    template <typename V> __device__ __forceinline__ static void run(V* v) { Dft<R, S>::run(v); }
+};
+template <int S, unsigned M> struct DftZ<2, S, M> {
+    template <typename V> __device__ __forceinline__ static void run(V* v) {
+        const ZV<zbit(M, 0), V> a{v[0]};
+        const ZV<zbit(M, 1), V> b{v[1]};
+        v[0] = zget(zadd(a, b));
+        v[1] = zget(zsub(a, b));
+    }
+};
+template <int S, unsigned M> struct DftZ<3, S, M> {
+    template <typename V> __device__ __forceinline__ static void run(V* v) {
+        using T = scalar_t<V>;
+        constexpr T h = (T)0.866025403784438646763723170752936183;  // sqrt(3)/2
+        const ZV<zbit(M, 0), V> x0{v[0]};
+        const ZV<zbit(M, 1), V> x1{v[1]};
+        const ZV<zbit(M, 2), V> x2{v[2]};
+        const auto t = zadd(x1, x2);
+        const auto d = zsub(x1, x2);
+        const auto m = zfma(x0, (T)-0.5, t);
+        const auto r = zmul_si<S>(zscale(d, h));
+        v[0] = zget(zadd(x0, t));
+        v[1] = zget(zadd(m, r));
+        v[2] = zget(zsub(m, r));
+    }
+};
+template <int S, unsigned M> struct DftZ<4, S, M> {
+    template <typename V> __device__ __forceinline__ static void run(V* v) {
+        const ZV<zbit(M, 0), V> x0{v[0]};
+        const ZV<zbit(M, 1), V> x1{v[1]};
+        const ZV<zbit(M, 2), V> x2{v[2]};
+        const ZV<zbit(M, 3), V> x3{v[3]};
+        const auto t0 = zadd(x0, x2), t1 = zsub(x0, x2);
+        const auto t2 = zadd(x1, x3), t3 = zmul_si<S>(zsub(x1, x3));
+        v[0] = zget(zadd(t0, t2));
+        v[2] = zget(zsub(t0, t2));
+        v[1] = zget(zadd(t1, t3));
+        v[3] = zget(zsub(t1, t3));
+    }
+};
+template <int S, unsigned M> struct DftZ<5, S, M> {
+    template <typename V> __device__ __forceinline__ static void run(V* v) {
+        using T = scalar_t<V>;
+        constexpr T c1 = (T)ct::cos_turn(1, 5), c2 = (T)ct::cos_turn(2, 5);
+        constexpr T s1 = (T)ct::sin_turn(1, 5), s2 = (T)ct::sin_turn(2, 5);
+        const ZV<zbit(M, 0), V> x0{v[0]};
+        const ZV<zbit(M, 1), V> x1{v[1]};
+        const ZV<zbit(M, 2), V> x2{v[2]};
+        const ZV<zbit(M, 3), V> x3{v[3]};
+        const ZV<zbit(M, 4), V> x4{v[4]};
+        const auto a1 = zadd(x1, x4), b1 = zsub(x1, x4);
+        const auto a2 = zadd(x2, x3), b2 = zsub(x2, x3);
+        const auto p1 = zfma(zfma(x0, c1, a1), c2, a2);
+        const auto p2 = zfma(zfma(x0, c2, a1), c1, a2);
+        const auto q1 = zmul_si<S>(zfma(zscale(b1, s1), s2, b2));
+        const auto q2 = zmul_si<S>(zfma(zscale(b1, s2), -s1, b2));
+        v[0] = zget(zadd(zadd(x0, a1), a2));
+        v[1] = zget(zadd(p1, q1));
+        v[4] = zget(zsub(p1, q1));
+        v[2] = zget(zadd(p2, q2));
+        v[3] = zget(zsub(p2, q2));
+    }
+};
+// composite R = A * B as in DftAB: a first-pass group whose inputs are all
+// known zero is skipped (its outputs stay zero), and the second pass knows
+// which groups those were.
+template <int A, int B, unsigned M> struct ZMaskAB {
+    static constexpr unsigned group(int n2) {
+        unsigned g = 0;
+        for (int n1 = 0; n1 < A; ++n1) g |= ((M >> (B * n1 + n2)) & 1u) << n1;
+        return g;
+    }
+    static constexpr unsigned second() {
+        unsigned m = 0;
+        for (int n2 = 0; n2 < B; ++n2) m |= (group(n2) ? 1u : 0u) << n2;
+        return m;
+    }
+};
+template <int A, int B, int S, unsigned M> struct DftABZ {
+    template <typename V> __device__ __forceinline__ static void run(V* v) {
+        constexpr int R = A * B;
+        using MK = ZMaskAB<A, B, M>;
+        V y[R];
+        sfor<B>([&](auto n2c) {
+            constexpr int n2 = decltype(n2c)::value;
+            constexpr unsigned g = MK::group(n2);
+            if constexpr (g != 0) {
+                V t[A];
+                sfor<A>([&](auto n1) { t[n1] = v[B * n1 + n2]; });
+                DftZ<A, S, g>::run(t);
+                sfor<A>([&](auto k1) { y[n2 * A + k1] = tw_const<R, S, n2 * k1>(t[k1]); });
+            } else {
+                sfor<A>([&](auto k1) { y[n2 * A + k1] = czero<V>(); });
+            }
+        });
+        constexpr unsigned m2 = MK::second();
+        sfor<A>([&](auto k1) {
+            V t[B];
+            sfor<B>([&](auto n2) { t[n2] = y[n2 * A + k1]; });
+            DftZ<B, S, m2>::run(t);
+            sfor<B>([&](auto k2) { v[k1 + A * k2] = t[k2]; });
+        });
+    }
+};
+template <int R> constexpr unsigned zfull() { return R >= 32 ? ~0u : (1u << R) - 1u; }
+#define VLOC_DFTZ_AB(RR, AA, BB)                                                              \
+    template <int S, unsigned M> struct DftZ<RR, S, M> {                                    \
+        template <typename V> __device__ __forceinline__ static void run(V* v) {            \
+            if constexpr ((M & zfull<RR>()) == zfull<RR>()) Dft<RR, S>::run(v);             \
+            else DftABZ<AA, BB, S, M>::run(v);                                               \
+        }                                                                                    \
+    };
+VLOC_DFTZ_AB(6, 2, 3)
+VLOC_DFTZ_AB(8, 4, 2)
+VLOC_DFTZ_AB(9, 3, 3)
+VLOC_DFTZ_AB(10, 2, 5)
+VLOC_DFTZ_AB(12, 4, 3)
+VLOC_DFTZ_AB(15, 3, 5)
+VLOC_DFTZ_AB(16, 4, 4)
+#undef VLOC_DFTZ_AB
+
 // ------------------------------------------------------------ per-axis plan
 constexpr int kMaxStages = 4;
 constexpr int kLines = 32;          // lines per tile (one per lane)

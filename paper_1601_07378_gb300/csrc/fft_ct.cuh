@@ -73,6 +73,42 @@ template <int N> struct Sched {
     static constexpr int NSR(int s) { int p = 1; for (int i = 0; i < s; ++i) p *= P.r[P.nst - 1 - i]; return p; }
 };
 
+// ---- x rows of the quarter-sphere plane set
+// When the occupied x-planes are exactly x = 0..Q and N - Q .. N - 1 (Q =
+// N / 4: a cut-off sphere of radius N/4 grid units, the cuboid of Fig. 5)
+// every row the x-pass touches is known at compile time.  Row r of unit i
+// of the first inverse stage (and of the last forward stage) is x = i + r NA
+// (NA = N / R0); its kind says whether it is always outside the cuboid
+// (a known-zero input, an output that is never stored), always inside it,
+// or on its edge (inside for some units i only), and where its plane sits.
+template <int N> struct QRows {
+    static constexpr int Q = N / 4;
+    static constexpr int NP = 2 * Q + 1;
+    static constexpr int R0 = Sched<N>::R(0);
+    static constexpr int NA = N / R0;
+    static_assert(NA - 1 < N - 2 * Q, "a row cannot touch both edges");
+    // 0: outside for every unit; 1: low rows, always inside; 2: high rows,
+    // always inside; 3: low edge (inside iff i <= Q - r NA); 4: high edge
+    // (inside iff i >= N - Q - r NA)
+    static constexpr int kind(int r) {
+        const int lo = r * NA, hi = r * NA + NA - 1;
+        return hi <= Q ? 1 : lo >= N - Q ? 2 : lo <= Q ? 3 : hi >= N - Q ? 4 : 0;
+    }
+    // plane of row r for unit i: i + off(r)
+    static constexpr int off(int r) { return (kind(r) == 1 || kind(r) == 3) ? r * NA : r * NA - N + NP; }
+    static constexpr unsigned mask() {
+        unsigned m = 0;
+        for (int r = 0; r < R0; ++r) m |= (kind(r) ? 1u : 0u) << r;
+        return m;
+    }
+    template <int r> __device__ __forceinline__ static bool inside(int i) {
+        constexpr int k = kind(r);
+        if constexpr (k == 1 || k == 2) return true;
+        else if constexpr (k == 3) return i <= Q - r * NA;
+        else if constexpr (k == 4) return i >= N - Q - r * NA;
+        else return false;
+    }
+};
 // Shared line buffer for lane pairs: [N][kLdP] FP32 complex, pitch even so a
 // pair of adjacent lines is one aligned 16-byte vector.
 constexpr int kLdP = kLines + 2;

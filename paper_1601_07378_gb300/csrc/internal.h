@@ -26,6 +26,11 @@ struct DevTables {
     int S, T, NP;
     int n1, n2, n3;
     long long npw;
+    // 1 when the occupied x-planes are exactly x = 0..n1/4 and n1 - n1/4 ..
+    // n1 - 1 in ascending order (a sphere of radius n1/4 in grid units, the
+    // cuboid of Fig. 5 for R = n/4): the x-pass kernels then take the plane
+    // of each row at compile time
+    int xq;
 };
 
 struct LaunchAxes {
@@ -174,6 +179,7 @@ namespace vloc {
 struct HostTableLayout {
     size_t o_row, o_tp, o_ts, o_tpp, o_tpw, o_plp, o_xr, total;
     int S, T, NP;
+    int xq;  // DevTables::xq
 };
 
 // DevTables pointing into a device copy of the table block at `base`.

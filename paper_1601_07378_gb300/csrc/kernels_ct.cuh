@@ -356,6 +356,132 @@ __global__ void __launch_bounds__(32 * W, minb_k3(N)) k3_ct(DevTables t, const f
     RevStage<N, -1, W, nst - 1>::template run<false>(stw, sb, xr, slot, sub, warp, act);
 }
 
+// ------------------------------------------------- K3, quarter-sphere form
+// Twiddle tables of the two table-twiddled stages of a two-stage length
+// N = R0 R1, one row per unit residue k: twA[k][r] = w^(k r), k < R0, r < R1
+// (the inverse stage that ends the first transform) and twB[k][r] = w^(k r),
+// k < R1, r < R0 (the forward stage that ends the second), w = exp(2 pi i /
+// N), so a unit reads its R - 1 twiddles at consecutive addresses.
+template <int N> __host__ __device__ constexpr size_t k3q_smem() {
+    return (size_t)N * kLdP * sizeof(float2) + 2 * (size_t)N * sizeof(float2);
+}
+
+#ifndef VLOC_MINB_K3Q
+#define VLOC_MINB_K3Q 5
+#endif
+constexpr int minb_k3q(int n) { return n <= 96 ? VLOC_MINB_K3Q : minb_k3(n); }
+template <int N, int W>
+__global__ void __launch_bounds__(32 * W, minb_k3q(N)) k3q_ct(DevTables t, const float2* __restrict__ tw1,
+                                                  const float* __restrict__ Vr, float2* slab) {
+    using SC = Sched<N>;
+    static_assert(SC::nst == 2, "quarter-sphere x-pass: two-stage lengths");
+    using QR = QRows<N>;
+    constexpr int R0 = SC::R(0), R1 = SC::R(1);
+    constexpr int NA = N / R0;  // units of the first inverse and the last forward stage
+    constexpr int NB = N / R1;  // units of the chained middle stage
+    constexpr int UA = (NA + 2 * W - 1) / (2 * W), UB = (NB + 2 * W - 1) / (2 * W);
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float2* buf = reinterpret_cast<float2*>(smem_raw);
+    float2* twA = buf + N * kLdP;
+    float2* twB = twA + N;
+    const int n2 = t.n2, n3 = t.n3;
+    const int slot = slot_of(), sub = sub_of(), warp = warp_of();
+    const int y = blockIdx.x;
+    const int z0 = blockIdx.y * kLines;
+    const long long b = blockIdx.z;
+    const int lines = min(kLines, n3 - z0);
+    const bool act = 2 * slot < lines;
+    for (int e = threadIdx.x; e < N; e += 32 * W) {
+        twA[e] = tw1[(e / R1) * (e % R1)];
+        twB[e] = tw1[(e / R0) * (e % R0)];
+    }
+    __syncthreads();
+    const int pstride = n2 * n3;
+    float2* sl = slab + b * t.NP * (long long)pstride + y * n3 + z0 + 2 * slot;  // plane 0, this lane's pair
+    const float* vrow = Vr + (long long)y * n3 + z0 + 2 * slot;
+    SmemP sb{buf};
+
+    // inverse x-FFT, first stage (radix R0, no twiddles): global rows -> buffer
+    if (act) {
+#pragma unroll
+        for (int u = 0; u < UA; ++u) {
+            const int i = 2 * (warp + u * W) + sub;
+            if (NA % (2 * W) == 0 || i < NA) {
+                P2f h[R0];
+                sfor<R0>([&](auto rc) {
+                    constexpr int r = decltype(rc)::value;
+                    if constexpr (QR::kind(r) == 0) h[r] = czero<P2f>();
+                    else h[r] = QR::template inside<r>(i) ? *reinterpret_cast<const P2f*>(sl + (i + QR::off(r)) * pstride)
+                                                          : czero<P2f>();
+                });
+                DftZ<R0, +1, QR::mask()>::run(h);
+#pragma unroll
+                for (int r = 0; r < R0; ++r) sb(i * R0 + r, slot, h[r]);
+            }
+        }
+    }
+    __syncthreads();
+    // last inverse stage -> psi(x) V(x, y, z) -> first forward stage, in
+    // registers (unit i holds x = i + r NB in both)
+    P2f h[UB][R1];
+    if (act) {
+#pragma unroll
+        for (int u = 0; u < UB; ++u) {
+            const int i = 2 * (warp + u * W) + sub;
+            if (NB % (2 * W) == 0 || i < NB) {
+#pragma unroll
+                for (int r = 0; r < R1; ++r) h[u][r] = sb(i + r * NB, slot);
+                const float2* tw = twA + i * R1;  // i < NB = R0
+#pragma unroll
+                for (int r = 1; r < R1; ++r) h[u][r] = cmul(h[u][r], tw[r]);
+                Dft<R1, +1>::run(h[u]);
+#pragma unroll
+                for (int r = 0; r < R1; ++r) {
+                    const float2 w = *reinterpret_cast<const float2*>(vrow + (i + r * NB) * pstride);
+                    h[u][r].a = cscale(h[u][r].a, w.x);
+                    h[u][r].b = cscale(h[u][r].b, w.y);
+                }
+                Dft<R1, -1>::run(h[u]);
+            }
+        }
+    }
+    __syncthreads();
+    if (act) {
+#pragma unroll
+        for (int u = 0; u < UB; ++u) {
+            const int i = 2 * (warp + u * W) + sub;
+            if (NB % (2 * W) == 0 || i < NB) {
+#pragma unroll
+                for (int r = 0; r < R1; ++r) sb(i * R1 + r, slot, h[u][r]);
+            }
+        }
+    }
+    __syncthreads();
+    // forward x-FFT, last stage (radix R0, twiddled): buffer -> the occupied
+    // global rows; outputs of rows outside the cuboid are never formed
+    if (act) {
+#pragma unroll
+        for (int u = 0; u < UA; ++u) {
+            const int i = 2 * (warp + u * W) + sub;
+            if (NA % (2 * W) == 0 || i < NA) {
+                P2f g[R0];
+#pragma unroll
+                for (int r = 0; r < R0; ++r) g[r] = sb(i + r * NA, slot);
+                const float2* tw = twB + i * R0;  // i < NA = R1
+#pragma unroll
+                for (int r = 1; r < R0; ++r) g[r] = cmulc(g[r], tw[r]);
+                Dft<R0, -1>::run(g);
+                sfor<R0>([&](auto rc) {
+                    constexpr int r = decltype(rc)::value;
+                    if constexpr (QR::kind(r) != 0) {
+                        if (QR::template inside<r>(i)) *reinterpret_cast<P2f*>(sl + (i + QR::off(r)) * pstride) = g[r];
+                    }
+                });
+            }
+        }
+    }
+}
+
 // ------------------------------------------------------------------ K4
 template <int N>
 __global__ void __launch_bounds__(kThreads, minb_k4(N)) k4_ct(DevTables t, const float2* __restrict__ tw3,
@@ -629,6 +755,18 @@ int LaunchCT<T, N>::k3(const DevTables& t, const void* tw1, const void* V, long 
                        cudaStream_t st) {
     if (tma) return launch_k3_tma<N>(t, tw1, V, nb, slab, *tma, st);
     constexpr int W = k3_warps(N);
+    if constexpr (Sched<N>::nst == 2) {
+        if (t.xq) {
+            constexpr size_t sm = k3q_smem<N>();
+            static const cudaError_t onceq =
+                sm <= 48 * 1024 ? cudaSuccess
+                                : cudaFuncSetAttribute(k3q_ct<N, W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+            if (onceq) return (int)onceq;
+            const dim3 grid(t.n2, (t.n3 + kLines - 1) / kLines, (unsigned)nb);
+            k3q_ct<N, W><<<grid, 32 * W, sm, st>>>(t, (const float2*)tw1, (const float*)V, (float2*)slab);
+            return (int)cudaGetLastError();
+        }
+    }
     static const cudaError_t once = CtSmem<N>::ensure(k3_ct<N, W>);
     if (once) return (int)once;
     const dim3 grid(t.n2, (t.n3 + kLines - 1) / kLines, (unsigned)nb);

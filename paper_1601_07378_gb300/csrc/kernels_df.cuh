@@ -247,6 +247,118 @@ __global__ void __launch_bounds__(kThreads) k3_w(DevTables t, const typename Pol
     RevStage<N, -1, kWarps, nst - 1, V, TW>::template run<false>(stw, sb, xr, slot, sub, warp, act);
 }
 
+// ------------------------------------------------- K3, quarter-sphere form
+// The x-pass of k3_w for the quarter-sphere x-plane set (QRows, fft_ct.cuh):
+// rows known outside the cuboid are neither loaded nor transformed in the
+// first inverse stage, and never formed in the last forward stage; the two
+// table-twiddled stages read per-unit twiddle rows (twA / twB).
+template <class Pol, int N> __host__ __device__ constexpr size_t k3q_w_smem() {
+    return (size_t)N * kLdP * sizeof(float2) + 2 * (size_t)N * sizeof(typename Pol::TW);
+}
+template <class Pol, int N>
+__global__ void __launch_bounds__(kThreads) k3q_w(DevTables t, const typename Pol::TW* __restrict__ tw1,
+                                                 const typename Pol::VR* __restrict__ Vr, typename Pol::V* slab) {
+    using V = typename Pol::V;
+    using TW = typename Pol::TW;
+    using SC = Sched<N>;
+    static_assert(SC::nst == 2, "quarter-sphere x-pass: two-stage lengths");
+    using QR = QRows<N>;
+    constexpr int W = kWarps;
+    constexpr int R0 = SC::R(0), R1 = SC::R(1);
+    constexpr int NA = N / R0, NB = N / R1;
+    constexpr int UA = (NA + 2 * W - 1) / (2 * W), UB = (NB + 2 * W - 1) / (2 * W);
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float2* buf = reinterpret_cast<float2*>(smem_raw);
+    TW* twA = reinterpret_cast<TW*>(buf + N * kLdP);
+    TW* twB = twA + N;
+    const int n2 = t.n2, n3 = t.n3;
+    const int slot = slot_of_df(), sub = sub_of_df(), warp = warp_of_df();
+    const int y = blockIdx.x;
+    const int z0 = blockIdx.y * kLinesDF;
+    const long long b = blockIdx.z;
+    const int lines = min(kLinesDF, n3 - z0);
+    const bool act = slot < lines;
+    for (int e = threadIdx.x; e < N; e += kThreads) {
+        twA[e] = tw1[(e / R1) * (e % R1)];
+        twB[e] = tw1[(e / R0) * (e % R0)];
+    }
+    __syncthreads();
+    const int pstride = n2 * n3;
+    V* sl = slab + b * t.NP * (long long)pstride + y * n3 + z0 + slot;
+    const typename Pol::VR* vrow = Vr + (long long)y * n3 + z0 + slot;
+    SmemT<V> sb{buf};
+
+    if (act) {
+#pragma unroll
+        for (int u = 0; u < UA; ++u) {
+            const int i = 2 * (warp + u * W) + sub;
+            if (NA % (2 * W) == 0 || i < NA) {
+                V h[R0];
+                sfor<R0>([&](auto rc) {
+                    constexpr int r = decltype(rc)::value;
+                    if constexpr (QR::kind(r) == 0) h[r] = czero<V>();
+                    else h[r] = QR::template inside<r>(i) ? sl[(i + QR::off(r)) * pstride] : czero<V>();
+                });
+                DftZ<R0, +1, QR::mask()>::run(h);
+#pragma unroll
+                for (int r = 0; r < R0; ++r) sb(i * R0 + r, slot, h[r]);
+            }
+        }
+    }
+    __syncthreads();
+    V h[UB][R1];
+    if (act) {
+#pragma unroll
+        for (int u = 0; u < UB; ++u) {
+            const int i = 2 * (warp + u * W) + sub;
+            if (NB % (2 * W) == 0 || i < NB) {
+#pragma unroll
+                for (int r = 0; r < R1; ++r) h[u][r] = sb(i + r * NB, slot);
+                const TW* tw = twA + i * R1;
+#pragma unroll
+                for (int r = 1; r < R1; ++r) h[u][r] = cmul(h[u][r], tw[r]);
+                Dft<R1, +1>::run(h[u]);
+#pragma unroll
+                for (int r = 0; r < R1; ++r) h[u][r] = Pol::mul_v(h[u][r], vrow[(i + r * NB) * pstride]);
+                Dft<R1, -1>::run(h[u]);
+            }
+        }
+    }
+    __syncthreads();
+    if (act) {
+#pragma unroll
+        for (int u = 0; u < UB; ++u) {
+            const int i = 2 * (warp + u * W) + sub;
+            if (NB % (2 * W) == 0 || i < NB) {
+#pragma unroll
+                for (int r = 0; r < R1; ++r) sb(i * R1 + r, slot, h[u][r]);
+            }
+        }
+    }
+    __syncthreads();
+    if (act) {
+#pragma unroll
+        for (int u = 0; u < UA; ++u) {
+            const int i = 2 * (warp + u * W) + sub;
+            if (NA % (2 * W) == 0 || i < NA) {
+                V g[R0];
+#pragma unroll
+                for (int r = 0; r < R0; ++r) g[r] = sb(i + r * NA, slot);
+                const TW* tw = twB + i * R0;
+#pragma unroll
+                for (int r = 1; r < R0; ++r) g[r] = cmulc(g[r], tw[r]);
+                Dft<R0, -1>::run(g);
+                sfor<R0>([&](auto rc) {
+                    constexpr int r = decltype(rc)::value;
+                    if constexpr (QR::kind(r) != 0) {
+                        if (QR::template inside<r>(i)) sl[(i + QR::off(r)) * pstride] = w_store(g[r]);
+                    }
+                });
+            }
+        }
+    }
+}
+
 // ------------------------------------------------------------------ K4
 template <class Pol, int N>
 __global__ void __launch_bounds__(kThreads) k4_w(DevTables t, const typename Pol::TW* __restrict__ tw3,
@@ -330,9 +442,21 @@ template <int P, int N>
 int LaunchF64<P, N>::k3(const DevTables& t, const void* tw1, const void* V, long long nb, void* slab,
                         cudaStream_t st) {
     using Pol = PolOf<P>;
+    const dim3 grid(t.n2, (t.n3 + kLinesDF - 1) / kLinesDF, (unsigned)nb);
+    if constexpr (Sched<N>::nst == 2) {
+        if (t.xq) {
+            constexpr size_t sm = k3q_w_smem<Pol, N>();
+            static const cudaError_t onceq =
+                sm <= 48 * 1024 ? cudaSuccess
+                                : cudaFuncSetAttribute(k3q_w<Pol, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+            if (onceq) return (int)onceq;
+            k3q_w<Pol, N><<<grid, kThreads, sm, st>>>(t, (const typename Pol::TW*)tw1, (const typename Pol::VR*)V,
+                                                      (typename Pol::V*)slab);
+            return (int)cudaGetLastError();
+        }
+    }
     static const cudaError_t once = WSmem<Pol, N>::ensure(k3_w<Pol, N>);
     if (once) return (int)once;
-    const dim3 grid(t.n2, (t.n3 + kLinesDF - 1) / kLinesDF, (unsigned)nb);
     k3_w<Pol, N><<<grid, kThreads, WSmem<Pol, N>::sm, st>>>(t, (const typename Pol::TW*)tw1,
                                                            (const typename Pol::VR*)V, (typename Pol::V*)slab);
     return (int)cudaGetLastError();

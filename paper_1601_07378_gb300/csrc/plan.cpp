@@ -440,6 +440,17 @@ int vloc_plan_create(vloc_plan* out, int n1, int n2, int n3, const int32_t* g, i
         L.o_xr = append(xrow_plane);
         L.total = blob.size();
         L.S = S; L.T = T; L.NP = NP;
+        // the quarter-sphere x-plane pattern (x = 0..Q and n1 - Q .. n1 - 1,
+        // Q = n1 / 4, planes in ascending x), which the x-pass kernels can
+        // take at compile time; VLOC_NO_XQ (a test aid) turns the
+        // specialisation off
+        const int Q = n1 / 4;
+        bool xq = NP == 2 * Q + 1 && Q >= 1 && std::getenv("VLOC_NO_XQ") == nullptr;
+        for (int x = 0; xq && x < n1; ++x) {
+            const int want = x <= Q ? x : x >= n1 - Q ? x - n1 + NP : -1;
+            xq = xrow_plane[x] == want;
+        }
+        L.xq = xq ? 1 : 0;
     }
 
     if (host_only) {
@@ -1199,7 +1210,8 @@ int vloc_get_info(vloc_plan p, vloc_info* info) {
     info->npw = p->npw_user;
     info->nsticks = p->S; info->nplanes = p->NP; info->nparts = p->P;
     info->lines_per_tile = kLinesPerTile;
-    info->path = (p->fast ? 1 : 0) | (p->gamma ? 4 : 0) | (p->df ? 8 : 0) | (p->k3tma_on ? 16 : 0);
+    info->path = (p->fast ? 1 : 0) | (p->gamma ? 4 : 0) | (p->df ? 8 : 0) | (p->k3tma_on ? 16 : 0) |
+                 (p->lay.xq ? 32 : 0);
     info->chunk_bands = p->chunk;
     info->workspace_bytes = (int64_t)p->ws_bytes;
     for (int a = 0; a < 3; ++a) {
@@ -1232,5 +1244,6 @@ DevTables vloc::device_tables(const int* base, const HostTableLayout& L, int n1,
     t.xrow_plane = base + L.o_xr;
     t.S = L.S; t.T = L.T; t.NP = L.NP;
     t.n1 = n1; t.n2 = n2; t.n3 = n3; t.npw = npw;
+    t.xq = L.xq;
     return t;
 }

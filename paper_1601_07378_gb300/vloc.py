@@ -256,6 +256,7 @@ class VlocPlan:
             "gamma": bool(inf.path & 4),
             "double_float": bool(inf.path & 8),
             "x_tma": bool(inf.path & 16),
+            "x_quarter": bool(inf.path & 32),
         }
 
     def set_schedule(self, axis: int, radices):

@@ -195,3 +195,17 @@ def test_poison_flag_is_accepted_on_host_plans(lib):
     rc, h = _create(lib, (8, 8, 8), g, flags=vloc.VLOC_F32 | vloc.VLOC_HOST_ONLY | vloc.VLOC_POISON_WORKSPACE)
     assert rc == 0
     assert lib.vloc_plan_destroy(h) == 0
+
+
+def test_quarter_sphere_plane_set_is_detected(lib):
+    # the x-pass kernels specialise for the plane set of a sphere of radius
+    # n1/4 (x = 0..n1/4 and n1 - n1/4 .. n1 - 1, Sec. 4.3 / Fig. 5)
+    import torch
+    n = (48, 30, 30)
+    g = synth.sphere_glist(*n, 12)
+    assert vloc.VlocPlan(n, g, torch.complex64, host_only=True).info()["x_quarter"]
+    assert vloc.VlocPlan(n, g[::-1], torch.complex64, host_only=True).info()["x_quarter"]
+    strict = g[(g.astype(np.int64) ** 2).sum(axis=1) < 144]
+    shifted = g + np.array([1, 0, 0], dtype=g.dtype)
+    for other in (synth.sphere_glist(*n, 11.5), strict, shifted):
+        assert not vloc.VlocPlan(n, other, torch.complex64, host_only=True).info()["x_quarter"]
