@@ -109,6 +109,31 @@ template <int N> struct QRows {
         else return false;
     }
 };
+// First stage of an inverse x-transform (radix R0, no twiddles) read from
+// the quarter-sphere rows: `load(p)` returns the value of plane p for this
+// lane's line(s); rows outside the cuboid are known zeros; results go to
+// rows i R0 + r of `dst`.  W warps share the NA units.
+template <int N, int W, class V, class Load, class Dst>
+__device__ __forceinline__ void xq_first_inverse(const Load& load, const Dst& dst, int slot, int sub, int warp) {
+    using QR = QRows<N>;
+    constexpr int R0 = QR::R0, NA = QR::NA, UA = (NA + 2 * W - 1) / (2 * W);
+#pragma unroll
+    for (int u = 0; u < UA; ++u) {
+        const int i = 2 * (warp + u * W) + sub;
+        if (NA % (2 * W) == 0 || i < NA) {
+            V h[R0];
+            sfor<R0>([&](auto rc) {
+                constexpr int r = decltype(rc)::value;
+                if constexpr (QR::kind(r) == 0) h[r] = czero<V>();
+                else h[r] = QR::template inside<r>(i) ? load(i + QR::off(r)) : czero<V>();
+            });
+            DftZ<R0, +1, QR::mask()>::run(h);
+#pragma unroll
+            for (int r = 0; r < R0; ++r) dst(i * R0 + r, slot, h[r]);
+        }
+    }
+}
+
 // Shared line buffer for lane pairs: [N][kLdP] FP32 complex, pitch even so a
 // pair of adjacent lines is one aligned 16-byte vector.
 constexpr int kLdP = kLines + 2;

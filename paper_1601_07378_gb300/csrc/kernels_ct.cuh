@@ -713,6 +713,80 @@ __global__ void __launch_bounds__(kThreads, minb(N, 5)) k3d_ct(DevTables t, cons
     }
 }
 
+// Density x-pass for the quarter-sphere plane set: k3d_ct with the first
+// inverse stage reading only the cuboid's rows (xq_first_inverse).
+template <int N>
+__global__ void __launch_bounds__(kThreads, minb(N, 5)) k3dq_ct(DevTables t, const float2* __restrict__ tw1,
+                                                   const float2* slab, int nb, int bpg, const float* __restrict__ occ,
+                                                   long long b_base, int pair, long long nreal,
+                                                   double* __restrict__ partial) {
+    using SC = Sched<N>;
+    static_assert(SC::nst == 2, "quarter-sphere x-pass: two-stage lengths");
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int n2 = t.n2, n3 = t.n3;
+    float2* buf = reinterpret_cast<float2*>(smem_raw);
+    float2* stw = buf + N * kLdP;
+    const int slot = slot_of(), sub = sub_of(), warp = warp_of();
+    const int y = blockIdx.x;
+    const int z0 = blockIdx.y * kLines;
+    const int grp = blockIdx.z;
+    const int lines = min(kLines, n3 - z0);
+    const bool act = 2 * slot < lines;
+    load_tw<float>(stw, tw1, N);
+    __syncthreads();
+    const int pstride = n2 * n3;
+    using L = NatStage<N, +1, kWarps, 1>;
+    constexpr int R = SC::R(1);
+    float2 acc[L::U][R];
+#pragma unroll
+    for (int u = 0; u < L::U; ++u)
+#pragma unroll
+        for (int r = 0; r < R; ++r) acc[u][r] = make_float2(0.f, 0.f);
+    SmemP sb{buf};
+    const int b1 = min(nb, (grp + 1) * bpg);
+    for (int b = grp * bpg; b < b1; ++b) {
+        double wxd, wyd;
+        density_weights(occ, b_base + b, pair, nreal, wxd, wyd);
+        const float wx = (float)wxd, wy = (float)wyd;
+        const float2* sl = slab + (long long)b * t.NP * pstride + y * n3 + z0 + 2 * slot;
+        if (act)
+            xq_first_inverse<N, kWarps, P2f>([&](int p) { return *reinterpret_cast<const P2f*>(sl + p * pstride); },
+                                             sb, slot, sub, warp);
+        __syncthreads();
+        if (act) {
+#pragma unroll
+            for (int u = 0; u < L::U; ++u) {
+                const int i = 2 * (warp + u * kWarps) + sub;
+                if (L::NI % (2 * kWarps) == 0 || i < L::NI) {
+                    P2f h[R];
+                    L::compute_unit(h, stw, sb, i, slot);
+#pragma unroll
+                    for (int r = 0; r < R; ++r) {
+                        acc[u][r].x += wx * h[r].a.x * h[r].a.x + wy * h[r].a.y * h[r].a.y;
+                        acc[u][r].y += wx * h[r].b.x * h[r].b.x + wy * h[r].b.y * h[r].b.y;
+                    }
+                }
+            }
+        }
+        __syncthreads();
+    }
+    if (act) {
+        double* part = partial + (long long)grp * N * pstride + y * n3 + z0 + 2 * slot;
+#pragma unroll
+        for (int u = 0; u < L::U; ++u) {
+            const int i = 2 * (warp + u * kWarps) + sub;
+            if (L::NI % (2 * kWarps) == 0 || i < L::NI) {
+#pragma unroll
+                for (int r = 0; r < R; ++r) {
+                    double* q = part + (i + r * L::NI) * pstride;
+                    q[0] = (double)acc[u][r].x;
+                    q[1] = (double)acc[u][r].y;
+                }
+            }
+        }
+    }
+}
+
 // ------------------------------------------------------------ launchers
 template <int N> struct CtSmem {
     static constexpr size_t sm = ct_smem<N>();
@@ -806,10 +880,19 @@ int LaunchCT<T, N>::k3g(int sign, const DevTables& t, const void* tw1, long long
 template <typename T, int N>
 int LaunchCT<T, N>::k3d(const DevTables& t, const void* tw1, const void* slab, long long nb, int bpg, const void* occ,
                         long long b_base, int pair, long long nreal, double* partial, cudaStream_t st) {
-    static const cudaError_t once = CtSmem<N>::ensure(k3d_ct<N>);
-    if (once) return (int)once;
     const int ng = (int)((nb + bpg - 1) / bpg);
     const dim3 grid(t.n2, (t.n3 + kLines - 1) / kLines, ng);
+    if constexpr (Sched<N>::nst == 2) {
+        if (t.xq) {
+            static const cudaError_t onceq = CtSmem<N>::ensure(k3dq_ct<N>);
+            if (onceq) return (int)onceq;
+            k3dq_ct<N><<<grid, kThreads, CtSmem<N>::sm, st>>>(t, (const float2*)tw1, (const float2*)slab, (int)nb, bpg,
+                                                              (const float*)occ, b_base, pair, nreal, partial);
+            return (int)cudaGetLastError();
+        }
+    }
+    static const cudaError_t once = CtSmem<N>::ensure(k3d_ct<N>);
+    if (once) return (int)once;
     k3d_ct<N><<<grid, kThreads, CtSmem<N>::sm, st>>>(t, (const float2*)tw1, (const float2*)slab, (int)nb, bpg,
                                                      (const float*)occ, b_base, pair, nreal, partial);
     return (int)cudaGetLastError();

@@ -12,6 +12,7 @@ import numpy as np
 import pytest
 
 from helpers import TOL, make_case, oracle_apply, rel_l2_per_band
+from oracle import oracle as O
 from paper_1601_07378_gb300 import synth, vloc
 
 torch = pytest.importorskip("torch")
@@ -84,3 +85,18 @@ def test_quarter_x_pass_backward_chunks_and_poison(monkeypatch):
     assert rel_l2_per_band(gc.cpu().numpy(), gc0.cpu().numpy().astype(np.complex128)).max() < 3e-7
     assert torch.equal(gV, gV0)   # dL/dV does not use the forward x-pass
     assert rel_l2_per_band(out.cpu().numpy(), oracle_apply(n, g, c, V)).max() < TOL["f32"]
+
+
+@pytest.mark.parametrize("n1,m,nb", [(48, 30, 5), (96, 50, 3), (144, 80, 2)])
+def test_quarter_density_matches_oracle(n1, m, nb, monkeypatch):
+    # the density's x-pass reads only the cuboid's rows in its first stage
+    n = (n1, m, m)
+    g, c, _ = make_case(n, n1 / 4, nb, seed=85, order="shuffled", prec="f32")
+    occ = np.linspace(2.0, 0.5, nb).astype(np.float32)
+    q, ref = _plans(n, g, torch.complex64, monkeypatch, chunk=2)
+    ct, ot = torch.from_numpy(c).cuda(), torch.from_numpy(occ).cuda()
+    rho = q.density(ct, ot).cpu().numpy().astype(np.float64)
+    rho0 = ref.density(ct, ot).cpu().numpy().astype(np.float64)
+    want = O.density(n, g, c.astype(np.complex128), occ.astype(np.float64))
+    assert np.linalg.norm(rho - want) / np.linalg.norm(want) < TOL["f32"]
+    assert np.linalg.norm(rho - rho0) / np.linalg.norm(rho0) < 3e-7
