@@ -122,7 +122,9 @@ typedef struct vloc_info {
                                  /* bit 4: TMA x-pass in use;                     */
                                  /* bit 5: the x-planes are the quarter-sphere    */
                                  /* set x = 0..n1/4, n1 - n1/4 .. n1 - 1, and the */
-                                 /* x-pass kernels take them at compile time      */
+                                 /* x-pass kernels take them at compile time;     */
+                                 /* bit 6: every |l| <= n3/4, and the z-pass       */
+                                 /* kernels skip the rows outside that band       */
 } vloc_info;
 
 /*

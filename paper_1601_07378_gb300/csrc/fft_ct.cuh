@@ -134,6 +134,13 @@ __device__ __forceinline__ void xq_first_inverse(const Load& load, const Dst& ds
     }
 }
 
+// Rows x of a length-N line that the first inverse stage of the natural
+// schedule may read when every nonzero input lies in the quarter band (row
+// x is read by unit x % NA as row x / NA)
+template <int N> __device__ __forceinline__ bool xq_row_read(int x) {
+    return (QRows<N>::mask() >> (x / QRows<N>::NA)) & 1u;
+}
+
 // Shared line buffer for lane pairs: [N][kLdP] FP32 complex, pitch even so a
 // pair of adjacent lines is one aligned 16-byte vector.
 constexpr int kLdP = kLines + 2;

@@ -31,6 +31,9 @@ struct DevTables {
     // cuboid of Fig. 5 for R = n/4): the x-pass kernels then take the plane
     // of each row at compile time
     int xq;
+    // 1 when every plane wave has l mod n3 in 0..n3/4 or n3 - n3/4 .. n3 - 1
+    // (|l| <= n3/4): the z-pass kernels then skip the rows outside that band
+    int zq;
 };
 
 struct LaunchAxes {
@@ -180,6 +183,7 @@ struct HostTableLayout {
     size_t o_row, o_tp, o_ts, o_tpp, o_tpw, o_plp, o_xr, total;
     int S, T, NP;
     int xq;  // DevTables::xq
+    int zq;  // DevTables::zq
 };
 
 // DevTables pointing into a device copy of the table block at `base`.

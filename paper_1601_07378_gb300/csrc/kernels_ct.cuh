@@ -154,46 +154,51 @@ __device__ __forceinline__ void gather_entries_p(const int2* __restrict__ ent, i
         }
     }
 }
-// Tile rows <-> cylinder: warp w moves lines w, w + 4, ...; lane j moves
-// elements z = j, j + 32, ... of the line (coalesced along the stick, no
-// index division).
+// Tile rows <-> cylinder, a line pair (2s, 2s + 1) per warp pass: lane j
+// moves elements z = j, j + 32, ... of both lines as one 16-byte shared-memory
+// access (rows are 272 bytes apart, so the 16-byte accesses of a warp hit
+// distinct banks; one line per lane would be a 2-way conflict) and two
+// coalesced global accesses, one per stick.
 template <int NN>
 __device__ __forceinline__ void rows_out_p(const float2* buf, float2* __restrict__ cb, const int* sticks, int lines) {
     constexpr int K = (NN + 31) / 32;
     const int lane = threadIdx.x & 31;
-    for (int l = threadIdx.x >> 5; l < lines; l += kWarps) {
-        float2* row = cb + (long long)sticks[l] * NN;
-        float2 v[K];
+    for (int sp = threadIdx.x >> 5; 2 * sp < lines; sp += kWarps) {
+        const bool two = 2 * sp + 1 < lines;
+        float2* row0 = cb + (long long)sticks[2 * sp] * NN;
+        float2* row1 = cb + (long long)sticks[two ? 2 * sp + 1 : 2 * sp] * NN;
+        P2f v[K];
 #pragma unroll
         for (int k = 0; k < K; ++k)
-            if (NN % 32 == 0 || lane + 32 * k < NN) v[k] = buf[(lane + 32 * k) * kLdP + l];
+            if (NN % 32 == 0 || lane + 32 * k < NN)
+                v[k] = *reinterpret_cast<const P2f*>(buf + (lane + 32 * k) * kLdP + 2 * sp);
 #pragma unroll
         for (int k = 0; k < K; ++k)
-            if (NN % 32 == 0 || lane + 32 * k < NN) row[lane + 32 * k] = v[k];
+            if (NN % 32 == 0 || lane + 32 * k < NN) {
+                row0[lane + 32 * k] = v[k].a;
+                if (two) row1[lane + 32 * k] = v[k].b;
+            }
     }
 }
 template <int NN>
 __device__ __forceinline__ void rows_in_p(float2* buf, const float2* __restrict__ cb, const int* sticks, int lines) {
     constexpr int K = (NN + 31) / 32;
     const int lane = threadIdx.x & 31;
-    // two lines per pass: twice the loads in flight
-    for (int l = threadIdx.x >> 5; l < lines; l += 2 * kWarps) {
-        const int l2 = l + kWarps;
-        const float2* row = cb + (long long)sticks[l] * NN;
-        const float2* row2 = cb + (long long)sticks[l2 < lines ? l2 : l] * NN;
-        float2 v[K], v2[K];
+    for (int sp = threadIdx.x >> 5; 2 * sp < lines; sp += kWarps) {
+        const bool two = 2 * sp + 1 < lines;
+        const float2* row0 = cb + (long long)sticks[2 * sp] * NN;
+        const float2* row1 = cb + (long long)sticks[two ? 2 * sp + 1 : 2 * sp] * NN;
+        P2f v[K];
 #pragma unroll
         for (int k = 0; k < K; ++k)
             if (NN % 32 == 0 || lane + 32 * k < NN) {
-                v[k] = row[lane + 32 * k];
-                v2[k] = row2[lane + 32 * k];
+                v[k].a = row0[lane + 32 * k];
+                v[k].b = two ? row1[lane + 32 * k] : make_float2(0.f, 0.f);
             }
 #pragma unroll
         for (int k = 0; k < K; ++k)
-            if (NN % 32 == 0 || lane + 32 * k < NN) {
-                buf[(lane + 32 * k) * kLdP + l] = v[k];
-                if (l2 < lines) buf[(lane + 32 * k) * kLdP + l2] = v2[k];
-            }
+            if (NN % 32 == 0 || lane + 32 * k < NN)
+                *reinterpret_cast<P2f*>(buf + (lane + 32 * k) * kLdP + 2 * sp) = v[k];
     }
 }
 
@@ -249,6 +254,81 @@ __global__ void __launch_bounds__(kThreads, minb_k1(N)) k1_ct(DevTables t, const
     scatter_tile_p<N>(t.tile_pw, t.tile_pw_ptr[tile], t.tile_pw_ptr[tile + 1], coeffs + b * t.npw, buf);
     fft_ct<N, +1, kWarps, false, true, true>(stw, SmemP{buf}, SmemP{buf}, buf, slot_of(), sub_of(), warp_of(),
                                              2 * slot_of() < lines);
+    __syncthreads();
+    rows_out_p<N>(buf, cyl + b * (long long)t.S * N, t.tile_sticks + s0, lines);
+}
+
+// ------------------------------------------------- K1, quarter-band form
+// When every plane wave has |l| <= N/4 (a sphere of radius n3/4: the z rows
+// of each stick lie in the band of Fig. 5), only the rows the first inverse
+// stage reads are cleared, and that stage skips the rows known to be zero.
+template <int N>
+__global__ void __launch_bounds__(kThreads, minb_k1(N)) k1q_ct(DevTables t, const float2* __restrict__ tw3,
+                                                  const float2* __restrict__ coeffs, float2* __restrict__ cyl) {
+    using SC = Sched<N>;
+    static_assert(SC::nst == 2, "quarter-band z-pass: two-stage lengths");
+    using QR = QRows<N>;
+    constexpr int R0 = QR::R0, NA = QR::NA, W = kWarps;
+    constexpr int UA = (NA + 2 * W - 1) / (2 * W);
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float2* buf = reinterpret_cast<float2*>(smem_raw);
+    float2* stw = buf + N * kLdP;
+    const int tile = blockIdx.x;
+    const long long b = blockIdx.y;
+    const int slot = slot_of(), sub = sub_of(), warp = warp_of();
+    load_tw<float>(stw, tw3, N);
+    const int s0 = t.tile_ptr[tile], lines = t.tile_ptr[tile + 1] - s0;
+    {   // scatter: first batch's loads, clearing of the rows stage 0 reads, stores
+        constexpr int B = VLOC_SCATTER_BATCH;
+        const int2* ent = t.tile_pw;
+        const int e0 = t.tile_pw_ptr[tile], e1 = t.tile_pw_ptr[tile + 1];
+        const float2* c = coeffs + b * t.npw;
+        int2 en[B];
+        float2 val[B];
+        const int base0 = e0 + (int)threadIdx.x;
+        entries_load_p<B>(ent, base0, e1, c, en, val);
+        constexpr int RW = kLdP / 2;  // float4 per row
+        for (int i = threadIdx.x; i < N * RW; i += kThreads)
+            if (xq_row_read<N>(i / RW)) reinterpret_cast<float4*>(buf)[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+        __syncthreads();
+        entries_store_p<B>(buf, en, val);
+        for (int base = base0 + B * kThreads; base < e1; base += B * kThreads) {
+            entries_load_p<B>(ent, base, e1, c, en, val);
+            entries_store_p<B>(buf, en, val);
+        }
+        __syncthreads();
+    }
+    const bool act = 2 * slot < lines;
+    SmemP sb{buf};
+    // first inverse stage in place (every unit's values in registers, then stored)
+    P2f h[UA][R0];
+    if (act) {
+#pragma unroll
+        for (int u = 0; u < UA; ++u) {
+            const int i = 2 * (warp + u * W) + sub;
+            if (NA % (2 * W) == 0 || i < NA) {
+                sfor<R0>([&](auto rc) {
+                    constexpr int r = decltype(rc)::value;
+                    if constexpr (QR::kind(r) == 0) h[u][r] = czero<P2f>();
+                    else h[u][r] = sb(i + r * NA, slot);
+                });
+                DftZ<R0, +1, QR::mask()>::run(h[u]);
+            }
+        }
+    }
+    __syncthreads();
+    if (act) {
+#pragma unroll
+        for (int u = 0; u < UA; ++u) {
+            const int i = 2 * (warp + u * W) + sub;
+            if (NA % (2 * W) == 0 || i < NA) {
+#pragma unroll
+                for (int r = 0; r < R0; ++r) sb(i * R0 + r, slot, h[u][r]);
+            }
+        }
+    }
+    __syncthreads();
+    NatStage<N, +1, W, 1>::template run<true>(stw, sb, sb, slot, sub, warp, act);
     __syncthreads();
     rows_out_p<N>(buf, cyl + b * (long long)t.S * N, t.tile_sticks + s0, lines);
 }
@@ -498,6 +578,54 @@ __global__ void __launch_bounds__(kThreads, minb_k4(N)) k4_ct(DevTables t, const
     __syncthreads();
     fft_ct<N, -1, kWarps, false, true, true>(stw, SmemP{buf}, SmemP{buf}, buf, slot_of(), sub_of(), warp_of(),
                                              2 * slot_of() < lines);
+    __syncthreads();
+    gather_entries_p(t.tile_pw, t.tile_pw_ptr[tile], t.tile_pw_ptr[tile + 1], buf, out + b * t.npw, scale, diag,
+                     diag ? cin + b * t.npw : cin);
+}
+
+// ------------------------------------------------- K4, quarter-band form
+// The forward z-pass in the reversed schedule, whose last stage (radix R0)
+// writes row x = i + r NA of unit i: rows outside the band |l| <= N/4 are
+// never gathered, so they are never formed.
+template <int N>
+__global__ void __launch_bounds__(kThreads, minb_k4(N)) k4q_ct(DevTables t, const float2* __restrict__ tw3,
+                                                  const float2* __restrict__ cyl, float2* out, float scale,
+                                                  const float* __restrict__ diag, const float2* cin) {
+    using SC = Sched<N>;
+    static_assert(SC::nst == 2, "quarter-band z-pass: two-stage lengths");
+    using QR = QRows<N>;
+    constexpr int R0 = QR::R0, W = kWarps;
+    using L = RevStage<N, -1, W, 1>;  // radix R0, rows i + r NA
+    static_assert(L::NI == QR::NA, "last forward stage rows");
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float2* buf = reinterpret_cast<float2*>(smem_raw);
+    float2* stw = buf + N * kLdP;
+    const int tile = blockIdx.x;
+    const long long b = blockIdx.y;
+    const int slot = slot_of(), sub = sub_of(), warp = warp_of();
+    load_tw<float>(stw, tw3, N);
+    const int s0 = t.tile_ptr[tile], lines = t.tile_ptr[tile + 1] - s0;
+    rows_in_p<N>(buf, cyl + b * (long long)t.S * N, t.tile_sticks + s0, lines);
+    __syncthreads();
+    const bool act = 2 * slot < lines;
+    SmemP sb{buf};
+    RevStage<N, -1, W, 0>::template run<true>(stw, sb, sb, slot, sub, warp, act);
+    __syncthreads();
+    P2f h[L::U][R0];
+    if (act) L::compute(h, stw, sb, slot, sub, warp);
+    __syncthreads();
+    if (act) {
+#pragma unroll
+        for (int u = 0; u < L::U; ++u) {
+            const int i = 2 * (warp + u * W) + sub;
+            if (L::NI % (2 * W) == 0 || i < L::NI) {
+                sfor<R0>([&](auto rc) {
+                    constexpr int r = decltype(rc)::value;
+                    if constexpr (QR::kind(r) != 0) sb(i + r * QR::NA, slot, h[u][r]);
+                });
+            }
+        }
+    }
     __syncthreads();
     gather_entries_p(t.tile_pw, t.tile_pw_ptr[tile], t.tile_pw_ptr[tile + 1], buf, out + b * t.npw, scale, diag,
                      diag ? cin + b * t.npw : cin);
@@ -800,6 +928,15 @@ template <typename T, int N>
 int LaunchCT<T, N>::k1(const DevTables& t, const void* tw3, const void* coeffs, long long nb, void* cyl,
                        cudaStream_t st) {
     static_assert(std::is_same<T, float>::value, "compile-time kernels are FP32");
+    if constexpr (Sched<N>::nst == 2) {
+        if (t.zq) {
+            static const cudaError_t onceq = CtSmem<N>::ensure(k1q_ct<N>);
+            if (onceq) return (int)onceq;
+            k1q_ct<N><<<dim3(t.T, (unsigned)nb), kThreads, CtSmem<N>::sm, st>>>(t, (const float2*)tw3,
+                                                                                 (const float2*)coeffs, (float2*)cyl);
+            return (int)cudaGetLastError();
+        }
+    }
     static const cudaError_t once = CtSmem<N>::ensure(k1_ct<N>);
     if (once) return (int)once;
     k1_ct<N><<<dim3(t.T, (unsigned)nb), kThreads, CtSmem<N>::sm, st>>>(t, (const float2*)tw3, (const float2*)coeffs,
@@ -900,9 +1037,18 @@ int LaunchCT<T, N>::k3d(const DevTables& t, const void* tw1, const void* slab, l
 template <typename T, int N>
 int LaunchCT<T, N>::k4(const DevTables& t, const void* tw3, const void* cyl, long long nb, void* out,
                        const void* diag, const void* cin, cudaStream_t st) {
+    const float scale = (float)(1.0 / ((double)t.n1 * t.n2 * t.n3));
+    if constexpr (Sched<N>::nst == 2) {
+        if (t.zq) {
+            static const cudaError_t onceq = CtSmem<N>::ensure(k4q_ct<N>);
+            if (onceq) return (int)onceq;
+            k4q_ct<N><<<dim3(t.T, (unsigned)nb), kThreads, CtSmem<N>::sm, st>>>(
+                t, (const float2*)tw3, (const float2*)cyl, (float2*)out, scale, (const float*)diag, (const float2*)cin);
+            return (int)cudaGetLastError();
+        }
+    }
     static const cudaError_t once = CtSmem<N>::ensure(k4_ct<N>);
     if (once) return (int)once;
-    const float scale = (float)(1.0 / ((double)t.n1 * t.n2 * t.n3));
     k4_ct<N><<<dim3(t.T, (unsigned)nb), kThreads, CtSmem<N>::sm, st>>>(t, (const float2*)tw3, (const float2*)cyl,
                                                                        (float2*)out, scale, (const float*)diag,
                                                                        (const float2*)cin);

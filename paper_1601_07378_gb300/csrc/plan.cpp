@@ -451,6 +451,15 @@ int vloc_plan_create(vloc_plan* out, int n1, int n2, int n3, const int32_t* g, i
             xq = xrow_plane[x] == want;
         }
         L.xq = xq ? 1 : 0;
+        // every l within the quarter band of n3 (the z-pass kernels take the
+        // band at compile time; VLOC_NO_XQ turns this off too)
+        const int Q3 = n3 / 4;
+        bool zq = Q3 >= 1 && std::getenv("VLOC_NO_XQ") == nullptr;
+        for (int64_t q = 0; zq && q < npw; ++q) {
+            const int z = pw_z[q];
+            zq = z <= Q3 || z >= n3 - Q3;
+        }
+        L.zq = zq ? 1 : 0;
     }
 
     if (host_only) {
@@ -1211,7 +1220,7 @@ int vloc_get_info(vloc_plan p, vloc_info* info) {
     info->nsticks = p->S; info->nplanes = p->NP; info->nparts = p->P;
     info->lines_per_tile = kLinesPerTile;
     info->path = (p->fast ? 1 : 0) | (p->gamma ? 4 : 0) | (p->df ? 8 : 0) | (p->k3tma_on ? 16 : 0) |
-                 (p->lay.xq ? 32 : 0);
+                 (p->lay.xq ? 32 : 0) | (p->lay.zq ? 64 : 0);
     info->chunk_bands = p->chunk;
     info->workspace_bytes = (int64_t)p->ws_bytes;
     for (int a = 0; a < 3; ++a) {
@@ -1245,5 +1254,6 @@ DevTables vloc::device_tables(const int* base, const HostTableLayout& L, int n1,
     t.S = L.S; t.T = L.T; t.NP = L.NP;
     t.n1 = n1; t.n2 = n2; t.n3 = n3; t.npw = npw;
     t.xq = L.xq;
+    t.zq = L.zq;
     return t;
 }

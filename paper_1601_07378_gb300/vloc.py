@@ -257,6 +257,7 @@ class VlocPlan:
             "double_float": bool(inf.path & 8),
             "x_tma": bool(inf.path & 16),
             "x_quarter": bool(inf.path & 32),
+            "z_quarter": bool(inf.path & 64),
         }
 
     def set_schedule(self, axis: int, radices):

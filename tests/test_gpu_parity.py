@@ -357,13 +357,13 @@ def test_graph_batched_matches_individual():
                                           ((48, 60, 72), 11, 9, 0), ((32, 48, 96), 8, 20, 7)])
 def test_x_tma_option_is_bit_identical(n, R, nb, chunk, monkeypatch):
     # the persistent TMA x-pass (VLOC_X_TMA) runs the same arithmetic as the
-    # general x-pass (k3_ct; the quarter-sphere form is turned off for the
-    # reference plan): forward and backward results equal bit for bit
+    # general x-pass (k3_ct; the quarter-sphere forms are turned off in both
+    # plans): forward and backward results equal bit for bit
     g, c, V = make_case(n, R, nb, seed=5, order="shuffled", prec="f32")
-    monkeypatch.setenv("VLOC_NO_XQ", "1")
+    monkeypatch.setenv("VLOC_NO_XQ", "1")   # the same general z-, y- and x-passes in both plans
     ref_plan, ct, Vt, ref = run(n, g, c, V, "f32", chunk=chunk)
-    monkeypatch.delenv("VLOC_NO_XQ")
     plan = vloc.VlocPlan(n, g, torch.complex64, chunk=chunk, x_tma=True)
+    monkeypatch.delenv("VLOC_NO_XQ")
     assert plan.info()["x_tma"]
     out = plan.apply(ct, Vt)
     gt = torch.from_numpy(synth.coefficients(g, nb, seed=6, dtype=np.complex64)).cuda()

@@ -100,3 +100,30 @@ def test_quarter_density_matches_oracle(n1, m, nb, monkeypatch):
     want = O.density(n, g, c.astype(np.complex128), occ.astype(np.float64))
     assert np.linalg.norm(rho - want) / np.linalg.norm(want) < TOL["f32"]
     assert np.linalg.norm(rho - rho0) / np.linalg.norm(rho0) < 3e-7
+
+
+@pytest.mark.parametrize("n3,m", CASES)
+@pytest.mark.parametrize("prec", ["f32", "f64"])
+def test_quarter_band_z_pass_matches_oracle(n3, m, prec, monkeypatch):
+    # every |l| <= n3/4: K1 clears and reads only the band's rows, K4's last
+    # forward stage forms only them (FP32 kernels; FP64 plans take the
+    # general z-pass and are checked alongside)
+    n = (m, m, n3)
+    g, c, V = make_case(n, n3 / 4, 3, seed=86, order="shuffled", prec=prec)
+    dt = torch.complex64 if prec == "f32" else torch.complex128
+    q = vloc.VlocPlan(n, g, dt)
+    monkeypatch.setenv("VLOC_NO_XQ", "1")
+    ref = vloc.VlocPlan(n, g, dt)
+    monkeypatch.delenv("VLOC_NO_XQ")
+    assert q.info()["z_quarter"] and not ref.info()["z_quarter"]
+    ct, Vt = torch.from_numpy(c).cuda(), torch.from_numpy(V).cuda()
+    out, out_ref = q.apply(ct, Vt), ref.apply(ct, Vt)
+    h = torch.from_numpy(np.linspace(0.5, 2.0, len(g))).to("cuda", Vt.dtype)   # a diagonal added in the gather
+    outh = q.apply_h(ct, Vt, h)
+    torch.cuda.synchronize()
+    o = out.cpu().numpy()
+    want = oracle_apply(n, g, c, V)
+    assert rel_l2_per_band(o, want).max() < TOL[prec]
+    assert rel_l2_per_band(o, out_ref.cpu().numpy().astype(np.complex128)).max() < (3e-7 if prec == "f32" else 1e-14)
+    want_h = want + np.asarray(h.cpu().numpy(), np.float64)[None, :] * c.astype(np.complex128)
+    assert rel_l2_per_band(outh.cpu().numpy(), want_h).max() < TOL[prec]
