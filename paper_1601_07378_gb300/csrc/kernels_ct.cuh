@@ -447,7 +447,16 @@ template <int N> __host__ __device__ constexpr size_t k3q_smem() {
 }
 
 #ifndef VLOC_MINB_K3Q
-#define VLOC_MINB_K3Q 5
+#define VLOC_MINB_K3Q 6
+#endif
+// chain units left over after the full rounds run as single-line tasks
+// spread over every thread (1), or as a partial round of line-pair units (0)
+#ifndef VLOC_K3Q_SPLIT
+#define VLOC_K3Q_SPLIT 1
+#endif
+// preferred shared-memory carveout of the quarter-sphere x-pass, percent
+#ifndef VLOC_K3Q_CARVEOUT
+#define VLOC_K3Q_CARVEOUT 100
 #endif
 constexpr int minb_k3q(int n) { return n <= 96 ? VLOC_MINB_K3Q : minb_k3(n); }
 template <int N, int W>
@@ -471,11 +480,12 @@ __global__ void __launch_bounds__(32 * W, minb_k3q(N)) k3q_ct(DevTables t, const
     const long long b = blockIdx.z;
     const int lines = min(kLines, n3 - z0);
     const bool act = 2 * slot < lines;
+    // twiddle rows (first read after the barrier that ends stage 0, which
+    // needs none)
     for (int e = threadIdx.x; e < N; e += 32 * W) {
         twA[e] = tw1[(e / R1) * (e % R1)];
         twB[e] = tw1[(e / R0) * (e % R0)];
     }
-    __syncthreads();
     const int pstride = n2 * n3;
     float2* sl = slab + b * t.NP * (long long)pstride + y * n3 + z0 + 2 * slot;  // plane 0, this lane's pair
     const float* vrow = Vr + (long long)y * n3 + z0 + 2 * slot;
@@ -502,37 +512,69 @@ __global__ void __launch_bounds__(32 * W, minb_k3q(N)) k3q_ct(DevTables t, const
     }
     __syncthreads();
     // last inverse stage -> psi(x) V(x, y, z) -> first forward stage, in
-    // registers (unit i holds x = i + r NB in both)
-    P2f h[UB][R1];
+    // registers (unit i holds x = i + r NB in both).  FR full rounds give
+    // every unit slot a line-pair unit; the LU units left over are split into
+    // single lines (32 line tasks per unit) spread over all threads, so no
+    // warp waits at the next barrier for a half-empty round.
+    constexpr int FR = VLOC_K3Q_SPLIT ? NB / (2 * W) : (NB + 2 * W - 1) / (2 * W);
+    constexpr int LU = VLOC_K3Q_SPLIT ? NB % (2 * W) : 0;
+    constexpr int LT = (LU * 32 + 32 * W - 1) / (32 * W);  // line tasks per thread
+    auto chain = [&](auto& hv, int i, const float* vr, auto vload) {
+        const float2* tw = twA + i * R1;  // i < NB = R0
+#pragma unroll
+        for (int r = 1; r < R1; ++r) hv[r] = cmul(hv[r], tw[r]);
+        Dft<R1, +1>::run(hv);
+#pragma unroll
+        for (int r = 0; r < R1; ++r) vload(hv[r], vr + (i + r * NB) * pstride);
+        Dft<R1, -1>::run(hv);
+    };
+    P2f h[FR > 0 ? FR : 1][R1];
+    float2 hl[LT > 0 ? LT : 1][R1];
     if (act) {
 #pragma unroll
-        for (int u = 0; u < UB; ++u) {
+        for (int u = 0; u < FR; ++u) {
             const int i = 2 * (warp + u * W) + sub;
-            if (NB % (2 * W) == 0 || i < NB) {
+            if (NB % (2 * W) != 0 && i >= NB) continue;
 #pragma unroll
-                for (int r = 0; r < R1; ++r) h[u][r] = sb(i + r * NB, slot);
-                const float2* tw = twA + i * R1;  // i < NB = R0
+            for (int r = 0; r < R1; ++r) h[u][r] = sb(i + r * NB, slot);
+            chain(h[u], i, vrow, [](P2f& v, const float* q) {
+                const float2 w = *reinterpret_cast<const float2*>(q);
+                v.a = cscale(v.a, w.x);
+                v.b = cscale(v.b, w.y);
+            });
+        }
+    }
+    if constexpr (LU > 0) {
 #pragma unroll
-                for (int r = 1; r < R1; ++r) h[u][r] = cmul(h[u][r], tw[r]);
-                Dft<R1, +1>::run(h[u]);
+        for (int k = 0; k < LT; ++k) {
+            const int tk = threadIdx.x + k * 32 * W;  // line task: unit, slot, line
+            const int i = FR * 2 * W + tk / 32, ls = (tk >> 1) & 15, ln = tk & 1;
+            if (tk < LU * 32 && 2 * ls < lines) {
 #pragma unroll
-                for (int r = 0; r < R1; ++r) {
-                    const float2 w = *reinterpret_cast<const float2*>(vrow + (i + r * NB) * pstride);
-                    h[u][r].a = cscale(h[u][r].a, w.x);
-                    h[u][r].b = cscale(h[u][r].b, w.y);
-                }
-                Dft<R1, -1>::run(h[u]);
+                for (int r = 0; r < R1; ++r) hl[k][r] = buf[(i + r * NB) * kLdP + 2 * ls + ln];
+                chain(hl[k], i, Vr + (long long)y * n3 + z0 + 2 * ls + ln,
+                      [](float2& v, const float* q) { v = cscale(v, *q); });
             }
         }
     }
     __syncthreads();
     if (act) {
 #pragma unroll
-        for (int u = 0; u < UB; ++u) {
+        for (int u = 0; u < FR; ++u) {
             const int i = 2 * (warp + u * W) + sub;
-            if (NB % (2 * W) == 0 || i < NB) {
+            if (NB % (2 * W) != 0 && i >= NB) continue;
 #pragma unroll
-                for (int r = 0; r < R1; ++r) sb(i * R1 + r, slot, h[u][r]);
+            for (int r = 0; r < R1; ++r) sb(i * R1 + r, slot, h[u][r]);
+        }
+    }
+    if constexpr (LU > 0) {
+#pragma unroll
+        for (int k = 0; k < LT; ++k) {
+            const int tk = threadIdx.x + k * 32 * W;
+            const int i = FR * 2 * W + tk / 32, ls = (tk >> 1) & 15, ln = tk & 1;
+            if (tk < LU * 32 && 2 * ls < lines) {
+#pragma unroll
+                for (int r = 0; r < R1; ++r) buf[(i * R1 + r) * kLdP + 2 * ls + ln] = hl[k][r];
             }
         }
     }
@@ -969,9 +1011,13 @@ int LaunchCT<T, N>::k3(const DevTables& t, const void* tw1, const void* V, long 
     if constexpr (Sched<N>::nst == 2) {
         if (t.xq) {
             constexpr size_t sm = k3q_smem<N>();
+            // the largest shared-memory carveout, so shared memory does not cap
+            // the resident blocks below what the registers allow
             static const cudaError_t onceq =
-                sm <= 48 * 1024 ? cudaSuccess
-                                : cudaFuncSetAttribute(k3q_ct<N, W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+                cudaFuncSetAttribute(k3q_ct<N, W>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                     VLOC_K3Q_CARVEOUT) != cudaSuccess ? cudaErrorInvalidValue
+                : sm <= 48 * 1024 ? cudaSuccess
+                                  : cudaFuncSetAttribute(k3q_ct<N, W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
             if (onceq) return (int)onceq;
             const dim3 grid(t.n2, (t.n3 + kLines - 1) / kLines, (unsigned)nb);
             k3q_ct<N, W><<<grid, 32 * W, sm, st>>>(t, (const float2*)tw1, (const float*)V, (float2*)slab);
