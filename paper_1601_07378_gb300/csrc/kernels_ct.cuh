@@ -454,11 +454,23 @@ template <int N> __host__ __device__ constexpr size_t k3q_smem() {
 #ifndef VLOC_K3Q_SPLIT
 #define VLOC_K3Q_SPLIT 1
 #endif
-// preferred shared-memory carveout of the quarter-sphere x-pass, percent
-#ifndef VLOC_K3Q_CARVEOUT
-#define VLOC_K3Q_CARVEOUT 100
+
+#ifndef VLOC_MINB_K3Q_100
+#define VLOC_MINB_K3Q_100 6
 #endif
-constexpr int minb_k3q(int n) { return n <= 96 ? VLOC_MINB_K3Q : minb_k3(n); }
+#ifndef VLOC_MINB_K3Q_120
+#define VLOC_MINB_K3Q_120 5
+#endif
+#ifndef VLOC_MINB_K3Q_128
+#define VLOC_MINB_K3Q_128 5
+#endif
+#ifndef VLOC_MINB_K3Q_144
+#define VLOC_MINB_K3Q_144 4
+#endif
+constexpr int minb_k3q(int n) {
+    return n <= 96 ? VLOC_MINB_K3Q : n == 100 ? VLOC_MINB_K3Q_100 : n == 120 ? VLOC_MINB_K3Q_120
+           : n == 128 ? VLOC_MINB_K3Q_128 : n == 144 ? VLOC_MINB_K3Q_144 : 1;
+}
 template <int N, int W>
 __global__ void __launch_bounds__(32 * W, minb_k3q(N)) k3q_ct(DevTables t, const float2* __restrict__ tw1,
                                                   const float* __restrict__ Vr, float2* slab) {
@@ -1011,13 +1023,11 @@ int LaunchCT<T, N>::k3(const DevTables& t, const void* tw1, const void* V, long 
     if constexpr (Sched<N>::nst == 2) {
         if (t.xq) {
             constexpr size_t sm = k3q_smem<N>();
-            // the largest shared-memory carveout, so shared memory does not cap
-            // the resident blocks below what the registers allow
+            // (a preferred shared-memory carveout, 86 % or 100 %, measured
+            // slower at every length than the driver's own choice)
             static const cudaError_t onceq =
-                cudaFuncSetAttribute(k3q_ct<N, W>, cudaFuncAttributePreferredSharedMemoryCarveout,
-                                     VLOC_K3Q_CARVEOUT) != cudaSuccess ? cudaErrorInvalidValue
-                : sm <= 48 * 1024 ? cudaSuccess
-                                  : cudaFuncSetAttribute(k3q_ct<N, W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+                sm <= 48 * 1024 ? cudaSuccess
+                                : cudaFuncSetAttribute(k3q_ct<N, W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
             if (onceq) return (int)onceq;
             const dim3 grid(t.n2, (t.n3 + kLines - 1) / kLines, (unsigned)nb);
             k3q_ct<N, W><<<grid, 32 * W, sm, st>>>(t, (const float2*)tw1, (const float*)V, (float2*)slab);
