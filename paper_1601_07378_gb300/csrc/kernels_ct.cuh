@@ -262,75 +262,109 @@ __global__ void __launch_bounds__(kThreads, minb_k1(N)) k1_ct(DevTables t, const
 // When every plane wave has |l| <= N/4 (a sphere of radius n3/4: the z rows
 // of each stick lie in the band of Fig. 5), only the rows the first inverse
 // stage reads are cleared, and that stage skips the rows known to be zero.
-template <int N>
-__global__ void __launch_bounds__(kThreads, minb_k1(N)) k1q_ct(DevTables t, const float2* __restrict__ tw3,
-                                                  const float2* __restrict__ coeffs, float2* __restrict__ cyl) {
+// A block runs BPC bands of one tile, each in its own tile buffer: the
+// tile's entries are loaded once and every band's coefficients are requested
+// and scattered before the first transform starts.
+#ifndef VLOC_K1_BPC
+#define VLOC_K1_BPC 1
+#endif
+#ifndef VLOC_MINB_K1Q2
+#define VLOC_MINB_K1Q2 4
+#endif
+template <int N, int BPC> __host__ __device__ constexpr size_t k1q_smem() {
+    return BPC * (size_t)N * kLdP * sizeof(float2) + (size_t)N * sizeof(float2);
+}
+template <int N, int BPC>
+__global__ void __launch_bounds__(kThreads, BPC > 1 ? VLOC_MINB_K1Q2 : minb_k1(N)) k1q_ct(DevTables t, const float2* __restrict__ tw3,
+                                                  const float2* __restrict__ coeffs, long long nb,
+                                                  float2* __restrict__ cyl) {
     using SC = Sched<N>;
     static_assert(SC::nst == 2, "quarter-band z-pass: two-stage lengths");
     using QR = QRows<N>;
     constexpr int R0 = QR::R0, NA = QR::NA, W = kWarps;
     constexpr int UA = (NA + 2 * W - 1) / (2 * W);
+    constexpr int B = VLOC_SCATTER_BATCH;
+    constexpr int RW = kLdP / 2;  // float4 per row
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    float2* buf = reinterpret_cast<float2*>(smem_raw);
-    float2* stw = buf + N * kLdP;
+    float2* buf0 = reinterpret_cast<float2*>(smem_raw);
+    float2* stw = buf0 + BPC * N * kLdP;
     const int tile = blockIdx.x;
-    const long long b = blockIdx.y;
+    const long long b0 = (long long)blockIdx.y * BPC;
+    const int nbk = (int)min((long long)BPC, nb - b0);
     const int slot = slot_of(), sub = sub_of(), warp = warp_of();
+    const int2* ent = t.tile_pw;
+    const int e0 = t.tile_pw_ptr[tile], e1 = t.tile_pw_ptr[tile + 1];
+    const int base0 = e0 + (int)threadIdx.x;
+    {   // scatter every band: first batch's loads, clearing of the rows
+        // stage 0 reads, stores
+        int2 en[B];
+        float2 val[BPC][B];
+#pragma unroll
+        for (int u = 0; u < B; ++u) {
+            const int e = base0 + u * kThreads;
+            en[u] = e < e1 ? ent[e] : make_int2(0, -1);
+        }
+#pragma unroll
+        for (int k = 0; k < BPC; ++k) {
+            const float2* c = coeffs + (b0 + k) * t.npw;
+#pragma unroll
+            for (int u = 0; u < B; ++u) val[k][u] = (k < nbk && en[u].y >= 0) ? c[en[u].x] : make_float2(0.f, 0.f);
+        }
+        for (int i = threadIdx.x; i < BPC * N * RW; i += kThreads)
+            if (xq_row_read<N>((i % (N * RW)) / RW)) reinterpret_cast<float4*>(buf0)[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < BPC; ++k) entries_store_p<B>(buf0 + k * N * kLdP, en, val[k]);
+        for (int base = base0 + B * kThreads; base < e1; base += B * kThreads) {
+#pragma unroll
+            for (int k = 0; k < BPC; ++k) {
+                if (k >= nbk) break;
+                entries_load_p<B>(ent, base, e1, coeffs + (b0 + k) * t.npw, en, val[0]);
+                entries_store_p<B>(buf0 + k * N * kLdP, en, val[0]);
+            }
+        }
+    }
     load_tw<float>(stw, tw3, N);
     const int s0 = t.tile_ptr[tile], lines = t.tile_ptr[tile + 1] - s0;
-    {   // scatter: first batch's loads, clearing of the rows stage 0 reads, stores
-        constexpr int B = VLOC_SCATTER_BATCH;
-        const int2* ent = t.tile_pw;
-        const int e0 = t.tile_pw_ptr[tile], e1 = t.tile_pw_ptr[tile + 1];
-        const float2* c = coeffs + b * t.npw;
-        int2 en[B];
-        float2 val[B];
-        const int base0 = e0 + (int)threadIdx.x;
-        entries_load_p<B>(ent, base0, e1, c, en, val);
-        constexpr int RW = kLdP / 2;  // float4 per row
-        for (int i = threadIdx.x; i < N * RW; i += kThreads)
-            if (xq_row_read<N>(i / RW)) reinterpret_cast<float4*>(buf)[i] = make_float4(0.f, 0.f, 0.f, 0.f);
-        __syncthreads();
-        entries_store_p<B>(buf, en, val);
-        for (int base = base0 + B * kThreads; base < e1; base += B * kThreads) {
-            entries_load_p<B>(ent, base, e1, c, en, val);
-            entries_store_p<B>(buf, en, val);
-        }
-        __syncthreads();
-    }
     const bool act = 2 * slot < lines;
-    SmemP sb{buf};
-    // first inverse stage in place (every unit's values in registers, then stored)
-    P2f h[UA][R0];
-    if (act) {
+    __syncthreads();
 #pragma unroll
-        for (int u = 0; u < UA; ++u) {
-            const int i = 2 * (warp + u * W) + sub;
-            if (NA % (2 * W) == 0 || i < NA) {
-                sfor<R0>([&](auto rc) {
-                    constexpr int r = decltype(rc)::value;
-                    if constexpr (QR::kind(r) == 0) h[u][r] = czero<P2f>();
-                    else h[u][r] = sb(i + r * NA, slot);
-                });
-                DftZ<R0, +1, QR::mask()>::run(h[u]);
+    for (int k = 0; k < BPC; ++k) {
+        if (k >= nbk) break;  // uniform over the block
+        float2* buf = buf0 + k * N * kLdP;
+        SmemP sb{buf};
+        // first inverse stage in place (every unit's values in registers, then stored)
+        P2f h[UA][R0];
+        if (act) {
+#pragma unroll
+            for (int u = 0; u < UA; ++u) {
+                const int i = 2 * (warp + u * W) + sub;
+                if (NA % (2 * W) == 0 || i < NA) {
+                    sfor<R0>([&](auto rc) {
+                        constexpr int r = decltype(rc)::value;
+                        if constexpr (QR::kind(r) == 0) h[u][r] = czero<P2f>();
+                        else h[u][r] = sb(i + r * NA, slot);
+                    });
+                    DftZ<R0, +1, QR::mask()>::run(h[u]);
+                }
             }
         }
-    }
-    __syncthreads();
-    if (act) {
+        __syncthreads();
+        if (act) {
 #pragma unroll
-        for (int u = 0; u < UA; ++u) {
-            const int i = 2 * (warp + u * W) + sub;
-            if (NA % (2 * W) == 0 || i < NA) {
+            for (int u = 0; u < UA; ++u) {
+                const int i = 2 * (warp + u * W) + sub;
+                if (NA % (2 * W) == 0 || i < NA) {
 #pragma unroll
-                for (int r = 0; r < R0; ++r) sb(i * R0 + r, slot, h[u][r]);
+                    for (int r = 0; r < R0; ++r) sb(i * R0 + r, slot, h[u][r]);
+                }
             }
         }
+        __syncthreads();
+        NatStage<N, +1, W, 1>::template run<true>(stw, sb, sb, slot, sub, warp, act);
+        __syncthreads();
+        rows_out_p<N>(buf, cyl + (b0 + k) * (long long)t.S * N, t.tile_sticks + s0, lines);
     }
-    __syncthreads();
-    NatStage<N, +1, W, 1>::template run<true>(stw, sb, sb, slot, sub, warp, act);
-    __syncthreads();
-    rows_out_p<N>(buf, cyl + b * (long long)t.S * N, t.tile_sticks + s0, lines);
 }
 
 // ------------------------------------------------------------------ K2
@@ -984,10 +1018,14 @@ int LaunchCT<T, N>::k1(const DevTables& t, const void* tw3, const void* coeffs, 
     static_assert(std::is_same<T, float>::value, "compile-time kernels are FP32");
     if constexpr (Sched<N>::nst == 2) {
         if (t.zq) {
-            static const cudaError_t onceq = CtSmem<N>::ensure(k1q_ct<N>);
+            constexpr int BPC = VLOC_K1_BPC;
+            constexpr size_t sm = k1q_smem<N, BPC>();
+            static const cudaError_t onceq =
+                sm <= 48 * 1024 ? cudaSuccess
+                                : cudaFuncSetAttribute(k1q_ct<N, BPC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
             if (onceq) return (int)onceq;
-            k1q_ct<N><<<dim3(t.T, (unsigned)nb), kThreads, CtSmem<N>::sm, st>>>(t, (const float2*)tw3,
-                                                                                 (const float2*)coeffs, (float2*)cyl);
+            k1q_ct<N, BPC><<<dim3(t.T, (unsigned)((nb + BPC - 1) / BPC)), kThreads, sm, st>>>(
+                t, (const float2*)tw3, (const float2*)coeffs, nb, (float2*)cyl);
             return (int)cudaGetLastError();
         }
     }
