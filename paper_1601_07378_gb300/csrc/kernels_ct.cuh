@@ -691,8 +691,8 @@ __global__ void __launch_bounds__(kThreads, minb_k4(N)) k4q_ct(DevTables t, cons
     const int tile = blockIdx.x;
     const long long b = blockIdx.y;
     const int slot = slot_of(), sub = sub_of(), warp = warp_of();
-    load_tw<float>(stw, tw3, N);
     const int s0 = t.tile_ptr[tile], lines = t.tile_ptr[tile + 1] - s0;
+    load_tw<float>(stw, tw3, N);
     rows_in_p<N>(buf, cyl + b * (long long)t.S * N, t.tile_sticks + s0, lines);
     __syncthreads();
     const bool act = 2 * slot < lines;
@@ -771,6 +771,88 @@ __global__ void __launch_bounds__(kThreads) k3b_ct(DevTables t, const float2* __
             NatStage<N, +1, kWarps, 2>::template run<true>(stw, sb, sb, slot, sub, warp, act);
             __syncthreads();
         }
+        if (act) {
+#pragma unroll
+            for (int u = 0; u < L::U; ++u) {
+                const int i = 2 * (warp + u * kWarps) + sub;
+                if (L::NI % (2 * kWarps) == 0 || i < L::NI) {
+                    P2f h[R];
+                    L::compute_unit(h, stw, sb, i, slot);
+#pragma unroll
+                    for (int r = 0; r < R; ++r) {
+                        const P2f p = sa(i + r * L::NI, slot);
+                        acc[u][r].x += h[r].a.x * p.a.x + h[r].a.y * p.a.y;
+                        acc[u][r].y += h[r].b.x * p.b.x + h[r].b.y * p.b.y;
+                    }
+                }
+            }
+        }
+        __syncthreads();
+    }
+    if (act) {
+        double* part = partial + (long long)grp * t.n1 * pstride + y * n3 + z0 + 2 * slot;
+#pragma unroll
+        for (int u = 0; u < L::U; ++u) {
+            const int i = 2 * (warp + u * kWarps) + sub;
+            if (L::NI % (2 * kWarps) == 0 || i < L::NI) {
+#pragma unroll
+                for (int r = 0; r < R; ++r) {
+                    double* q = part + (i + r * L::NI) * pstride;
+                    q[0] = (double)acc[u][r].x * invN;
+                    q[1] = (double)acc[u][r].y * invN;
+                }
+            }
+        }
+    }
+}
+
+// dL/dV x-pass for the quarter-sphere plane set: k3b_ct with the first
+// inverse stage of both transforms reading only the cuboid's rows.
+#ifndef VLOC_MINB_K3BQ
+#define VLOC_MINB_K3BQ 1
+#endif
+template <int N>
+__global__ void __launch_bounds__(kThreads, VLOC_MINB_K3BQ) k3bq_ct(DevTables t, const float2* __restrict__ tw1,
+                                                   const float2* slab_c, const float2* slab_g, int nb, int bpg,
+                                                   double* __restrict__ partial, double invN) {
+    using SC = Sched<N>;
+    static_assert(SC::nst == 2, "quarter-sphere x-pass: two-stage lengths");
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int n2 = t.n2, n3 = t.n3;
+    float2* bufA = reinterpret_cast<float2*>(smem_raw);
+    float2* bufB = bufA + N * kLdP;
+    float2* stw = bufB + N * kLdP;
+    const int slot = slot_of(), sub = sub_of(), warp = warp_of();
+    const int y = blockIdx.x;
+    const int z0 = blockIdx.y * kLines;
+    const int grp = blockIdx.z;
+    const int lines = min(kLines, n3 - z0);
+    const bool act = 2 * slot < lines;
+    load_tw<float>(stw, tw1, N);
+    __syncthreads();
+    const int pstride = n2 * n3;
+    using L = NatStage<N, +1, kWarps, 1>;
+    constexpr int R = SC::R(1);
+    float2 acc[L::U][R];
+#pragma unroll
+    for (int u = 0; u < L::U; ++u)
+#pragma unroll
+        for (int r = 0; r < R; ++r) acc[u][r] = make_float2(0.f, 0.f);
+    SmemP sa{bufA}, sb{bufB};
+    const int b1 = min(nb, (grp + 1) * bpg);
+    for (int b = grp * bpg; b < b1; ++b) {
+        const long long off = (long long)b * t.NP * pstride + y * n3 + z0 + 2 * slot;
+        const float2* xc = slab_c + off;
+        const float2* xg = slab_g + off;
+        if (act) {
+            xq_first_inverse<N, kWarps, P2f>([&](int p) { return *reinterpret_cast<const P2f*>(xc + p * pstride); },
+                                             sa, slot, sub, warp);
+            xq_first_inverse<N, kWarps, P2f>([&](int p) { return *reinterpret_cast<const P2f*>(xg + p * pstride); },
+                                             sb, slot, sub, warp);
+        }
+        __syncthreads();
+        L::template run<true>(stw, sa, sa, slot, sub, warp, act);  // psi complete in A
+        __syncthreads();
         if (act) {
 #pragma unroll
             for (int u = 0; u < L::U; ++u) {
@@ -1089,6 +1171,17 @@ int LaunchCT<T, N>::k3b(const DevTables& t, const void* tw1, const void* sc, con
     const int ng = (int)((nb + bpg - 1) / bpg);
     const dim3 grid(t.n2, (t.n3 + kLines - 1) / kLines, ng);
     const double invN = 1.0 / ((double)t.n1 * t.n2 * t.n3);
+    if constexpr (Sched<N>::nst == 2) {
+        if (t.xq) {
+            static const cudaError_t onceq =
+                sm <= 48 * 1024 ? cudaSuccess
+                                : cudaFuncSetAttribute(k3bq_ct<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+            if (onceq) return (int)onceq;
+            k3bq_ct<N><<<grid, kThreads, sm, st>>>(t, (const float2*)tw1, (const float2*)sc, (const float2*)sg, (int)nb,
+                                                  bpg, partial, invN);
+            return (int)cudaGetLastError();
+        }
+    }
     k3b_ct<N><<<grid, kThreads, sm, st>>>(t, (const float2*)tw1, (const float2*)sc, (const float2*)sg, (int)nb, bpg,
                                           partial, invN);
     return (int)cudaGetLastError();
