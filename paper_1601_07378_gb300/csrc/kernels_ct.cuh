@@ -1012,14 +1012,20 @@ __global__ void __launch_bounds__(kThreads, minb(N, 5)) k3d_ct(DevTables t, cons
 }
 
 // Density x-pass for the quarter-sphere plane set: k3d_ct with the first
-// inverse stage reading only the cuboid's rows (xq_first_inverse).
+// inverse stage reading only the cuboid's rows (xq_first_inverse), and its
+// last stage balanced as in k3q_ct (units left over after the full rounds of
+// line-pair units run as single-line tasks spread over every thread).
+#ifndef VLOC_MINB_K3DQ
+#define VLOC_MINB_K3DQ 6
+#endif
 template <int N>
-__global__ void __launch_bounds__(kThreads, minb(N, 5)) k3dq_ct(DevTables t, const float2* __restrict__ tw1,
+__global__ void __launch_bounds__(kThreads, N <= 96 ? VLOC_MINB_K3DQ : 1) k3dq_ct(DevTables t, const float2* __restrict__ tw1,
                                                    const float2* slab, int nb, int bpg, const float* __restrict__ occ,
                                                    long long b_base, int pair, long long nreal,
                                                    double* __restrict__ partial) {
     using SC = Sched<N>;
     static_assert(SC::nst == 2, "quarter-sphere x-pass: two-stage lengths");
+    constexpr int W = kWarps;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int n2 = t.n2, n3 = t.n3;
     float2* buf = reinterpret_cast<float2*>(smem_raw);
@@ -1033,13 +1039,20 @@ __global__ void __launch_bounds__(kThreads, minb(N, 5)) k3dq_ct(DevTables t, con
     load_tw<float>(stw, tw1, N);
     __syncthreads();
     const int pstride = n2 * n3;
-    using L = NatStage<N, +1, kWarps, 1>;
-    constexpr int R = SC::R(1);
-    float2 acc[L::U][R];
+    using L = NatStage<N, +1, W, 1>;
+    constexpr int R = SC::R(1), NB = L::NI;
+    constexpr int FR = NB / (2 * W), LU = NB % (2 * W);
+    constexpr int LT = (LU * 32 + 32 * W - 1) / (32 * W);  // line tasks per thread
+    float2 acc[FR > 0 ? FR : 1][R];
+    float accl[LT > 0 ? LT : 1][R];
 #pragma unroll
-    for (int u = 0; u < L::U; ++u)
+    for (int u = 0; u < FR; ++u)
 #pragma unroll
         for (int r = 0; r < R; ++r) acc[u][r] = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int k = 0; k < LT; ++k)
+#pragma unroll
+        for (int r = 0; r < R; ++r) accl[k][r] = 0.f;
     SmemP sb{buf};
     const int b1 = min(nb, (grp + 1) * bpg);
     for (int b = grp * bpg; b < b1; ++b) {
@@ -1048,38 +1061,58 @@ __global__ void __launch_bounds__(kThreads, minb(N, 5)) k3dq_ct(DevTables t, con
         const float wx = (float)wxd, wy = (float)wyd;
         const float2* sl = slab + (long long)b * t.NP * pstride + y * n3 + z0 + 2 * slot;
         if (act)
-            xq_first_inverse<N, kWarps, P2f>([&](int p) { return *reinterpret_cast<const P2f*>(sl + p * pstride); },
-                                             sb, slot, sub, warp);
+            xq_first_inverse<N, W, P2f>([&](int p) { return *reinterpret_cast<const P2f*>(sl + p * pstride); }, sb,
+                                        slot, sub, warp);
         __syncthreads();
         if (act) {
 #pragma unroll
-            for (int u = 0; u < L::U; ++u) {
-                const int i = 2 * (warp + u * kWarps) + sub;
-                if (L::NI % (2 * kWarps) == 0 || i < L::NI) {
-                    P2f h[R];
-                    L::compute_unit(h, stw, sb, i, slot);
+            for (int u = 0; u < FR; ++u) {
+                const int i = 2 * (warp + u * W) + sub;
+                P2f h[R];
+                L::compute_unit(h, stw, sb, i, slot);
 #pragma unroll
-                    for (int r = 0; r < R; ++r) {
-                        acc[u][r].x += wx * h[r].a.x * h[r].a.x + wy * h[r].a.y * h[r].a.y;
-                        acc[u][r].y += wx * h[r].b.x * h[r].b.x + wy * h[r].b.y * h[r].b.y;
-                    }
+                for (int r = 0; r < R; ++r) {
+                    acc[u][r].x += wx * h[r].a.x * h[r].a.x + wy * h[r].a.y * h[r].a.y;
+                    acc[u][r].y += wx * h[r].b.x * h[r].b.x + wy * h[r].b.y * h[r].b.y;
+                }
+            }
+        }
+        if constexpr (LU > 0) {
+#pragma unroll
+            for (int k = 0; k < LT; ++k) {
+                const int tk = threadIdx.x + k * 32 * W;  // line task: unit, slot, line
+                const int i = FR * 2 * W + tk / 32, ls = (tk >> 1) & 15, ln = tk & 1;
+                if (tk < LU * 32 && 2 * ls < lines) {
+                    float2 h[R];
+                    NatStage<N, +1, W, 1, float2>::compute_unit(h, stw, SmemT<float2>{buf + ln}, i, ls);
+#pragma unroll
+                    for (int r = 0; r < R; ++r) accl[k][r] += wx * h[r].x * h[r].x + wy * h[r].y * h[r].y;
                 }
             }
         }
         __syncthreads();
     }
+    double* part0 = partial + (long long)grp * N * pstride + y * n3 + z0;
     if (act) {
-        double* part = partial + (long long)grp * N * pstride + y * n3 + z0 + 2 * slot;
 #pragma unroll
-        for (int u = 0; u < L::U; ++u) {
-            const int i = 2 * (warp + u * kWarps) + sub;
-            if (L::NI % (2 * kWarps) == 0 || i < L::NI) {
+        for (int u = 0; u < FR; ++u) {
+            const int i = 2 * (warp + u * W) + sub;
 #pragma unroll
-                for (int r = 0; r < R; ++r) {
-                    double* q = part + (i + r * L::NI) * pstride;
-                    q[0] = (double)acc[u][r].x;
-                    q[1] = (double)acc[u][r].y;
-                }
+            for (int r = 0; r < R; ++r) {
+                double* q = part0 + 2 * slot + (i + r * NB) * pstride;
+                q[0] = (double)acc[u][r].x;
+                q[1] = (double)acc[u][r].y;
+            }
+        }
+    }
+    if constexpr (LU > 0) {
+#pragma unroll
+        for (int k = 0; k < LT; ++k) {
+            const int tk = threadIdx.x + k * 32 * W;
+            const int i = FR * 2 * W + tk / 32, ls = (tk >> 1) & 15, ln = tk & 1;
+            if (tk < LU * 32 && 2 * ls < lines) {
+#pragma unroll
+                for (int r = 0; r < R; ++r) part0[2 * ls + ln + (i + r * NB) * pstride] = (double)accl[k][r];
             }
         }
     }
