@@ -124,7 +124,9 @@ typedef struct vloc_info {
                                  /* set x = 0..n1/4, n1 - n1/4 .. n1 - 1, and the */
                                  /* x-pass kernels take them at compile time;     */
                                  /* bit 6: every |l| <= n3/4, and the z-pass       */
-                                 /* kernels skip the rows outside that band       */
+                                 /* kernels skip the rows outside that band;      */
+                                 /* bit 7: Gamma-point pairs are formed and       */
+                                 /* separated inside the z-passes (no pack pass)  */
 } vloc_info;
 
 /*

@@ -34,6 +34,14 @@ struct DevTables {
     // 1 when every plane wave has l mod n3 in 0..n3/4 or n3 - n3/4 .. n3 - 1
     // (|l| <= n3/4): the z-pass kernels then skip the rows outside that band
     int zq;
+    // Gamma-point plans whose every G shares a z-pass tile with its -G (gok):
+    // per tile [gamma_h_ptr[t], gamma_h_ptr[t+1]) of gamma_h = {h, position
+    // of G, position of -G, 0} for the half-list plane waves h whose G lies
+    // in the tile (position = z | line << 16; the two coincide at G = 0)
+    int gok;
+    long long npw_half;  // half-list plane waves per real band (Gamma plans)
+    const int* gamma_h_ptr;
+    const int4* gamma_h;
 };
 
 struct LaunchAxes {
@@ -102,6 +110,13 @@ template <typename T, int N> struct LaunchCT {
                   cudaStream_t st);
     static int k4(const DevTables& t, const void* tw3, const void* cyl, long long nb, void* out, const void* diag,
                   const void* cin, cudaStream_t st);
+    // Gamma-point pairs (needs DevTables::gok): K1 forms pair p from real
+    // bands 2p, 2p + 1 of c [nreal][npw_half]; K4 writes both real bands'
+    // results (+ diag times the band when diag is set)
+    static int k1g(const DevTables& t, const void* tw3, const void* c, long long npairs, long long nreal, void* cyl,
+                   cudaStream_t st);
+    static int k4g(const DevTables& t, const void* tw3, const void* cyl, long long npairs, long long nreal, void* out,
+                   const void* diag, const void* cin, cudaStream_t st);
     static int k3b(const DevTables& t, const void* tw1, const void* sc, const void* sg, long long nb, int bpg,
                    double* partial, cudaStream_t st);
     static int k3g(int sign, const DevTables& t, const void* tw1, long long nb, void* slab, void* grid, cudaStream_t st);
@@ -166,6 +181,13 @@ int launch_gamma_pack(int dbl, const void* c, long long nb, long long nh, const 
                       long long np, cudaStream_t st);
 int launch_gamma_unpack(int dbl, const void* U, long long np, long long nfull, const int* neg, long long nh,
                         void* out, long long nb, const void* diag, const void* c, cudaStream_t st);
+// Gamma-point pairs formed / separated inside the FP32 compile-time z-passes
+// (DevTables::gok; n3 must have compiled kernels): K1 reads real bands
+// c [nreal][npw_half] as npairs pairs, K4 writes them back (+ diag * c)
+int launch_k1_gamma(const DevTables& t, const void* tw3, const void* c, long long npairs, long long nreal, void* cyl,
+                    cudaStream_t st);
+int launch_k4_gamma(const DevTables& t, const void* tw3, const void* cyl, long long npairs, long long nreal, void* out,
+                    const void* diag, const void* cin, cudaStream_t st);
 int launch_zero_f64(double* p, long long n, cudaStream_t st);
 size_t smem_bytes_for(int dbl, int n);
 size_t grad_smem_bytes(int dbl, int n);
@@ -184,6 +206,9 @@ struct HostTableLayout {
     int S, T, NP;
     int xq;  // DevTables::xq
     int zq;  // DevTables::zq
+    int gok;  // DevTables::gok
+    size_t o_ghp, o_gh;
+    long long nh;  // DevTables::npw_half
 };
 
 // DevTables pointing into a device copy of the table block at `base`.

@@ -161,6 +161,24 @@ int launch_k1_scatter_zpass(int dbl, int fast, const DevTables& t, const LaunchA
     }
     return dbl ? Launch<double>::k1(t, ax, tw3, coeffs, nb, cyl, st) : Launch<float>::k1(t, ax, tw3, coeffs, nb, cyl, st);
 }
+int launch_k1_gamma(const DevTables& t, const void* tw3, const void* c, long long npairs, long long nreal, void* cyl,
+                    cudaStream_t st) {
+    switch (t.n3) {
+#define VLOC_CASE(N) case N: return LaunchCT<float, N>::k1g(t, tw3, c, npairs, nreal, cyl, st);
+        VLOC_CT_SIZES(VLOC_CASE)
+#undef VLOC_CASE
+        default: return (int)cudaErrorInvalidValue;
+    }
+}
+int launch_k4_gamma(const DevTables& t, const void* tw3, const void* cyl, long long npairs, long long nreal, void* out,
+                    const void* diag, const void* cin, cudaStream_t st) {
+    switch (t.n3) {
+#define VLOC_CASE(N) case N: return LaunchCT<float, N>::k4g(t, tw3, cyl, npairs, nreal, out, diag, cin, st);
+        VLOC_CT_SIZES(VLOC_CASE)
+#undef VLOC_CASE
+        default: return (int)cudaErrorInvalidValue;
+    }
+}
 int launch_k2_ypass(int dbl, int fast, int sign, const DevTables& t, const LaunchAxes& ax, const void* tw2,
                     long long nb, void* cyl, void* slab, cudaStream_t st) {
     if (dbl && fast == 2) switch (t.n2) {

@@ -75,6 +75,52 @@ __device__ __forceinline__ int sub_of() { return (threadIdx.x >> 4) & 1; }
 __device__ __forceinline__ int warp_of() { return threadIdx.x >> 5; }
 
 // ------------------------------------------------------------- tile I/O
+// Gamma-point real mode (Sec. 4.3): two real bands 2p, 2p + 1 travel as one
+// complex band a + i b over the full G / -G list.  The z-passes can form
+// that band from the caller's half-list arrays as they read them, and
+// separate the two results as they write them, when every G shares a tile
+// with its -G (DevTables::gok).
+struct GammaArgs {
+    long long nh;        // half-list plane waves per real band
+    long long nreal;     // real bands of the call (the last pair may be half)
+    const float* diag;   // H apply: real [nh] diagonal added in the gather, or null
+    const float2* cin;   // the caller's bands [nreal][nh] (for diag)
+};
+// One batch of B of a tile's half-list entries {h, position of G, position
+// of -G, 0} of a Gamma pair (real bands a and b, b null when absent): the
+// entries and both bands' coefficients into registers, then a + i b at G and
+// conj(a) + i conj(b) at -G into the tile buffer (the real parts at G = 0,
+// whose two positions coincide).
+template <int B>
+__device__ __forceinline__ void gamma_load(const int4* __restrict__ ent, int base, int e1, const float2* __restrict__ a,
+                                           const float2* __restrict__ b, int4 (&en)[B], float2 (&va)[B],
+                                           float2 (&vb)[B]) {
+#pragma unroll
+    for (int u = 0; u < B; ++u) {
+        const int e = base + u * kThreads;
+        en[u] = e < e1 ? ent[e] : make_int4(-1, 0, 0, 0);
+    }
+#pragma unroll
+    for (int u = 0; u < B; ++u) {
+        va[u] = en[u].x >= 0 ? a[en[u].x] : make_float2(0.f, 0.f);
+        vb[u] = (en[u].x >= 0 && b) ? b[en[u].x] : make_float2(0.f, 0.f);
+    }
+}
+template <int B>
+__device__ __forceinline__ void gamma_store(float2* buf, const int4 (&en)[B], const float2 (&va)[B],
+                                            const float2 (&vb)[B]) {
+#pragma unroll
+    for (int u = 0; u < B; ++u) {
+        if (en[u].x < 0) continue;
+        float2* pg = buf + (en[u].y & 0xffff) * kLdP + (en[u].y >> 16);
+        if (en[u].y == en[u].z) {
+            *pg = make_float2(va[u].x, vb[u].x);
+        } else {
+            *pg = make_float2(va[u].x - vb[u].y, va[u].y + vb[u].x);
+            buf[(en[u].z & 0xffff) * kLdP + (en[u].z >> 16)] = make_float2(va[u].x + vb[u].y, vb[u].x - va[u].y);
+        }
+    }
+}
 // One batch of B of a tile's plane-wave entries starting at `base` (stride
 // kThreads): the entries and their coefficients into registers, then into
 // the tile buffer.
@@ -121,6 +167,28 @@ __device__ __forceinline__ void scatter_tile_p(const int2* __restrict__ ent, int
     }
     __syncthreads();
 }
+// The same for a Gamma pair p of the caller's real bands (GammaArgs).
+template <int N>
+__device__ __forceinline__ void scatter_tile_gamma(const DevTables& t, int tile, const float2* __restrict__ coeffs,
+                                                   long long p, const GammaArgs& g, float2* buf) {
+    constexpr int B = VLOC_SCATTER_BATCH;
+    int4 en[B];
+    float2 va[B], vb[B];
+    const float2* a = coeffs + 2 * p * g.nh;
+    const float2* b = 2 * p + 1 < g.nreal ? coeffs + (2 * p + 1) * g.nh : nullptr;
+    const int e0 = t.gamma_h_ptr[tile], e1 = t.gamma_h_ptr[tile + 1];
+    const int base0 = e0 + (int)threadIdx.x;
+    gamma_load<B>(t.gamma_h, base0, e1, a, b, en, va, vb);
+    for (int i = threadIdx.x; i < N * kLdP / 2; i += kThreads)
+        reinterpret_cast<float4*>(buf)[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    __syncthreads();
+    gamma_store<B>(buf, en, va, vb);
+    for (int base = base0 + B * kThreads; base < e1; base += B * kThreads) {
+        gamma_load<B>(t.gamma_h, base, e1, a, b, en, va, vb);
+        gamma_store<B>(buf, en, va, vb);
+    }
+    __syncthreads();
+}
 #ifndef VLOC_GATHER_BATCH
 #define VLOC_GATHER_BATCH 8
 #endif
@@ -152,6 +220,45 @@ __device__ __forceinline__ void gather_entries_p(const int2* __restrict__ ent, i
             for (int u = 0; u < GB; ++u)
                 if (en[u].y >= 0) o[en[u].x] = cscale(buf[(en[u].y & 0xffff) * kLdP + (en[u].y >> 16)], scale);
         }
+    }
+}
+// Gamma-point gather of pair p: for every half-list plane wave of the tile,
+// U(G) and U(-G) (both in the tile buffer, times 1/N) give the two real
+// bands' results, A a = (U(G) + conj U(-G)) / 2 and A b = (U(G) - conj
+// U(-G)) / 2i, plus diag times the band for an H apply.
+__device__ __forceinline__ void gather_gamma(const int4* __restrict__ ent, int e0, int e1, const float2* buf,
+                                             float2* oa, float2* ob, float scale, const float* __restrict__ diag,
+                                             const float2* ca, const float2* cb) {
+    for (int e = e0 + (int)threadIdx.x; e < e1; e += kThreads) {
+        const int4 en = ent[e];
+        const float2 x = cscale(buf[(en.y & 0xffff) * kLdP + (en.y >> 16)], scale);   // U(G)
+        const float2 y = cscale(buf[(en.z & 0xffff) * kLdP + (en.z >> 16)], scale);   // U(-G)
+        float2 a = make_float2((x.x + y.x) * 0.5f, (x.y - y.y) * 0.5f);
+        float2 b = make_float2((x.y + y.y) * 0.5f, (y.x - x.x) * 0.5f);
+        if (diag) {  // c is read before out is written (they may alias)
+            const float d = diag[en.x];
+            const float2 va = ca[en.x];
+            a.x += d * va.x; a.y += d * va.y;
+            if (ob) {
+                const float2 vb = cb[en.x];
+                b.x += d * vb.x; b.y += d * vb.y;
+            }
+        }
+        oa[en.x] = a;
+        if (ob) ob[en.x] = b;
+    }
+}
+template <bool GM>
+__device__ __forceinline__ void gather_tile(const DevTables& t, int tile, const float2* buf, float2* out, long long b,
+                                            float scale, const float* diag, const float2* cin, const GammaArgs& g) {
+    if constexpr (!GM) {
+        gather_entries_p(t.tile_pw, t.tile_pw_ptr[tile], t.tile_pw_ptr[tile + 1], buf, out + b * t.npw, scale, diag,
+                         diag ? cin + b * t.npw : cin);
+    } else {
+        const bool two = 2 * b + 1 < g.nreal;
+        gather_gamma(t.gamma_h, t.gamma_h_ptr[tile], t.gamma_h_ptr[tile + 1], buf, out + 2 * b * g.nh,
+                     two ? out + (2 * b + 1) * g.nh : nullptr, scale, g.diag, g.cin + 2 * b * g.nh,
+                     g.cin + (2 * b + 1) * g.nh);
     }
 }
 // Tile rows <-> cylinder, a line pair (2s, 2s + 1) per warp pass: lane j
@@ -241,9 +348,10 @@ struct XRowsP {  // x rows at fixed y: the occupied planes
 };
 
 // ------------------------------------------------------------------ K1
-template <int N>
+template <int N, bool GM = false>
 __global__ void __launch_bounds__(kThreads, minb_k1(N)) k1_ct(DevTables t, const float2* __restrict__ tw3,
-                                                 const float2* __restrict__ coeffs, float2* __restrict__ cyl) {
+                                                 const float2* __restrict__ coeffs, float2* __restrict__ cyl,
+                                                 GammaArgs g) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float2* buf = reinterpret_cast<float2*>(smem_raw);
     float2* stw = buf + N * kLdP;
@@ -251,7 +359,8 @@ __global__ void __launch_bounds__(kThreads, minb_k1(N)) k1_ct(DevTables t, const
     const long long b = blockIdx.y;
     load_tw<float>(stw, tw3, N);
     const int s0 = t.tile_ptr[tile], lines = t.tile_ptr[tile + 1] - s0;
-    scatter_tile_p<N>(t.tile_pw, t.tile_pw_ptr[tile], t.tile_pw_ptr[tile + 1], coeffs + b * t.npw, buf);
+    if constexpr (GM) scatter_tile_gamma<N>(t, tile, coeffs, b, g, buf);
+    else scatter_tile_p<N>(t.tile_pw, t.tile_pw_ptr[tile], t.tile_pw_ptr[tile + 1], coeffs + b * t.npw, buf);
     fft_ct<N, +1, kWarps, false, true, true>(stw, SmemP{buf}, SmemP{buf}, buf, slot_of(), sub_of(), warp_of(),
                                              2 * slot_of() < lines);
     __syncthreads();
@@ -262,22 +371,13 @@ __global__ void __launch_bounds__(kThreads, minb_k1(N)) k1_ct(DevTables t, const
 // When every plane wave has |l| <= N/4 (a sphere of radius n3/4: the z rows
 // of each stick lie in the band of Fig. 5), only the rows the first inverse
 // stage reads are cleared, and that stage skips the rows known to be zero.
-// A block runs BPC bands of one tile, each in its own tile buffer: the
-// tile's entries are loaded once and every band's coefficients are requested
-// and scattered before the first transform starts.
-#ifndef VLOC_K1_BPC
-#define VLOC_K1_BPC 1
-#endif
-#ifndef VLOC_MINB_K1Q2
-#define VLOC_MINB_K1Q2 4
-#endif
-template <int N, int BPC> __host__ __device__ constexpr size_t k1q_smem() {
-    return BPC * (size_t)N * kLdP * sizeof(float2) + (size_t)N * sizeof(float2);
-}
-template <int N, int BPC>
-__global__ void __launch_bounds__(kThreads, BPC > 1 ? VLOC_MINB_K1Q2 : minb_k1(N)) k1q_ct(DevTables t, const float2* __restrict__ tw3,
-                                                  const float2* __restrict__ coeffs, long long nb,
-                                                  float2* __restrict__ cyl) {
+// The first batch of the tile's entries and coefficients is requested before
+// the clearing, the twiddle table after the scatter.  GM: a Gamma-point pair per block,
+// formed from the caller's two real bands as they are read.
+template <int N, bool GM = false>
+__global__ void __launch_bounds__(kThreads, minb_k1(N)) k1q_ct(DevTables t, const float2* __restrict__ tw3,
+                                                  const float2* __restrict__ coeffs, float2* __restrict__ cyl,
+                                                  GammaArgs g) {
     using SC = Sched<N>;
     static_assert(SC::nst == 2, "quarter-band z-pass: two-stage lengths");
     using QR = QRows<N>;
@@ -286,85 +386,81 @@ __global__ void __launch_bounds__(kThreads, BPC > 1 ? VLOC_MINB_K1Q2 : minb_k1(N
     constexpr int B = VLOC_SCATTER_BATCH;
     constexpr int RW = kLdP / 2;  // float4 per row
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    float2* buf0 = reinterpret_cast<float2*>(smem_raw);
-    float2* stw = buf0 + BPC * N * kLdP;
+    float2* buf = reinterpret_cast<float2*>(smem_raw);
+    float2* stw = buf + N * kLdP;
     const int tile = blockIdx.x;
-    const long long b0 = (long long)blockIdx.y * BPC;
-    const int nbk = (int)min((long long)BPC, nb - b0);
+    const long long b = blockIdx.y;
     const int slot = slot_of(), sub = sub_of(), warp = warp_of();
-    const int2* ent = t.tile_pw;
-    const int e0 = t.tile_pw_ptr[tile], e1 = t.tile_pw_ptr[tile + 1];
-    const int base0 = e0 + (int)threadIdx.x;
-    {   // scatter every band: first batch's loads, clearing of the rows
-        // stage 0 reads, stores
-        int2 en[B];
-        float2 val[BPC][B];
-#pragma unroll
-        for (int u = 0; u < B; ++u) {
-            const int e = base0 + u * kThreads;
-            en[u] = e < e1 ? ent[e] : make_int2(0, -1);
-        }
-#pragma unroll
-        for (int k = 0; k < BPC; ++k) {
-            const float2* c = coeffs + (b0 + k) * t.npw;
-#pragma unroll
-            for (int u = 0; u < B; ++u) val[k][u] = (k < nbk && en[u].y >= 0) ? c[en[u].x] : make_float2(0.f, 0.f);
-        }
-        for (int i = threadIdx.x; i < BPC * N * RW; i += kThreads)
-            if (xq_row_read<N>((i % (N * RW)) / RW)) reinterpret_cast<float4*>(buf0)[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    auto clear_read_rows = [&] {
+        for (int i = threadIdx.x; i < N * RW; i += kThreads)
+            if (xq_row_read<N>(i / RW)) reinterpret_cast<float4*>(buf)[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    };
+    if constexpr (GM) {
+        int4 en[B];
+        float2 va[B], vb[B];
+        const float2* a = coeffs + 2 * b * g.nh;
+        const float2* bb = 2 * b + 1 < g.nreal ? coeffs + (2 * b + 1) * g.nh : nullptr;
+        const int e0 = t.gamma_h_ptr[tile], e1 = t.gamma_h_ptr[tile + 1];
+        const int base0 = e0 + (int)threadIdx.x;
+        gamma_load<B>(t.gamma_h, base0, e1, a, bb, en, va, vb);
+        clear_read_rows();
         __syncthreads();
-#pragma unroll
-        for (int k = 0; k < BPC; ++k) entries_store_p<B>(buf0 + k * N * kLdP, en, val[k]);
+        gamma_store<B>(buf, en, va, vb);
         for (int base = base0 + B * kThreads; base < e1; base += B * kThreads) {
-#pragma unroll
-            for (int k = 0; k < BPC; ++k) {
-                if (k >= nbk) break;
-                entries_load_p<B>(ent, base, e1, coeffs + (b0 + k) * t.npw, en, val[0]);
-                entries_store_p<B>(buf0 + k * N * kLdP, en, val[0]);
-            }
+            gamma_load<B>(t.gamma_h, base, e1, a, bb, en, va, vb);
+            gamma_store<B>(buf, en, va, vb);
+        }
+    } else {
+        int2 en[B];
+        float2 val[B];
+        const float2* c = coeffs + b * t.npw;
+        const int e0 = t.tile_pw_ptr[tile], e1 = t.tile_pw_ptr[tile + 1];
+        const int base0 = e0 + (int)threadIdx.x;
+        entries_load_p<B>(t.tile_pw, base0, e1, c, en, val);
+        clear_read_rows();
+        __syncthreads();
+        entries_store_p<B>(buf, en, val);
+        for (int base = base0 + B * kThreads; base < e1; base += B * kThreads) {
+            entries_load_p<B>(t.tile_pw, base, e1, c, en, val);
+            entries_store_p<B>(buf, en, val);
         }
     }
     load_tw<float>(stw, tw3, N);
     const int s0 = t.tile_ptr[tile], lines = t.tile_ptr[tile + 1] - s0;
     const bool act = 2 * slot < lines;
     __syncthreads();
+    SmemP sb{buf};
+    // first inverse stage in place (every unit's values in registers, then stored)
+    P2f h[UA][R0];
+    if (act) {
 #pragma unroll
-    for (int k = 0; k < BPC; ++k) {
-        if (k >= nbk) break;  // uniform over the block
-        float2* buf = buf0 + k * N * kLdP;
-        SmemP sb{buf};
-        // first inverse stage in place (every unit's values in registers, then stored)
-        P2f h[UA][R0];
-        if (act) {
-#pragma unroll
-            for (int u = 0; u < UA; ++u) {
-                const int i = 2 * (warp + u * W) + sub;
-                if (NA % (2 * W) == 0 || i < NA) {
-                    sfor<R0>([&](auto rc) {
-                        constexpr int r = decltype(rc)::value;
-                        if constexpr (QR::kind(r) == 0) h[u][r] = czero<P2f>();
-                        else h[u][r] = sb(i + r * NA, slot);
-                    });
-                    DftZ<R0, +1, QR::mask()>::run(h[u]);
-                }
+        for (int u = 0; u < UA; ++u) {
+            const int i = 2 * (warp + u * W) + sub;
+            if (NA % (2 * W) == 0 || i < NA) {
+                sfor<R0>([&](auto rc) {
+                    constexpr int r = decltype(rc)::value;
+                    if constexpr (QR::kind(r) == 0) h[u][r] = czero<P2f>();
+                    else h[u][r] = sb(i + r * NA, slot);
+                });
+                DftZ<R0, +1, QR::mask()>::run(h[u]);
             }
         }
-        __syncthreads();
-        if (act) {
-#pragma unroll
-            for (int u = 0; u < UA; ++u) {
-                const int i = 2 * (warp + u * W) + sub;
-                if (NA % (2 * W) == 0 || i < NA) {
-#pragma unroll
-                    for (int r = 0; r < R0; ++r) sb(i * R0 + r, slot, h[u][r]);
-                }
-            }
-        }
-        __syncthreads();
-        NatStage<N, +1, W, 1>::template run<true>(stw, sb, sb, slot, sub, warp, act);
-        __syncthreads();
-        rows_out_p<N>(buf, cyl + (b0 + k) * (long long)t.S * N, t.tile_sticks + s0, lines);
     }
+    __syncthreads();
+    if (act) {
+#pragma unroll
+        for (int u = 0; u < UA; ++u) {
+            const int i = 2 * (warp + u * W) + sub;
+            if (NA % (2 * W) == 0 || i < NA) {
+#pragma unroll
+                for (int r = 0; r < R0; ++r) sb(i * R0 + r, slot, h[u][r]);
+            }
+        }
+    }
+    __syncthreads();
+    NatStage<N, +1, W, 1>::template run<true>(stw, sb, sb, slot, sub, warp, act);
+    __syncthreads();
+    rows_out_p<N>(buf, cyl + b * (long long)t.S * N, t.tile_sticks + s0, lines);
 }
 
 // ------------------------------------------------------------------ K2
@@ -651,10 +747,10 @@ __global__ void __launch_bounds__(32 * W, minb_k3q(N)) k3q_ct(DevTables t, const
 }
 
 // ------------------------------------------------------------------ K4
-template <int N>
+template <int N, bool GM = false>
 __global__ void __launch_bounds__(kThreads, minb_k4(N)) k4_ct(DevTables t, const float2* __restrict__ tw3,
                                                  const float2* __restrict__ cyl, float2* out, float scale,
-                                                 const float* __restrict__ diag, const float2* cin) {
+                                                 const float* __restrict__ diag, const float2* cin, GammaArgs g) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float2* buf = reinterpret_cast<float2*>(smem_raw);
     float2* stw = buf + N * kLdP;
@@ -667,18 +763,17 @@ __global__ void __launch_bounds__(kThreads, minb_k4(N)) k4_ct(DevTables t, const
     fft_ct<N, -1, kWarps, false, true, true>(stw, SmemP{buf}, SmemP{buf}, buf, slot_of(), sub_of(), warp_of(),
                                              2 * slot_of() < lines);
     __syncthreads();
-    gather_entries_p(t.tile_pw, t.tile_pw_ptr[tile], t.tile_pw_ptr[tile + 1], buf, out + b * t.npw, scale, diag,
-                     diag ? cin + b * t.npw : cin);
+    gather_tile<GM>(t, tile, buf, out, b, scale, diag, cin, g);
 }
 
 // ------------------------------------------------- K4, quarter-band form
 // The forward z-pass in the reversed schedule, whose last stage (radix R0)
 // writes row x = i + r NA of unit i: rows outside the band |l| <= N/4 are
 // never gathered, so they are never formed.
-template <int N>
+template <int N, bool GM = false>
 __global__ void __launch_bounds__(kThreads, minb_k4(N)) k4q_ct(DevTables t, const float2* __restrict__ tw3,
                                                   const float2* __restrict__ cyl, float2* out, float scale,
-                                                  const float* __restrict__ diag, const float2* cin) {
+                                                  const float* __restrict__ diag, const float2* cin, GammaArgs g) {
     using SC = Sched<N>;
     static_assert(SC::nst == 2, "quarter-band z-pass: two-stage lengths");
     using QR = QRows<N>;
@@ -715,8 +810,7 @@ __global__ void __launch_bounds__(kThreads, minb_k4(N)) k4q_ct(DevTables t, cons
         }
     }
     __syncthreads();
-    gather_entries_p(t.tile_pw, t.tile_pw_ptr[tile], t.tile_pw_ptr[tile + 1], buf, out + b * t.npw, scale, diag,
-                     diag ? cin + b * t.npw : cin);
+    gather_tile<GM>(t, tile, buf, out, b, scale, diag, cin, g);
 }
 
 // ----------------------------------------------------------------- K3b
@@ -1127,28 +1221,37 @@ template <int N> struct CtSmem {
     }
 };
 
+// K1 over nb bands (GM: nb Gamma-point pairs formed from the caller's real
+// bands as they are read)
+template <int N, bool GM>
+int launch_k1_ct(const DevTables& t, const void* tw3, const void* coeffs, long long nb, void* cyl, const GammaArgs& g,
+                 cudaStream_t st) {
+    if constexpr (Sched<N>::nst == 2) {
+        if (t.zq) {
+            static const cudaError_t onceq = CtSmem<N>::ensure(k1q_ct<N, GM>);
+            if (onceq) return (int)onceq;
+            k1q_ct<N, GM><<<dim3(t.T, (unsigned)nb), kThreads, CtSmem<N>::sm, st>>>(t, (const float2*)tw3,
+                                                                                    (const float2*)coeffs,
+                                                                                    (float2*)cyl, g);
+            return (int)cudaGetLastError();
+        }
+    }
+    static const cudaError_t once = CtSmem<N>::ensure(k1_ct<N, GM>);
+    if (once) return (int)once;
+    k1_ct<N, GM><<<dim3(t.T, (unsigned)nb), kThreads, CtSmem<N>::sm, st>>>(t, (const float2*)tw3,
+                                                                           (const float2*)coeffs, (float2*)cyl, g);
+    return (int)cudaGetLastError();
+}
 template <typename T, int N>
 int LaunchCT<T, N>::k1(const DevTables& t, const void* tw3, const void* coeffs, long long nb, void* cyl,
                        cudaStream_t st) {
     static_assert(std::is_same<T, float>::value, "compile-time kernels are FP32");
-    if constexpr (Sched<N>::nst == 2) {
-        if (t.zq) {
-            constexpr int BPC = VLOC_K1_BPC;
-            constexpr size_t sm = k1q_smem<N, BPC>();
-            static const cudaError_t onceq =
-                sm <= 48 * 1024 ? cudaSuccess
-                                : cudaFuncSetAttribute(k1q_ct<N, BPC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-            if (onceq) return (int)onceq;
-            k1q_ct<N, BPC><<<dim3(t.T, (unsigned)((nb + BPC - 1) / BPC)), kThreads, sm, st>>>(
-                t, (const float2*)tw3, (const float2*)coeffs, nb, (float2*)cyl);
-            return (int)cudaGetLastError();
-        }
-    }
-    static const cudaError_t once = CtSmem<N>::ensure(k1_ct<N>);
-    if (once) return (int)once;
-    k1_ct<N><<<dim3(t.T, (unsigned)nb), kThreads, CtSmem<N>::sm, st>>>(t, (const float2*)tw3, (const float2*)coeffs,
-                                                                       (float2*)cyl);
-    return (int)cudaGetLastError();
+    return launch_k1_ct<N, false>(t, tw3, coeffs, nb, cyl, GammaArgs{}, st);
+}
+template <typename T, int N>
+int LaunchCT<T, N>::k1g(const DevTables& t, const void* tw3, const void* coeffs, long long npairs, long long nreal,
+                        void* cyl, cudaStream_t st) {
+    return launch_k1_ct<N, true>(t, tw3, coeffs, npairs, cyl, GammaArgs{t.npw_half, nreal, nullptr, nullptr}, st);
 }
 template <typename T, int N>
 int LaunchCT<T, N>::k2(int sign, const DevTables& t, const void* tw2, long long nb, void* cyl, void* slab,
@@ -1254,25 +1357,36 @@ int LaunchCT<T, N>::k3d(const DevTables& t, const void* tw1, const void* slab, l
                                                      (const float*)occ, b_base, pair, nreal, partial);
     return (int)cudaGetLastError();
 }
-template <typename T, int N>
-int LaunchCT<T, N>::k4(const DevTables& t, const void* tw3, const void* cyl, long long nb, void* out,
-                       const void* diag, const void* cin, cudaStream_t st) {
+template <int N, bool GM>
+int launch_k4_ct(const DevTables& t, const void* tw3, const void* cyl, long long nb, void* out, const void* diag,
+                 const void* cin, const GammaArgs& g, cudaStream_t st) {
     const float scale = (float)(1.0 / ((double)t.n1 * t.n2 * t.n3));
     if constexpr (Sched<N>::nst == 2) {
         if (t.zq) {
-            static const cudaError_t onceq = CtSmem<N>::ensure(k4q_ct<N>);
+            static const cudaError_t onceq = CtSmem<N>::ensure(k4q_ct<N, GM>);
             if (onceq) return (int)onceq;
-            k4q_ct<N><<<dim3(t.T, (unsigned)nb), kThreads, CtSmem<N>::sm, st>>>(
-                t, (const float2*)tw3, (const float2*)cyl, (float2*)out, scale, (const float*)diag, (const float2*)cin);
+            k4q_ct<N, GM><<<dim3(t.T, (unsigned)nb), kThreads, CtSmem<N>::sm, st>>>(
+                t, (const float2*)tw3, (const float2*)cyl, (float2*)out, scale, (const float*)diag, (const float2*)cin,
+                g);
             return (int)cudaGetLastError();
         }
     }
-    static const cudaError_t once = CtSmem<N>::ensure(k4_ct<N>);
+    static const cudaError_t once = CtSmem<N>::ensure(k4_ct<N, GM>);
     if (once) return (int)once;
-    k4_ct<N><<<dim3(t.T, (unsigned)nb), kThreads, CtSmem<N>::sm, st>>>(t, (const float2*)tw3, (const float2*)cyl,
-                                                                       (float2*)out, scale, (const float*)diag,
-                                                                       (const float2*)cin);
+    k4_ct<N, GM><<<dim3(t.T, (unsigned)nb), kThreads, CtSmem<N>::sm, st>>>(
+        t, (const float2*)tw3, (const float2*)cyl, (float2*)out, scale, (const float*)diag, (const float2*)cin, g);
     return (int)cudaGetLastError();
+}
+template <typename T, int N>
+int LaunchCT<T, N>::k4(const DevTables& t, const void* tw3, const void* cyl, long long nb, void* out,
+                       const void* diag, const void* cin, cudaStream_t st) {
+    return launch_k4_ct<N, false>(t, tw3, cyl, nb, out, diag, cin, GammaArgs{}, st);
+}
+template <typename T, int N>
+int LaunchCT<T, N>::k4g(const DevTables& t, const void* tw3, const void* cyl, long long npairs, long long nreal,
+                        void* out, const void* diag, const void* cin, cudaStream_t st) {
+    return launch_k4_ct<N, true>(t, tw3, cyl, npairs, out, nullptr, nullptr,
+                                 GammaArgs{t.npw_half, nreal, (const float*)diag, (const float2*)cin}, st);
 }
 
 }  // namespace vloc

@@ -145,6 +145,7 @@ struct vloc_plan_s {
     int* d_err = nullptr;       // set by a kernel whose bounded wait ran out
     bool k3tma_on = false;      // x-pass through the persistent TMA kernel
     bool poison = false;        // VLOC_POISON_WORKSPACE: NaN-fill before every chunk
+    bool gfused = false;        // Gamma pairs formed and separated inside the z-passes
     vloc::K3Tma k3tma{};
     bool gamma = false;       // Gamma-point real mode (half-sphere coefficients)
     long long npw_user = 0;   // plane waves per band in the caller's arrays
@@ -369,7 +370,34 @@ int vloc_plan_create(vloc_plan* out, int n1, int n2, int n3, const int32_t* g, i
             if (weight[a] != weight[b]) return weight[a] > weight[b];
             return stick_id[a] < stick_id[b];
         });
-        for (int r = 0; r < S; ++r) part[srt[r]] = r % P;
+        if (!(flags & VLOC_GAMMA)) {
+            for (int r = 0; r < S; ++r) part[srt[r]] = r % P;
+        } else {
+            // Gamma-point plans deal a stick and its mirror (-h, -k) together
+            // (Sec. 4.3: c(-G) = conj c(G) pairs them), so that one z-pass
+            // block holds both G and -G of every plane wave it owns.  The same
+            // rule on pairs: weight descending, ties by the smaller stick id,
+            // the k-th pair to part k mod P, at most 16 pairs per part.
+            std::vector<int> mirror(S);
+            for (int s2 = 0; s2 < S; ++s2) {
+                const long long a = stick_id[s2] / n2, bb = stick_id[s2] % n2;
+                const long long mid = ((n1 - a) % n1) * n2 + (n2 - bb) % n2;
+                const auto it = std::lower_bound(stick_id.begin(), stick_id.end(), mid);
+                mirror[s2] = (it != stick_id.end() && *it == mid) ? (int)(it - stick_id.begin()) : -1;
+            }
+            std::vector<int> pairs;  // first stick of each pair, in sorted order
+            for (int r = 0; r < S; ++r) {
+                const int s2 = srt[r], m = mirror[s2];
+                if (m < 0 || s2 <= m) pairs.push_back(s2);
+                else if (mirror[m] != s2) pairs.push_back(s2);
+            }
+            P = std::max(P, (int)((pairs.size() + kLinesPerTile / 2 - 1) / (kLinesPerTile / 2)));
+            for (size_t r = 0; r < pairs.size(); ++r) {
+                const int s2 = pairs[r], m = mirror[s2];
+                part[s2] = (int32_t)(r % P);
+                if (m >= 0) part[m] = (int32_t)(r % P);
+            }
+        }
     } else {
         int m, ncol;
         process_grid(P, &m, &ncol);
@@ -425,6 +453,34 @@ int vloc_plan_create(vloc_plan* out, int n1, int n2, int n3, const int32_t* g, i
     p->S = S; p->NP = NP; p->P = P; p->T = T;
     p->stick_part = part;
 
+    // ---- Gamma-point table for the z-passes that form and separate the
+    // real band pairs themselves (used when every G and its -G share a tile):
+    // per tile, {h, position of G, position of -G, 0} (position = z | line
+    // << 16) for every half-list plane wave whose G lies in the tile
+    std::vector<int> gamma_h_ptr, gamma_h;
+    bool gamma_ok = false;
+    if (flags & VLOC_GAMMA) {
+        const int64_t nh = npw_user;
+        std::vector<int> tile_of(npw, -1), pos_of(npw, 0);
+        for (int tt = 0; tt < T; ++tt)
+            for (int e = tile_pw_ptr[tt]; e < tile_pw_ptr[tt + 1]; ++e) {
+                const int f = tile_pw[2 * e];
+                tile_of[f] = tt;
+                pos_of[f] = tile_pw[2 * e + 1];
+            }
+        gamma_ok = true;
+        for (int64_t q = 0; gamma_ok && q < nh; ++q) gamma_ok = tile_of[q] == tile_of[gamma_neg[q]];
+        if (gamma_ok) {
+            std::vector<std::vector<int>> per(T);
+            for (int64_t q = 0; q < nh; ++q) per[tile_of[q]].push_back((int)q);
+            gamma_h_ptr.push_back(0);
+            for (int tt = 0; tt < T; ++tt) {
+                for (int q : per[tt]) gamma_h.insert(gamma_h.end(), {q, pos_of[q], pos_of[gamma_neg[q]], 0});
+                gamma_h_ptr.push_back((int)(gamma_h.size() / 4));
+            }
+        }
+    }
+
     // ---- host copy of the index tables, as the kernels read them
     {
         std::vector<int>& blob = p->host_tables;
@@ -438,6 +494,11 @@ int vloc_plan_create(vloc_plan* out, int n1, int n2, int n3, const int32_t* g, i
         L.o_tpw = append(tile_pw);
         L.o_plp = append(plane_ptr);
         L.o_xr = append(xrow_plane);
+        L.gok = gamma_ok ? 1 : 0;
+        L.nh = (flags & VLOC_GAMMA) ? npw_user : 0;
+        L.o_ghp = append(gamma_h_ptr);
+        while (blob.size() & 3) blob.push_back(0);  // int4 alignment
+        L.o_gh = append(gamma_h);
         L.total = blob.size();
         L.S = S; L.T = T; L.NP = NP;
         // the quarter-sphere x-plane pattern (x = 0..Q and n1 - Q .. n1 - 1,
@@ -487,6 +548,9 @@ int vloc_plan_create(vloc_plan* out, int n1, int n2, int n3, const int32_t* g, i
         free_plan(p); return cuda_fail(e, "upload tables");
     }
     p->dt = device_tables(p->d_tables, p->lay, n1, n2, n3, npw);
+    // the pair-forming z-passes exist for the FP32 compile-time kernels;
+    // VLOC_GAMMA_PACK (a test aid) keeps the separate pack / unpack passes
+    p->gfused = p->gamma && p->lay.gok && !dbl && p->fast && has_ct(n3) && std::getenv("VLOC_GAMMA_PACK") == nullptr;
 
     // ---- twiddles exp(+2 pi i j / n), FP64-made
     for (int a = 0; a < 3; ++a) {
@@ -585,6 +649,7 @@ int vloc_plan_set_schedule(vloc_plan p, int axis, int nst, const int32_t* radix)
     p->fast = 0;
     p->df = false;
     p->k3tma_on = false;
+    p->gfused = false;
     for (auto& g : p->graphs)
         if (g.exec) cudaGraphExecDestroy(g.exec);
     p->graphs.clear();
@@ -705,8 +770,34 @@ static int apply_impl(vloc_plan p, const void* c, const void* V, int64_t nb, voi
 // Gamma-point real mode: bands 2p and 2p+1 (real in r-space) travel as one
 // complex band a + i b through the chain; each result pair is separated with
 // U(G) and conj U(-G).
+// Gamma-point apply with the pairs formed and separated inside the z-passes
+// (FP32 compile-time kernels, every G in the same tile as its -G): no pack
+// or unpack pass and no pair buffers.
+static int gamma_apply_fused(vloc_plan p, const void* c, const void* V, int64_t nb, void* out, cudaStream_t st,
+                             const void* diag) {
+    const long long npairs = (nb + 1) / 2;
+    const size_t ustride = (size_t)p->npw_user * p->elem;
+    const DevTables& t = p->dt;
+    const LaunchAxes& ax = p->ax;
+    for (long long p0 = 0; p0 < npairs; p0 += p->chunk) {
+        const long long cp = std::min<long long>(p->chunk, npairs - p0);
+        const long long b0 = 2 * p0, bn = std::min<long long>(nb - b0, 2 * cp);
+        const void* cc = (const char*)c + b0 * ustride;
+        void* oo = (char*)out + b0 * ustride;
+        int rc;
+        if ((rc = poison(p, st))) return rc;
+        if ((rc = launch(p, KK_SCATTER_Z, st, [&] { return launch_k1_gamma(t, p->d_tw[2], cc, cp, bn, p->d_cyl, st); }))) return rc;
+        if ((rc = launch(p, KK_Y_INV, st, [&] { return launch_k2_ypass(0, p->fast, +1, t, ax, p->d_tw[1], cp, p->d_cyl, p->d_slab, st); }))) return rc;
+        if ((rc = launch(p, KK_X_V, st, [&] { return launch_k3_xpass_v(0, p->fast, t, ax, p->d_tw[0], V, cp, p->d_slab, st, p->k3tma_on ? &p->k3tma : nullptr); }))) return rc;
+        if ((rc = launch(p, KK_Y_FWD, st, [&] { return launch_k2_ypass(0, p->fast, -1, t, ax, p->d_tw[1], cp, p->d_cyl, p->d_slab, st); }))) return rc;
+        if ((rc = launch(p, KK_Z_GATHER, st, [&] { return launch_k4_gamma(t, p->d_tw[2], p->d_cyl, cp, bn, oo, diag, cc, st); }))) return rc;
+    }
+    return VLOC_OK;
+}
+
 static int gamma_apply(vloc_plan p, const void* c, const void* V, int64_t nb, void* out, cudaStream_t st,
                        const void* diag) {
+    if (p->gfused) return gamma_apply_fused(p, c, V, nb, out, st, diag);
     const long long npairs = (nb + 1) / 2;
     const size_t full = (size_t)p->npw * p->elem;
     char* C = (char*)p->d_gamma_buf;
@@ -1220,7 +1311,7 @@ int vloc_get_info(vloc_plan p, vloc_info* info) {
     info->nsticks = p->S; info->nplanes = p->NP; info->nparts = p->P;
     info->lines_per_tile = kLinesPerTile;
     info->path = (p->fast ? 1 : 0) | (p->gamma ? 4 : 0) | (p->df ? 8 : 0) | (p->k3tma_on ? 16 : 0) |
-                 (p->lay.xq ? 32 : 0) | (p->lay.zq ? 64 : 0);
+                 (p->lay.xq ? 32 : 0) | (p->lay.zq ? 64 : 0) | (p->gfused ? 128 : 0);
     info->chunk_bands = p->chunk;
     info->workspace_bytes = (int64_t)p->ws_bytes;
     for (int a = 0; a < 3; ++a) {
@@ -1255,5 +1346,9 @@ DevTables vloc::device_tables(const int* base, const HostTableLayout& L, int n1,
     t.n1 = n1; t.n2 = n2; t.n3 = n3; t.npw = npw;
     t.xq = L.xq;
     t.zq = L.zq;
+    t.gok = L.gok;
+    t.npw_half = L.nh;
+    t.gamma_h_ptr = base + L.o_ghp;
+    t.gamma_h = reinterpret_cast<const int4*>(base + L.o_gh);
     return t;
 }

@@ -258,6 +258,7 @@ class VlocPlan:
             "x_tma": bool(inf.path & 16),
             "x_quarter": bool(inf.path & 32),
             "z_quarter": bool(inf.path & 64),
+            "gamma_fused": bool(inf.path & 128),
         }
 
     def set_schedule(self, axis: int, radices):

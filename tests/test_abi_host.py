@@ -209,3 +209,30 @@ def test_quarter_sphere_plane_set_is_detected(lib):
     shifted = g + np.array([1, 0, 0], dtype=g.dtype)
     for other in (synth.sphere_glist(*n, 11.5), strict, shifted):
         assert not vloc.VlocPlan(n, other, torch.complex64, host_only=True).info()["x_quarter"]
+
+
+@pytest.mark.parametrize("n,R", [((16, 18, 20), 4.5), ((96, 96, 96), 24), ((30, 45, 27), 7)])
+def test_gamma_partition_deals_mirror_pairs(lib, n, R):
+    # Gamma-point plans deal a stick (h, k) and its mirror (-h, -k) to the
+    # same part: the greedy rule (Sec. 3.2) applied to pairs, weight
+    # descending, ties by the smaller stick id, the k-th pair to part k mod P
+    import torch
+    g = synth.sphere_glist(*n, R, order="shuffled", seed=5)
+    gh = synth.half_sphere(g)
+    plan = vloc.VlocPlan(n, gh, torch.complex64, host_only=True, gamma=True)
+    part, P = plan.partition()
+    ids, w = O.sticks(n, g)            # the full G / -G list's sticks, ascending id
+    assert len(part) == len(ids)
+    sid = {int(s): i for i, s in enumerate(ids)}
+    mirror = np.array([sid[((n[0] - s // n[1]) % n[0]) * n[1] + (n[1] - s % n[1]) % n[1]] for s in ids])
+    assert np.array_equal(part, part[mirror])
+    assert np.bincount(part, minlength=P).max() <= 32
+    # restatement of the rule
+    order = sorted(range(len(ids)), key=lambda i: (-int(w[i]), int(ids[i])))
+    pairs = [i for i in order if i <= mirror[i]]
+    P2 = max((len(ids) + 31) // 32, (len(pairs) + 15) // 16)
+    assert P == P2
+    want = np.empty(len(ids), dtype=np.int32)
+    for r, i in enumerate(pairs):
+        want[i] = want[mirror[i]] = r % P2
+    assert np.array_equal(part, want)

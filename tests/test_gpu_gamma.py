@@ -150,3 +150,47 @@ def test_gamma_rejects():
         plan.backward(c, c, V)
     assert e.value.code == -7
     assert np.array_equal(plan.index_map(), O.index_map(n, gh))
+
+
+@pytest.mark.parametrize("n,R,nb,chunk", [((24, 24, 24), 6, 1, 0), ((24, 24, 24), 6, 7, 2), ((40, 36, 50), 8, 5, 0),
+                                          ((30, 45, 27), 7, 6, 0), ((96, 96, 96), 24, 9, 4),
+                                          ((48, 48, 60), 11, 4, 1)])
+def test_gamma_pairs_formed_in_the_z_passes(n, R, nb, chunk, monkeypatch):
+    # FP32 compile-time plans form each pair a + i b as K1 reads the half
+    # list and separate the results as K4 writes them (no pack or unpack
+    # pass); against the oracle and against the plan with the separate passes
+    gh, c, V = gamma_case(n, R, nb, seed=23, order="shuffled", prec="f32")
+    plan = vloc.VlocPlan(n, gh, torch.complex64, gamma=True, chunk=chunk, poison=True)
+    monkeypatch.setenv("VLOC_GAMMA_PACK", "1")
+    ref_plan = vloc.VlocPlan(n, gh, torch.complex64, gamma=True, chunk=chunk)
+    monkeypatch.delenv("VLOC_GAMMA_PACK")
+    fused = all(x in (24, 32, 48, 60, 64, 72, 80, 96, 100, 120, 128, 144) for x in n[2:])
+    assert plan.info()["gamma_fused"] == fused and not ref_plan.info()["gamma_fused"]
+    ct = torch.from_numpy(c).cuda()
+    Vt = torch.from_numpy(V).cuda()
+    out = plan.apply(ct, Vt)
+    out_ref = ref_plan.apply(ct, Vt)
+    d = torch.from_numpy(np.linspace(0.25, 3.0, len(gh)).astype(np.float32)).cuda()
+    outh = plan.apply_h(ct, Vt, d)
+    torch.cuda.synchronize()
+    want = oracle_gamma(n, gh, c, V)
+    assert rel_l2_per_band(out.cpu().numpy(), want).max() < TOL["f32"]
+    assert rel_l2_per_band(out.cpu().numpy(), out_ref.cpu().numpy().astype(np.complex128)).max() < 3e-7
+    want_h = want + d.cpu().numpy().astype(np.float64)[None, :] * c.astype(np.complex128)
+    assert rel_l2_per_band(outh.cpu().numpy(), want_h).max() < TOL["f32"]
+    # out == coeffs
+    ca = ct.clone()
+    plan.apply(ca, Vt, out=ca)
+    torch.cuda.synchronize()
+    assert torch.equal(ca, out)
+
+
+def test_gamma_pair_forming_needs_mirrors_in_one_tile():
+    # the row/column partitions of Sec. 4.1 / 4.2 do not keep a stick and its
+    # mirror together, so their Gamma plans keep the separate passes
+    n = (32, 32, 32)
+    gh = synth.half_sphere(synth.sphere_glist(*n, 8))
+    assert vloc.VlocPlan(n, gh, torch.complex64, gamma=True).info()["gamma_fused"]
+    assert not vloc.VlocPlan(n, gh, torch.complex64, gamma=True, partition="basic").info()["gamma_fused"]
+    assert not vloc.VlocPlan(n, gh, torch.complex128, gamma=True).info()["gamma_fused"]
+    assert not vloc.VlocPlan(n, gh, torch.complex64, gamma=True, generic=True).info()["gamma_fused"]
