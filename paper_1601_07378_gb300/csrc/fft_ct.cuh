@@ -101,6 +101,13 @@ template <int N> struct QRows {
         for (int r = 0; r < R0; ++r) m |= (kind(r) ? 1u : 0u) << r;
         return m;
     }
+    // index of row group r among the groups that meet the cuboid
+    static constexpr int group(int r) {
+        int j = 0;
+        for (int q = 0; q < r; ++q) j += kind(q) ? 1 : 0;
+        return j;
+    }
+    static constexpr int groups() { return group(R0); }
     template <int r> __device__ __forceinline__ static bool inside(int i) {
         constexpr int k = kind(r);
         if constexpr (k == 1 || k == 2) return true;

@@ -38,6 +38,11 @@ struct DevTables {
     // per tile [gamma_h_ptr[t], gamma_h_ptr[t+1]) of gamma_h = {h, position
     // of G, position of -G, 0} for the half-list plane waves h whose G lies
     // in the tile (position = z | line << 16; the two coincide at G = 0)
+    // dense z-band table of plain plans (zd_rows > 0): [T][zd_rows][32] caller
+    // index of the plane wave at each (row, line) of a tile's first-stage row
+    // groups that meet the band |l| <= n3/4, or -1
+    int zd_rows;
+    const int* zdense;
     int gok;
     long long npw_half;  // half-list plane waves per real band (Gamma plans)
     const int* gamma_h_ptr;
@@ -207,7 +212,8 @@ struct HostTableLayout {
     int xq;  // DevTables::xq
     int zq;  // DevTables::zq
     int gok;  // DevTables::gok
-    size_t o_ghp, o_gh;
+    size_t o_ghp, o_gh, o_zd;
+    int zd_rows;
     long long nh;  // DevTables::npw_half
 };
 

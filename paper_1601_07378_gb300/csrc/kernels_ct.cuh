@@ -463,6 +463,65 @@ __global__ void __launch_bounds__(kThreads, minb_k1(N)) k1q_ct(DevTables t, cons
     rows_out_p<N>(buf, cyl + b * (long long)t.S * N, t.tile_sticks + s0, lines);
 }
 
+// ------------------------------------------------- K1, direct form
+// The quarter-band z-pass without the tile scatter: each thread loads its
+// own first-stage inputs through the dense z-band table (row x = i + r NA,
+// two lines per lane), so the tile buffer needs no clearing and the first
+// stage no shared-memory round trip before it.  Plain (complex) plans only:
+// for Gamma-point pairs the scatter over half-list entries, which reads each
+// pair of real coefficients once for G and -G, measured faster (0.207
+// against 0.298 ms per 1024 real bands at 96^3).
+#ifndef VLOC_K1_DIRECT
+#define VLOC_K1_DIRECT 1
+#endif
+template <int N>
+__global__ void __launch_bounds__(kThreads, minb_k1(N)) k1d_ct(DevTables t, const float2* __restrict__ tw3,
+                                                  const float2* __restrict__ coeffs, float2* __restrict__ cyl) {
+    using SC = Sched<N>;
+    static_assert(SC::nst == 2, "quarter-band z-pass: two-stage lengths");
+    using QR = QRows<N>;
+    constexpr int R0 = QR::R0, NA = QR::NA, W = kWarps;
+    constexpr int UA = (NA + 2 * W - 1) / (2 * W);
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float2* buf = reinterpret_cast<float2*>(smem_raw);
+    float2* stw = buf + N * kLdP;
+    const int tile = blockIdx.x;
+    const long long b = blockIdx.y;
+    const int slot = slot_of(), sub = sub_of(), warp = warp_of();
+    const int* zd = t.zdense + (size_t)tile * (QR::groups() * NA) * kLines + 2 * slot;
+    const float2* c = coeffs + b * t.npw;
+    auto coef = [&](int x) { return x == -1 ? make_float2(0.f, 0.f) : c[x]; };
+    SmemP sb{buf};
+#pragma unroll
+    for (int u = 0; u < UA; ++u) {
+        const int i = 2 * (warp + u * W) + sub;
+        if (NA % (2 * W) == 0 || i < NA) {
+            int2 e[R0];
+            sfor<R0>([&](auto rc) {
+                constexpr int r = decltype(rc)::value;
+                if constexpr (QR::kind(r) != 0)
+                    e[r] = *reinterpret_cast<const int2*>(zd + (QR::group(r) * NA + i) * kLines);
+            });
+            P2f h[R0];
+            sfor<R0>([&](auto rc) {
+                constexpr int r = decltype(rc)::value;
+                if constexpr (QR::kind(r) == 0) h[r] = czero<P2f>();
+                else h[r] = P2f{coef(e[r].x), coef(e[r].y)};
+            });
+            DftZ<R0, +1, QR::mask()>::run(h);
+#pragma unroll
+            for (int r = 0; r < R0; ++r) sb(i * R0 + r, slot, h[r]);
+        }
+    }
+    load_tw<float>(stw, tw3, N);
+    const int s0 = t.tile_ptr[tile], lines = t.tile_ptr[tile + 1] - s0;
+    const bool act = 2 * slot < lines;
+    __syncthreads();
+    NatStage<N, +1, W, 1>::template run<true>(stw, sb, sb, slot, sub, warp, act);
+    __syncthreads();
+    rows_out_p<N>(buf, cyl + b * (long long)t.S * N, t.tile_sticks + s0, lines);
+}
+
 // ------------------------------------------------------------------ K2
 template <int S, int N>
 __global__ void __launch_bounds__(kThreads, minb_k2(N, S)) k2_ct(DevTables t, const float2* __restrict__ tw2, float2* cyl,
@@ -811,6 +870,79 @@ __global__ void __launch_bounds__(kThreads, minb_k4(N)) k4q_ct(DevTables t, cons
     }
     __syncthreads();
     gather_tile<GM>(t, tile, buf, out, b, scale, diag, cin, g);
+}
+
+// ------------------------------------------------- K4, direct form
+// k4q_ct without the gather pass: the last forward stage (radix R0, rows
+// x = i + r NA, the row structure of the dense z-band table) writes each
+// result straight to its caller position, times 1/N, plus diag times the
+// band for an H apply.  Plain plans with the dense table.
+#ifndef VLOC_K4_DIRECT
+#define VLOC_K4_DIRECT 1
+#endif
+template <int N>
+__global__ void __launch_bounds__(kThreads, minb_k4(N)) k4d_ct(DevTables t, const float2* __restrict__ tw3,
+                                                  const float2* __restrict__ cyl, float2* out, float scale,
+                                                  const float* __restrict__ diag, const float2* cin) {
+    using SC = Sched<N>;
+    static_assert(SC::nst == 2, "quarter-band z-pass: two-stage lengths");
+    using QR = QRows<N>;
+    constexpr int R0 = QR::R0, NA = QR::NA, W = kWarps;
+    using L = RevStage<N, -1, W, 1>;  // radix R0, rows i + r NA
+    static_assert(L::NI == NA, "last forward stage rows");
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float2* buf = reinterpret_cast<float2*>(smem_raw);
+    float2* stw = buf + N * kLdP;
+    const int tile = blockIdx.x;
+    const long long b = blockIdx.y;
+    const int slot = slot_of(), sub = sub_of(), warp = warp_of();
+    load_tw<float>(stw, tw3, N);
+    const int s0 = t.tile_ptr[tile], lines = t.tile_ptr[tile + 1] - s0;
+    rows_in_p<N>(buf, cyl + b * (long long)t.S * N, t.tile_sticks + s0, lines);
+    __syncthreads();
+    const bool act = 2 * slot < lines;
+    SmemP sb{buf};
+    RevStage<N, -1, W, 0>::template run<true>(stw, sb, sb, slot, sub, warp, act);
+    __syncthreads();
+    if (!act) return;
+    const int* zd = t.zdense + (size_t)tile * (QR::groups() * NA) * kLines + 2 * slot;
+    float2* o = out + b * t.npw;
+    const float2* ci = cin + b * t.npw;
+#pragma unroll
+    for (int u = 0; u < L::U; ++u) {
+        const int i = 2 * (warp + u * W) + sub;
+        if (L::NI % (2 * W) == 0 || i < L::NI) {
+            int2 e[R0];
+            sfor<R0>([&](auto rc) {
+                constexpr int r = decltype(rc)::value;
+                if constexpr (QR::kind(r) != 0)
+                    e[r] = *reinterpret_cast<const int2*>(zd + (QR::group(r) * NA + i) * kLines);
+            });
+            P2f h[R0];
+            L::compute_unit(h, stw, sb, i, slot);
+            sfor<R0>([&](auto rc) {
+                constexpr int r = decltype(rc)::value;
+                if constexpr (QR::kind(r) != 0) {
+                    const int xa = e[r].x, xb = e[r].y;
+                    if (diag) {  // H = diag + A (c is read before out is written: they may alias)
+                        if (xa != -1) {
+                            const float d = diag[xa];
+                            const float2 cv = ci[xa], v = cscale(h[r].a, scale);
+                            o[xa] = make_float2(v.x + d * cv.x, v.y + d * cv.y);
+                        }
+                        if (xb != -1) {
+                            const float d = diag[xb];
+                            const float2 cv = ci[xb], v = cscale(h[r].b, scale);
+                            o[xb] = make_float2(v.x + d * cv.x, v.y + d * cv.y);
+                        }
+                    } else {
+                        if (xa != -1) o[xa] = cscale(h[r].a, scale);
+                        if (xb != -1) o[xb] = cscale(h[r].b, scale);
+                    }
+                }
+            });
+        }
+    }
 }
 
 // ----------------------------------------------------------------- K3b
@@ -1227,6 +1359,15 @@ template <int N, bool GM>
 int launch_k1_ct(const DevTables& t, const void* tw3, const void* coeffs, long long nb, void* cyl, const GammaArgs& g,
                  cudaStream_t st) {
     if constexpr (Sched<N>::nst == 2) {
+        // the dense table exists for plain plans only (its entries are caller
+        // indices of the complex band the kernel reads)
+        if (!GM && VLOC_K1_DIRECT && t.zd_rows == QRows<N>::groups() * QRows<N>::NA) {
+            static const cudaError_t onced = CtSmem<N>::ensure(k1d_ct<N>);
+            if (onced) return (int)onced;
+            k1d_ct<N><<<dim3(t.T, (unsigned)nb), kThreads, CtSmem<N>::sm, st>>>(t, (const float2*)tw3,
+                                                                                (const float2*)coeffs, (float2*)cyl);
+            return (int)cudaGetLastError();
+        }
         if (t.zq) {
             static const cudaError_t onceq = CtSmem<N>::ensure(k1q_ct<N, GM>);
             if (onceq) return (int)onceq;
@@ -1362,6 +1503,13 @@ int launch_k4_ct(const DevTables& t, const void* tw3, const void* cyl, long long
                  const void* cin, const GammaArgs& g, cudaStream_t st) {
     const float scale = (float)(1.0 / ((double)t.n1 * t.n2 * t.n3));
     if constexpr (Sched<N>::nst == 2) {
+        if (!GM && VLOC_K4_DIRECT && t.zd_rows == QRows<N>::groups() * QRows<N>::NA) {
+            static const cudaError_t onced = CtSmem<N>::ensure(k4d_ct<N>);
+            if (onced) return (int)onced;
+            k4d_ct<N><<<dim3(t.T, (unsigned)nb), kThreads, CtSmem<N>::sm, st>>>(
+                t, (const float2*)tw3, (const float2*)cyl, (float2*)out, scale, (const float*)diag, (const float2*)cin);
+            return (int)cudaGetLastError();
+        }
         if (t.zq) {
             static const cudaError_t onceq = CtSmem<N>::ensure(k4q_ct<N, GM>);
             if (onceq) return (int)onceq;

@@ -453,6 +453,40 @@ int vloc_plan_create(vloc_plan* out, int n1, int n2, int n3, const int32_t* g, i
     p->S = S; p->NP = NP; p->P = P; p->T = T;
     p->stick_part = part;
 
+    // ---- dense z-band table for the z-pass that loads each first-stage input
+    // itself (plain plans): per tile, for every row x = i + r NA (NA = n3 /
+    // R0, R0 the first radix of the n3 schedule) of a row group r that meets
+    // the band |l| <= n3/4, and every line of the tile, the caller index of
+    // the plane wave there, or -1.  Rows [tile][group j][i][line], groups in
+    // r order.
+    std::vector<int> zdense;
+    int zd_rows = 0;
+    {
+        const int R0 = p->ax.radix[2][0], Q3 = n3 / 4;
+        const int NA3 = R0 > 0 ? n3 / R0 : 0;
+        std::vector<int> groups;
+        if (p->ax.nst[2] == 2 && Q3 >= 1 && NA3 > 0)
+            for (int r = 0; r < R0; ++r) {
+                const int lo = r * NA3, hi = r * NA3 + NA3 - 1;
+                if (hi <= Q3 || lo >= n3 - Q3 || lo <= Q3 || hi >= n3 - Q3) groups.push_back(r);
+            }
+        bool band = !groups.empty() && !(flags & VLOC_GAMMA);
+        for (int64_t q = 0; band && q < npw; ++q) band = pw_z[q] <= Q3 || pw_z[q] >= n3 - Q3;
+        if (band) {
+            std::vector<int> slot_of_row(n3, -1);
+            for (size_t j = 0; j < groups.size(); ++j)
+                for (int i = 0; i < NA3; ++i) slot_of_row[i + groups[j] * NA3] = (int)(j * NA3 + i);
+            zd_rows = (int)groups.size() * NA3;
+            zdense.assign((size_t)T * zd_rows * kLinesPerTile, -1);
+            for (int tt = 0; tt < T; ++tt)
+                for (int e = tile_pw_ptr[tt]; e < tile_pw_ptr[tt + 1]; ++e) {
+                    const int f = tile_pw[2 * e], zl = tile_pw[2 * e + 1];
+                    const int z = zl & 0xffff, line = zl >> 16;
+                    zdense[((size_t)tt * zd_rows + slot_of_row[z]) * kLinesPerTile + line] = f;
+                }
+        }
+    }
+
     // ---- Gamma-point table for the z-passes that form and separate the
     // real band pairs themselves (used when every G and its -G share a tile):
     // per tile, {h, position of G, position of -G, 0} (position = z | line
@@ -497,6 +531,9 @@ int vloc_plan_create(vloc_plan* out, int n1, int n2, int n3, const int32_t* g, i
         L.gok = gamma_ok ? 1 : 0;
         L.nh = (flags & VLOC_GAMMA) ? npw_user : 0;
         L.o_ghp = append(gamma_h_ptr);
+        L.zd_rows = zd_rows;
+        while (blob.size() & 3) blob.push_back(0);  // 16-byte alignment
+        L.o_zd = append(zdense);
         while (blob.size() & 3) blob.push_back(0);  // int4 alignment
         L.o_gh = append(gamma_h);
         L.total = blob.size();
@@ -1347,6 +1384,8 @@ DevTables vloc::device_tables(const int* base, const HostTableLayout& L, int n1,
     t.xq = L.xq;
     t.zq = L.zq;
     t.gok = L.gok;
+    t.zd_rows = L.zd_rows;
+    t.zdense = base + L.o_zd;
     t.npw_half = L.nh;
     t.gamma_h_ptr = base + L.o_ghp;
     t.gamma_h = reinterpret_cast<const int4*>(base + L.o_gh);
