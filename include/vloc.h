@@ -281,6 +281,21 @@ int vloc_apply_batched(int ninst, const vloc_plan* plans, const void* const* coe
 int vloc_apply_host(vloc_plan plan, const void* coeffs_host, const void* V_host, int64_t nbands,
                     void* out_host, void* stream);
 
+/*
+ * vloc_apply_host_async -- vloc_apply_host without the synchronisation: the
+ * copies and the applies are enqueued and the call returns; `stream` is made
+ * to wait for the last copy out, so the results are in out_host once the
+ * caller's stream has reached that point (synchronise it before reading
+ * them).  coeffs_host, V_host and out_host must stay untouched until then.
+ * Consecutive calls on one plan overlap one call's last copies with the
+ * next call's first (the staging slots' state carries over), which is how a
+ * stream of band blocks keeps the host link busy.  Pinned host memory is
+ * required for the copies to be asynchronous.  Same errors as
+ * vloc_apply_host.
+ */
+int vloc_apply_host_async(vloc_plan plan, const void* coeffs_host, const void* V_host, int64_t nbands,
+                          void* out_host, void* stream);
+
 /* vloc_get_index_map -- grid_index[p] = ((h mod n1) n2 + (k mod n2)) n3 +
  * (l mod n3) for every G of the plan's list (host array of npw int64).
  * Eqs. 2-3. */

@@ -174,6 +174,8 @@ struct vloc_plan_s {
     cudaStream_t copy_stream = nullptr;  // host-to-device copies
     cudaStream_t d2h_stream = nullptr;   // device-to-host copies
     cudaEvent_t ev[12] = {};  // host-buffer staging: 3 events per staging slot
+    bool stage_used[4] = {};  // slot s has recorded its computed / copied-out events
+    int stage_next = 0;       // slot of the next chunk (kept across calls)
     int device = 0;
     int smem_optin = 0;
     std::mutex mu;
@@ -1198,7 +1200,12 @@ int vloc_apply_batched(int ninst, const vloc_plan* plans, const void* const* c, 
     return graph_run(plans[0], ps, std::move(key), (cudaStream_t)stream, branched);
 }
 
-int vloc_apply_host(vloc_plan p, const void* ch, const void* Vh, int64_t nb, void* oh, void* stream) {
+// Host-buffer apply; `blocking`: synchronise before return, otherwise leave
+// the caller's stream waiting for the last copy out, with the staging slots'
+// state kept for the next call (consecutive calls then overlap one call's
+// last copies with the next call's first ones).
+static int apply_host_impl(vloc_plan p, const void* ch, const void* Vh, int64_t nb, void* oh, void* stream,
+                           bool blocking) {
     if (!p || nb < 0) return VLOC_ERR_ARG;
     if ((p->flags & VLOC_HOST_ONLY) || p->gamma) return VLOC_ERR_STATE;
     if (nb == 0) return VLOC_OK;
@@ -1222,6 +1229,8 @@ int vloc_apply_host(vloc_plan p, const void* ch, const void* Vh, int64_t nb, voi
         p->stage_bytes = 0;
         if ((e = cudaMalloc(&p->d_stage, need))) return cuda_fail(e, "cudaMalloc(staging)");
         p->stage_bytes = need;
+        for (bool& u : p->stage_used) u = false;  // fresh slots (cudaFree waited for the old ones)
+        p->stage_next = 0;
         if (!p->copy_stream && (e = cudaStreamCreateWithFlags(&p->copy_stream, cudaStreamNonBlocking)))
             return cuda_fail(e, "copy stream");
         if (!p->d2h_stream && (e = cudaStreamCreateWithFlags(&p->d2h_stream, cudaStreamNonBlocking)))
@@ -1264,14 +1273,15 @@ int vloc_apply_host(vloc_plan p, const void* ch, const void* Vh, int64_t nb, voi
     const int64_t nchunks = (int64_t)sizes.size();
     int64_t b0 = 0;
     for (int64_t i = 0; i < nchunks; b0 += sizes[i], ++i) {
-        const int s = (int)(i % K);
+        const int s = (int)((p->stage_next + i) % K);
         const long long cb = sizes[i];
-        if (i >= K && (e = cudaStreamWaitEvent(p->copy_stream, p->ev[K + s], 0))) return cuda_fail(e, "wait");
+        const bool used = p->stage_used[s];  // an earlier chunk (of this or an earlier call) used the slot
+        if (used && (e = cudaStreamWaitEvent(p->copy_stream, p->ev[K + s], 0))) return cuda_fail(e, "wait");
         if ((e = cudaMemcpyAsync(slot_in[s], (const char*)ch + b0 * bstride, cb * bstride, cudaMemcpyHostToDevice, p->copy_stream)))
             return cuda_fail(e, "H2D coeffs");
         if ((e = cudaEventRecord(p->ev[s], p->copy_stream))) return cuda_fail(e, "record");
         if ((e = cudaStreamWaitEvent(st, p->ev[s], 0))) return cuda_fail(e, "wait");
-        if (i >= K && (e = cudaStreamWaitEvent(st, p->ev[2 * K + s], 0))) return cuda_fail(e, "wait");
+        if (used && (e = cudaStreamWaitEvent(st, p->ev[2 * K + s], 0))) return cuda_fail(e, "wait");
         int rc = apply_impl(p, slot_in[s], dV, cb, slot_out[s], st);
         if (rc) return rc;
         if ((e = cudaEventRecord(p->ev[K + s], st))) return cuda_fail(e, "record");
@@ -1279,11 +1289,27 @@ int vloc_apply_host(vloc_plan p, const void* ch, const void* Vh, int64_t nb, voi
         if ((e = cudaMemcpyAsync((char*)oh + b0 * bstride, slot_out[s], cb * bstride, cudaMemcpyDeviceToHost, p->d2h_stream)))
             return cuda_fail(e, "D2H out");
         if ((e = cudaEventRecord(p->ev[2 * K + s], p->d2h_stream))) return cuda_fail(e, "record");
+        p->stage_used[s] = true;
+    }
+    p->stage_next = (int)((p->stage_next + nchunks) % K);
+    if (!blocking) {
+        // the caller's stream reaches this point once every result is in host memory
+        const int last = (int)((p->stage_next + K - 1) % K);
+        if ((e = cudaStreamWaitEvent(st, p->ev[2 * K + last], 0))) return cuda_fail(e, "wait copy out");
+        return VLOC_OK;
     }
     if ((e = cudaStreamSynchronize(p->d2h_stream))) return cuda_fail(e, "sync copy");
     if ((e = cudaStreamSynchronize(p->copy_stream))) return cuda_fail(e, "sync copy");
     if ((e = cudaStreamSynchronize(st))) return cuda_fail(e, "sync");
     return VLOC_OK;
+}
+
+int vloc_apply_host(vloc_plan p, const void* ch, const void* Vh, int64_t nb, void* oh, void* stream) {
+    return apply_host_impl(p, ch, Vh, nb, oh, stream, true);
+}
+
+int vloc_apply_host_async(vloc_plan p, const void* ch, const void* Vh, int64_t nb, void* oh, void* stream) {
+    return apply_host_impl(p, ch, Vh, nb, oh, stream, false);
 }
 
 int vloc_device_status(vloc_plan p) {

@@ -46,7 +46,7 @@ EXPORTS = [
     "vloc_get_info", "vloc_strerror", "vloc_version", "vloc_last_cuda_error",
     "vloc_profile", "vloc_get_profile", "vloc_get_launch_count", "vloc_apply_noalloc",
     "vloc_plan_set_schedule", "vloc_to_real", "vloc_to_recip", "vloc_density",
-    "vloc_apply_h", "vloc_device_status", "vloc_alu_peak",
+    "vloc_apply_h", "vloc_device_status", "vloc_alu_peak", "vloc_apply_host_async",
 ]
 
 KERNEL_NAMES = ["k1_scatter_zpass", "k2_ypass_inv", "k3_xpass_v", "k2_ypass_fwd", "k4_zpass_gather",
@@ -96,7 +96,8 @@ def load(path: str | None = None) -> ctypes.CDLL:
         vp, i64, i32, c_int = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_int
         lib.vloc_plan_create.argtypes = [ctypes.POINTER(vp), c_int, c_int, c_int, ctypes.POINTER(i32), i64, c_int, i64, vp]
         lib.vloc_plan_destroy.argtypes = [vp]
-        for f in (lib.vloc_apply, lib.vloc_apply_adjoint, lib.vloc_apply_host, lib.vloc_apply_noalloc):
+        for f in (lib.vloc_apply, lib.vloc_apply_adjoint, lib.vloc_apply_host, lib.vloc_apply_noalloc,
+                  lib.vloc_apply_host_async):
             f.argtypes = [vp, vp, vp, i64, vp, vp]
         lib.vloc_backward.argtypes = [vp, vp, vp, vp, i64, vp, vp, vp]
         lib.vloc_apply_batched.argtypes = [c_int, ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(vp),
@@ -408,8 +409,11 @@ class VlocPlan:
                                      _stream_ptr(stream)), "vloc_density")
         return rho
 
-    def apply_host(self, c_host, V_host, out_host=None, *, stream=None):
-        """A c with host (CPU, preferably pinned) tensors; copies inside the call."""
+    def apply_host(self, c_host, V_host, out_host=None, *, stream=None, blocking: bool = True):
+        """A c with host (CPU, preferably pinned) tensors; copies inside the call.
+        ``blocking=False`` enqueues the copies and applies and returns at
+        once: ``out_host`` holds the result after ``stream`` is synchronised,
+        and the host tensors must stay untouched until then."""
         import torch
         if c_host.is_cuda or V_host.is_cuda:
             raise ValueError("apply_host takes CPU tensors")
@@ -423,8 +427,9 @@ class VlocPlan:
                 out_host.numel() != c_host.numel():
             raise ValueError("out_host must be a contiguous host tensor shaped like the coefficients")
         nb = c_host.numel() // self.npw
-        _check(self.lib.vloc_apply_host(self.handle, _ptr(c_host), _ptr(V_host), nb, _ptr(out_host),
-                                        _stream_ptr(stream)), "vloc_apply_host")
+        fn = self.lib.vloc_apply_host if blocking else self.lib.vloc_apply_host_async
+        _check(fn(self.handle, _ptr(c_host), _ptr(V_host), nb, _ptr(out_host), _stream_ptr(stream)),
+               "vloc_apply_host")
         return out_host
 
 

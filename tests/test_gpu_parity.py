@@ -191,6 +191,26 @@ def test_host_buffer_entry_matches_device_entry(prec):
     assert torch.equal(oh, out.cpu())
 
 
+@pytest.mark.parametrize("n,R,nb,chunk", [((32, 36, 40), 8, 13, 4), ((96, 96, 96), 24, 600, 0)])
+def test_async_host_buffer_calls_overlap_and_match(n, R, nb, chunk):
+    # consecutive asynchronous host-buffer calls on one plan (the staging
+    # slots' state carries from call to call): three calls into three
+    # outputs, one synchronisation, each equal to the device entry's result
+    g, c, V = make_case(n, R, nb, seed=13, prec="f32")
+    plan, ct, Vt, out = run(n, g, c, V, "f32", chunk=chunk)
+    Vh = Vt.cpu().pin_memory()
+    chs = [(ct * s).cpu().pin_memory() for s in (1.0, 2.0, 0.5)]
+    ohs = [torch.empty_like(h).pin_memory() for h in chs]
+    for h, o in zip(chs, ohs):
+        plan.apply_host(h, Vh, o, blocking=False)
+    torch.cuda.current_stream().synchronize()
+    for s, o in zip((1.0, 2.0, 0.5), ohs):
+        want = plan.apply(ct * s, Vt).cpu()
+        assert torch.equal(o, want)
+    # a blocking call after asynchronous ones
+    assert torch.equal(plan.apply_host(chs[0], Vh), out.cpu())
+
+
 def test_batched_matches_individual():
     cases = []
     for i, m in enumerate([16, 24, 30]):
