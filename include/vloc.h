@@ -92,6 +92,12 @@ extern "C" {
                                        /* the default x-pass at 96^3, kept opt-in.   */
                                        /* Its waits are bounded: see                 */
                                        /* vloc_device_status.                        */
+#define VLOC_Z_WARP             0x20000 /* FP32, n3 = 32, 64, 96 or 128, not Gamma: */
+                                       /* z-passes as warp-register transforms (one */
+                                       /* warp per stick pair, 32-point DFTs across */
+                                       /* the lanes by warp shuffles; info.path bit */
+                                       /* 8).  Measured slower than the tile z-      */
+                                       /* passes on GB300, kept opt-in.             */
 #define VLOC_POISON_WORKSPACE   0x10000 /* test aid: fill the plan's cylinder and   */
                                        /* slab workspace with NaN bytes before every */
                                        /* workspace chunk, so a pass that reads a    */
@@ -126,7 +132,9 @@ typedef struct vloc_info {
                                  /* bit 6: every |l| <= n3/4, and the z-pass       */
                                  /* kernels skip the rows outside that band;      */
                                  /* bit 7: Gamma-point pairs are formed and       */
-                                 /* separated inside the z-passes (no pack pass)  */
+                                 /* separated inside the z-passes (no pack pass); */
+                                 /* bit 8: the z-passes run as warp-register      */
+                                 /* transforms (VLOC_Z_WARP)                      */
 } vloc_info;
 
 /*

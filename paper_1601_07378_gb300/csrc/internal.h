@@ -43,6 +43,11 @@ struct DevTables {
     // groups that meet the band |l| <= n3/4, or -1
     int zd_rows;
     const int* zdense;
+    // class table of plain plans with n3 = 32 C, C <= 4 (zs = 1): [S][n3],
+    // entry [s][32 j + m] the caller index of the plane wave of stick s at
+    // z = C m + j, or -1 (the warp-register z-passes of kernels_zs.cuh)
+    int zs;
+    const int* zsh;
     int gok;
     long long npw_half;  // half-list plane waves per real band (Gamma plans)
     const int* gamma_h_ptr;
@@ -212,8 +217,9 @@ struct HostTableLayout {
     int xq;  // DevTables::xq
     int zq;  // DevTables::zq
     int gok;  // DevTables::gok
-    size_t o_ghp, o_gh, o_zd;
+    size_t o_ghp, o_gh, o_zd, o_zs;
     int zd_rows;
+    int zs;  // DevTables::zs
     long long nh;  // DevTables::npw_half
 };
 

@@ -14,6 +14,7 @@
 
 #include "fft_ct.cuh"
 #include "kernels_impl.cuh"
+#include "kernels_zs.cuh"
 
 // Minimum resident CTAs per SM asked of the compiler (caps a kernel's
 // registers at 65536 / (128 x MINB)).  Measured on GB300 at 96^3: the z- and
@@ -1358,6 +1359,13 @@ template <int N> struct CtSmem {
 template <int N, bool GM>
 int launch_k1_ct(const DevTables& t, const void* tw3, const void* coeffs, long long nb, void* cyl, const GammaArgs& g,
                  cudaStream_t st) {
+    if constexpr (zs_length<N>()) {
+        if (!GM && t.zs) {  // VLOC_Z_WARP plans
+            k1s_ct<N><<<dim3(zs_blocks(t.S), (unsigned)nb), kZsThreads, 0, st>>>(t, (const float2*)tw3,
+                                                                                (const float2*)coeffs, (float2*)cyl);
+            return (int)cudaGetLastError();
+        }
+    }
     if constexpr (Sched<N>::nst == 2) {
         // the dense table exists for plain plans only (its entries are caller
         // indices of the complex band the kernel reads)
@@ -1502,6 +1510,13 @@ template <int N, bool GM>
 int launch_k4_ct(const DevTables& t, const void* tw3, const void* cyl, long long nb, void* out, const void* diag,
                  const void* cin, const GammaArgs& g, cudaStream_t st) {
     const float scale = (float)(1.0 / ((double)t.n1 * t.n2 * t.n3));
+    if constexpr (zs_length<N>()) {
+        if (!GM && t.zs) {  // VLOC_Z_WARP plans
+            k4s_ct<N><<<dim3(zs_blocks(t.S), (unsigned)nb), kZsThreads, 0, st>>>(
+                t, (const float2*)tw3, (const float2*)cyl, (float2*)out, scale, (const float*)diag, (const float2*)cin);
+            return (int)cudaGetLastError();
+        }
+    }
     if constexpr (Sched<N>::nst == 2) {
         if (!GM && VLOC_K4_DIRECT && t.zd_rows == QRows<N>::groups() * QRows<N>::NA) {
             static const cudaError_t onced = CtSmem<N>::ensure(k4d_ct<N>);

@@ -257,7 +257,7 @@ int vloc_plan_create(vloc_plan* out, int n1, int n2, int n3, const int32_t* g, i
     if (part_flag != VLOC_PARTITION_GREEDY && part_flag != VLOC_PARTITION_BASIC && part_flag != VLOC_PARTITION_IMPROVED)
         return VLOC_ERR_ARG;
     if (flags & ~(0x003 | 0x0F0 | VLOC_GRAPH | VLOC_HOST_ONLY | VLOC_GENERIC_KERNELS | VLOC_GAMMA | VLOC_DOUBLE_FLOAT |
-                  VLOC_X_TMA | VLOC_POISON_WORKSPACE))
+                  VLOC_X_TMA | VLOC_POISON_WORKSPACE | VLOC_Z_WARP))
         return VLOC_ERR_ARG;
     if ((flags & VLOC_DOUBLE_FLOAT) && prec != VLOC_F64) return VLOC_ERR_ARG;
     const bool host_only = (flags & VLOC_HOST_ONLY) != 0;
@@ -489,6 +489,22 @@ int vloc_plan_create(vloc_plan* out, int n1, int n2, int n3, const int32_t* g, i
         }
     }
 
+    // ---- class table for the warp-register z-passes (VLOC_Z_WARP; plain
+    // FP32 plans, n3 = 32 C with C <= 4): per stick, the caller index of the
+    // plane wave at z = C m + j in entry 32 j + m, or -1
+    std::vector<int> zsh;
+    int zs_ok = 0;
+    if ((flags & VLOC_Z_WARP) && !(flags & VLOC_GAMMA) && !dbl && n3 % 32 == 0 && n3 / 32 >= 1 && n3 / 32 <= 4) {
+        const int C = n3 / 32;
+        zsh.assign((size_t)S * n3, -1);
+        for (int s = 0; s < S; ++s)
+            for (int q = stick_pw_ptr[s]; q < stick_pw_ptr[s + 1]; ++q) {
+                const int z = pw_z[q];
+                zsh[(size_t)s * n3 + 32 * (z % C) + z / C] = pw_user[q];
+            }
+        zs_ok = 1;
+    }
+
     // ---- Gamma-point table for the z-passes that form and separate the
     // real band pairs themselves (used when every G and its -G share a tile):
     // per tile, {h, position of G, position of -G, 0} (position = z | line
@@ -536,6 +552,8 @@ int vloc_plan_create(vloc_plan* out, int n1, int n2, int n3, const int32_t* g, i
         L.zd_rows = zd_rows;
         while (blob.size() & 3) blob.push_back(0);  // 16-byte alignment
         L.o_zd = append(zdense);
+        L.zs = zs_ok;
+        L.o_zs = append(zsh);
         while (blob.size() & 3) blob.push_back(0);  // int4 alignment
         L.o_gh = append(gamma_h);
         L.total = blob.size();
@@ -1374,7 +1392,8 @@ int vloc_get_info(vloc_plan p, vloc_info* info) {
     info->nsticks = p->S; info->nplanes = p->NP; info->nparts = p->P;
     info->lines_per_tile = kLinesPerTile;
     info->path = (p->fast ? 1 : 0) | (p->gamma ? 4 : 0) | (p->df ? 8 : 0) | (p->k3tma_on ? 16 : 0) |
-                 (p->lay.xq ? 32 : 0) | (p->lay.zq ? 64 : 0) | (p->gfused ? 128 : 0);
+                 (p->lay.xq ? 32 : 0) | (p->lay.zq ? 64 : 0) | (p->gfused ? 128 : 0) |
+                 (p->lay.zs && p->fast ? 256 : 0);
     info->chunk_bands = p->chunk;
     info->workspace_bytes = (int64_t)p->ws_bytes;
     for (int a = 0; a < 3; ++a) {
@@ -1412,6 +1431,8 @@ DevTables vloc::device_tables(const int* base, const HostTableLayout& L, int n1,
     t.gok = L.gok;
     t.zd_rows = L.zd_rows;
     t.zdense = base + L.o_zd;
+    t.zs = L.zs;
+    t.zsh = base + L.o_zs;
     t.npw_half = L.nh;
     t.gamma_h_ptr = base + L.o_ghp;
     t.gamma_h = reinterpret_cast<const int4*>(base + L.o_gh);

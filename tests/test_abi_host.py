@@ -211,6 +211,25 @@ def test_quarter_sphere_plane_set_is_detected(lib):
         assert not vloc.VlocPlan(n, other, torch.complex64, host_only=True).info()["x_quarter"]
 
 
+def test_warp_z_pass_selection(lib):
+    # VLOC_Z_WARP plans in FP32 with n3 = 32 C (C = 1..4) run the z-passes as
+    # warp-register transforms (info bit 8); without the flag, for Gamma-point
+    # and FP64 plans and for other lengths the tile z-passes run
+    import torch
+    for n3 in (32, 64, 96, 128):
+        n = (20, 18, n3)
+        g = synth.sphere_glist(*n, 7, order="shuffled", seed=3)
+        assert vloc.VlocPlan(n, g, torch.complex64, host_only=True, z_warp=True).info()["z_warp"]
+        assert not vloc.VlocPlan(n, g, torch.complex64, host_only=True).info()["z_warp"]
+        assert not vloc.VlocPlan(n, g, torch.complex128, host_only=True, z_warp=True).info()["z_warp"]
+        gh = synth.half_sphere(synth.sphere_glist(*n, 7))
+        assert not vloc.VlocPlan(n, gh, torch.complex64, host_only=True, gamma=True, z_warp=True).info()["z_warp"]
+    for n3 in (24, 48, 100, 120, 144):
+        n = (20, 18, n3)
+        g = synth.sphere_glist(*n, 7)
+        assert not vloc.VlocPlan(n, g, torch.complex64, host_only=True, z_warp=True).info()["z_warp"]
+
+
 @pytest.mark.parametrize("n,R", [((16, 18, 20), 4.5), ((96, 96, 96), 24), ((30, 45, 27), 7)])
 def test_gamma_partition_deals_mirror_pairs(lib, n, R):
     # Gamma-point plans deal a stick (h, k) and its mirror (-h, -k) to the
