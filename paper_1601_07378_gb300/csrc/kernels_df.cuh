@@ -145,8 +145,8 @@ __global__ void __launch_bounds__(kThreads) k1_w(DevTables t, const typename Pol
 
 // ------------------------------------------------------------------ K2
 template <class Pol, int S, int N>
-__global__ void __launch_bounds__(kThreads) k2_w(DevTables t, const typename Pol::TW* __restrict__ tw2,
-                                                typename Pol::V* cyl, typename Pol::V* slab) {
+__device__ __forceinline__ void k2w_body(const DevTables& t, const typename Pol::TW* __restrict__ tw2,
+                                         typename Pol::V* cyl, typename Pol::V* slab) {
     using V = typename Pol::V;
     using TW = typename Pol::TW;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -172,6 +172,20 @@ __global__ void __launch_bounds__(kThreads) k2_w(DevTables t, const typename Pol
     else
         fft_ct<N, -1, kWarps, false, false, false, V, TW>(stw, sr, cr, buf, slot_of_df(), sub_of_df(), warp_of_df(),
                                                              act);
+}
+template <class Pol, int S, int N>
+__global__ void __launch_bounds__(kThreads) k2_w(DevTables t, const typename Pol::TW* __restrict__ tw2,
+                                                typename Pol::V* cyl, typename Pol::V* slab) {
+    k2w_body<Pol, S, N>(t, tw2, cyl, slab);
+}
+// The same with five resident CTAs per SM asked of the compiler (at most 96
+// registers a thread), for the double-float inverse y-pass up to length 96:
+// left to itself the compiler gives it 103 registers and four CTAs per SM,
+// measured 3.74 against 2.63 ms per 1024 bands at 96^3.
+template <class Pol, int S, int N>
+__global__ void __launch_bounds__(kThreads, 5) k2_wb(DevTables t, const typename Pol::TW* __restrict__ tw2,
+                                                    typename Pol::V* cyl, typename Pol::V* slab) {
+    k2w_body<Pol, S, N>(t, tw2, cyl, slab);
 }
 
 // ------------------------------------------------------------------ K3
@@ -428,9 +442,17 @@ int LaunchF64<P, N>::k2(int sign, const DevTables& t, const void* tw2, long long
     using V = typename Pol::V;
     const dim3 grid(t.NP, (t.n3 + kLinesDF - 1) / kLinesDF, (unsigned)nb);
     if (sign > 0) {
-        static const cudaError_t once = WSmem<Pol, N>::ensure(k2_w<Pol, +1, N>);
-        if (once) return (int)once;
-        k2_w<Pol, +1, N><<<grid, kThreads, WSmem<Pol, N>::sm, st>>>(t, (const typename Pol::TW*)tw2, (V*)cyl, (V*)slab);
+        if constexpr (std::is_same<Pol, PolDF>::value && N <= 96) {
+            static const cudaError_t onceb = WSmem<Pol, N>::ensure(k2_wb<Pol, +1, N>);
+            if (onceb) return (int)onceb;
+            k2_wb<Pol, +1, N><<<grid, kThreads, WSmem<Pol, N>::sm, st>>>(t, (const typename Pol::TW*)tw2, (V*)cyl,
+                                                                         (V*)slab);
+        } else {
+            static const cudaError_t once = WSmem<Pol, N>::ensure(k2_w<Pol, +1, N>);
+            if (once) return (int)once;
+            k2_w<Pol, +1, N><<<grid, kThreads, WSmem<Pol, N>::sm, st>>>(t, (const typename Pol::TW*)tw2, (V*)cyl,
+                                                                        (V*)slab);
+        }
     } else {
         static const cudaError_t once = WSmem<Pol, N>::ensure(k2_w<Pol, -1, N>);
         if (once) return (int)once;
