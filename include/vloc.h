@@ -98,6 +98,14 @@ extern "C" {
                                        /* the lanes by warp shuffles; info.path bit */
                                        /* 8).  Measured slower than the tile z-      */
                                        /* passes on GB300, kept opt-in.             */
+#define VLOC_Z_BULK             0x40000 /* FP32, every |l| <= n3/4, each stick's    */
+                                       /* plane waves consecutive in the caller's   */
+                                       /* list with l ascending: the inverse z-pass */
+                                       /* stages each stick's coefficients by one   */
+                                       /* 1-D bulk copy on an mbarrier (info.path   */
+                                       /* bit 9).  Measured slower than the direct  */
+                                       /* loads on GB300, kept opt-in.  Its wait is */
+                                       /* bounded: see vloc_device_status.          */
 #define VLOC_POISON_WORKSPACE   0x10000 /* test aid: fill the plan's cylinder and   */
                                        /* slab workspace with NaN bytes before every */
                                        /* workspace chunk, so a pass that reads a    */
@@ -134,7 +142,9 @@ typedef struct vloc_info {
                                  /* bit 7: Gamma-point pairs are formed and       */
                                  /* separated inside the z-passes (no pack pass); */
                                  /* bit 8: the z-passes run as warp-register      */
-                                 /* transforms (VLOC_Z_WARP)                      */
+                                 /* transforms (VLOC_Z_WARP);                     */
+                                 /* bit 9: the inverse z-pass stages each stick's */
+                                 /* coefficients by one bulk copy (VLOC_Z_BULK)   */
 } vloc_info;
 
 /*

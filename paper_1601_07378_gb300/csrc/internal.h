@@ -48,6 +48,12 @@ struct DevTables {
     // z = C m + j, or -1 (the warp-register z-passes of kernels_zs.cuh)
     int zs;
     const int* zsh;
+    // stick runs of plain quarter-band plans whose every stick's plane waves
+    // are consecutive in the caller's list, l ascending (runs = 1): per tile
+    // line [T][32] {caller index of the first, its l, count, 0}
+    int runs;
+    const int4* run_tab;
+    int* err;  // the plan's device error flag (set by a bounded wait that ran out), or null
     int gok;
     long long npw_half;  // half-list plane waves per real band (Gamma plans)
     const int* gamma_h_ptr;
@@ -217,9 +223,10 @@ struct HostTableLayout {
     int xq;  // DevTables::xq
     int zq;  // DevTables::zq
     int gok;  // DevTables::gok
-    size_t o_ghp, o_gh, o_zd, o_zs;
+    size_t o_ghp, o_gh, o_zd, o_zs, o_rn;
     int zd_rows;
     int zs;  // DevTables::zs
+    int runs;  // DevTables::runs
     long long nh;  // DevTables::npw_half
 };
 

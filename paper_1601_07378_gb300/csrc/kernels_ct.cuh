@@ -15,6 +15,7 @@
 #include "fft_ct.cuh"
 #include "kernels_impl.cuh"
 #include "kernels_zs.cuh"
+#include "bulk_ptx.cuh"
 
 // Minimum resident CTAs per SM asked of the compiler (caps a kernel's
 // registers at 65536 / (128 x MINB)).  Measured on GB300 at 96^3: the z- and
@@ -518,6 +519,121 @@ __global__ void __launch_bounds__(kThreads, minb_k1(N)) k1d_ct(DevTables t, cons
     const int s0 = t.tile_ptr[tile], lines = t.tile_ptr[tile + 1] - s0;
     const bool act = 2 * slot < lines;
     __syncthreads();
+    NatStage<N, +1, W, 1>::template run<true>(stw, sb, sb, slot, sub, warp, act);
+    __syncthreads();
+    rows_out_p<N>(buf, cyl + b * (long long)t.S * N, t.tile_sticks + s0, lines);
+}
+
+// ------------------------------------------------- K1, bulk-staged form
+// For caller lists in stick order (every stick's plane waves consecutive with
+// l ascending and no gap, as the canonical order gives) each stick of the
+// tile is one contiguous run of the band's coefficients.  Lane l of warp 0
+// stages run l in shared memory: one 1-D bulk copy of its 16-byte-aligned
+// interior, completing on the block's mbarrier, and plain loads of the at
+// most two 8-byte end elements.  The threads then take their first-stage
+// inputs (row x = i + r NA of each of their two lines) from the staged runs
+// at position l(x) - lmin.  The staged runs share the tile buffer, so the
+// first stage's results wait in registers for a barrier.  The wait is
+// bounded: a copy that has not landed within about a second sets the error
+// flag, and the block waits (bounded) for its copies and returns.
+#ifndef VLOC_K1_BULK
+#define VLOC_K1_BULK 1
+#endif
+template <int N> constexpr int k1b_run_stride() { return (N / 2 + 3) & ~1; }  // >= count + 1, even
+template <int N> constexpr size_t k1b_smem() { return ct_smem<N>() + 16; }  // + mbarrier and flag
+template <int N>
+__global__ void __launch_bounds__(kThreads, minb_k1(N)) k1b_ct(DevTables t, const float2* __restrict__ tw3,
+                                                  const float2* __restrict__ coeffs, float2* __restrict__ cyl) {
+    using SC = Sched<N>;
+    static_assert(SC::nst == 2, "quarter-band z-pass: two-stage lengths");
+    using QR = QRows<N>;
+    constexpr int R0 = QR::R0, NA = QR::NA, W = kWarps;
+    constexpr int UA = (NA + 2 * W - 1) / (2 * W);
+    constexpr int RS = k1b_run_stride<N>();
+    static_assert(kLines * RS <= N * kLdP, "the staged runs fit in the tile buffer");
+    static_assert(ct_smem<N>() % 8 == 0, "mbarrier alignment");
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float2* buf = reinterpret_cast<float2*>(smem_raw);
+    float2* stw = buf + N * kLdP;
+    unsigned long long* bar = reinterpret_cast<unsigned long long*>(smem_raw + ct_smem<N>());
+    int* okf = reinterpret_cast<int*>(bar + 1);
+    const int tile = blockIdx.x;
+    const long long b = blockIdx.y;
+    const int slot = slot_of(), sub = sub_of(), warp = warp_of();
+    const int s0 = t.tile_ptr[tile], lines = t.tile_ptr[tile + 1] - s0;
+    const float2* c = coeffs + b * t.npw;
+    const int4* rt = t.run_tab + (size_t)tile * kLines;
+    if (threadIdx.x == 0) {
+        mbar_init(bar, 32);
+        mbar_fence_init();
+    }
+    __syncthreads();
+    if (warp == 0) {
+        const int lane = threadIdx.x;
+        unsigned bytes = 0;
+        const float2* src = nullptr;
+        float2* dst = nullptr;
+        if (lane < lines) {
+            const int4 r = rt[lane];
+            const float2* run = c + r.x;
+            const int a = (int)((reinterpret_cast<uintptr_t>(run) >> 3) & 1);  // element 0 off the 16-byte grid
+            const int n2 = (r.z - a) & ~1;                                     // aligned interior, even length
+            float2* st = buf + lane * RS;  // element p at slot p + a
+            if (a) st[1] = run[0];
+            if ((r.z - a) & 1) st[r.z - 1 + a] = run[r.z - 1];
+            if (n2 > 0) {
+                bytes = 8u * (unsigned)n2;
+                src = run + a;
+                dst = st + 2 * a;
+            }
+        }
+        mbar_expect_tx(bar, bytes);  // every lane of warp 0 arrives once
+        if (bytes) bulk_load_1d(dst, src, bytes, bar);
+    }
+    load_tw<float>(stw, tw3, N);
+    if (threadIdx.x == 0) *okf = mbar_wait_bounded(bar, 0) ? 1 : 0;
+    __syncthreads();
+    if (!*okf) {  // the same for every thread of the block
+        if (threadIdx.x == 0) {
+            if (t.err) atomicExch(t.err, 1);
+            mbar_wait_bounded(bar, 0);
+        }
+        return;
+    }
+    const int la = 2 * slot, lb = la + 1;
+    const int4 ra = la < lines ? rt[la] : make_int4(0, 0, 0, 0);
+    const int4 rb = lb < lines ? rt[lb] : make_int4(0, 0, 0, 0);
+    const int aa = (int)((reinterpret_cast<uintptr_t>(c + ra.x) >> 3) & 1);
+    const int ab = (int)((reinterpret_cast<uintptr_t>(c + rb.x) >> 3) & 1);
+    auto staged = [&](const int4& r, int a, int line, int x) {
+        const int p = (x <= N / 2 ? x : x - N) - r.y;
+        return (p >= 0 && p < r.z) ? buf[line * RS + p + a] : make_float2(0.f, 0.f);
+    };
+    SmemP sb{buf};
+    P2f h[UA][R0];
+#pragma unroll
+    for (int u = 0; u < UA; ++u) {
+        const int i = 2 * (warp + u * W) + sub;
+        if (NA % (2 * W) == 0 || i < NA) {
+            sfor<R0>([&](auto rc) {
+                constexpr int r = decltype(rc)::value;
+                if constexpr (QR::kind(r) == 0) h[u][r] = czero<P2f>();
+                else h[u][r] = P2f{staged(ra, aa, la, i + r * NA), staged(rb, ab, lb, i + r * NA)};
+            });
+            DftZ<R0, +1, QR::mask()>::run(h[u]);
+        }
+    }
+    __syncthreads();  // every staged run has been read
+#pragma unroll
+    for (int u = 0; u < UA; ++u) {
+        const int i = 2 * (warp + u * W) + sub;
+        if (NA % (2 * W) == 0 || i < NA) {
+#pragma unroll
+            for (int r = 0; r < R0; ++r) sb(i * R0 + r, slot, h[u][r]);
+        }
+    }
+    __syncthreads();
+    const bool act = 2 * slot < lines;
     NatStage<N, +1, W, 1>::template run<true>(stw, sb, sb, slot, sub, warp, act);
     __syncthreads();
     rows_out_p<N>(buf, cyl + b * (long long)t.S * N, t.tile_sticks + s0, lines);
@@ -1367,6 +1483,15 @@ int launch_k1_ct(const DevTables& t, const void* tw3, const void* coeffs, long l
         }
     }
     if constexpr (Sched<N>::nst == 2) {
+        if (!GM && VLOC_K1_BULK && t.runs && t.zd_rows == QRows<N>::groups() * QRows<N>::NA) {
+            constexpr size_t sm = k1b_smem<N>();
+            static const cudaError_t onceb =
+                sm <= 48 * 1024 ? cudaSuccess : cudaFuncSetAttribute(k1b_ct<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+            if (onceb) return (int)onceb;
+            k1b_ct<N><<<dim3(t.T, (unsigned)nb), kThreads, sm, st>>>(t, (const float2*)tw3, (const float2*)coeffs,
+                                                                    (float2*)cyl);
+            return (int)cudaGetLastError();
+        }
         // the dense table exists for plain plans only (its entries are caller
         // indices of the complex band the kernel reads)
         if (!GM && VLOC_K1_DIRECT && t.zd_rows == QRows<N>::groups() * QRows<N>::NA) {

@@ -178,12 +178,16 @@ __global__ void __launch_bounds__(kThreads) k2_w(DevTables t, const typename Pol
                                                 typename Pol::V* cyl, typename Pol::V* slab) {
     k2w_body<Pol, S, N>(t, tw2, cyl, slab);
 }
-// The same with five resident CTAs per SM asked of the compiler (at most 96
-// registers a thread), for the double-float inverse y-pass up to length 96:
-// left to itself the compiler gives it 103 registers and four CTAs per SM,
-// measured 3.74 against 2.63 ms per 1024 bands at 96^3.
+#ifndef VLOC_MINB_K2DF
+#define VLOC_MINB_K2DF 6
+#endif
+// The same with six resident CTAs per SM asked of the compiler (at most 80
+// registers a thread, no spills), for the double-float inverse y-pass up to
+// length 96: left to itself the compiler gives it 103 registers and four
+// CTAs per SM.  Measured at 96^3, ms per 1024 bands: 3.74 unbounded, 3.44
+// with a floor of 4 CTAs, 3.27 with 5, 2.51 with 6.
 template <class Pol, int S, int N>
-__global__ void __launch_bounds__(kThreads, 5) k2_wb(DevTables t, const typename Pol::TW* __restrict__ tw2,
+__global__ void __launch_bounds__(kThreads, VLOC_MINB_K2DF) k2_wb(DevTables t, const typename Pol::TW* __restrict__ tw2,
                                                     typename Pol::V* cyl, typename Pol::V* slab) {
     k2w_body<Pol, S, N>(t, tw2, cyl, slab);
 }

@@ -257,7 +257,7 @@ int vloc_plan_create(vloc_plan* out, int n1, int n2, int n3, const int32_t* g, i
     if (part_flag != VLOC_PARTITION_GREEDY && part_flag != VLOC_PARTITION_BASIC && part_flag != VLOC_PARTITION_IMPROVED)
         return VLOC_ERR_ARG;
     if (flags & ~(0x003 | 0x0F0 | VLOC_GRAPH | VLOC_HOST_ONLY | VLOC_GENERIC_KERNELS | VLOC_GAMMA | VLOC_DOUBLE_FLOAT |
-                  VLOC_X_TMA | VLOC_POISON_WORKSPACE | VLOC_Z_WARP))
+                  VLOC_X_TMA | VLOC_POISON_WORKSPACE | VLOC_Z_WARP | VLOC_Z_BULK))
         return VLOC_ERR_ARG;
     if ((flags & VLOC_DOUBLE_FLOAT) && prec != VLOC_F64) return VLOC_ERR_ARG;
     const bool host_only = (flags & VLOC_HOST_ONLY) != 0;
@@ -505,6 +505,33 @@ int vloc_plan_create(vloc_plan* out, int n1, int n2, int n3, const int32_t* g, i
         zs_ok = 1;
     }
 
+    // ---- stick runs for the bulk-staged z-pass (VLOC_Z_BULK): plain
+    // quarter-band plans (the dense table exists) whose every stick holds
+    // consecutive caller indices in l order with no gap in l (the canonical
+    // order); per tile line {first caller index, its l, count, 0}
+    std::vector<int> run_tab;
+    int runs_ok = 0;
+    if ((flags & VLOC_Z_BULK) && !(flags & VLOC_Z_WARP) && !dbl && zd_rows > 0) {
+        bool ok = true;
+        std::vector<int> first(S), lmin(S), cnt(S);
+        for (int s = 0; ok && s < S; ++s) {
+            const int q0 = stick_pw_ptr[s], q1 = stick_pw_ptr[s + 1];
+            auto lsig = [&](int q) { return pw_z[q] <= n3 / 2 ? pw_z[q] : pw_z[q] - n3; };
+            first[s] = pw_user[q0]; lmin[s] = lsig(q0); cnt[s] = q1 - q0;
+            for (int q = q0 + 1; ok && q < q1; ++q) ok = pw_user[q] == pw_user[q - 1] + 1 && lsig(q) == lsig(q - 1) + 1;
+        }
+        if (ok) {
+            run_tab.assign((size_t)T * kLinesPerTile * 4, 0);
+            for (int tt = 0; tt < T; ++tt)
+                for (int i = tile_ptr[tt]; i < tile_ptr[tt + 1]; ++i) {
+                    const int s = tile_sticks[i];
+                    int* e = &run_tab[((size_t)tt * kLinesPerTile + (i - tile_ptr[tt])) * 4];
+                    e[0] = first[s]; e[1] = lmin[s]; e[2] = cnt[s];
+                }
+            runs_ok = 1;
+        }
+    }
+
     // ---- Gamma-point table for the z-passes that form and separate the
     // real band pairs themselves (used when every G and its -G share a tile):
     // per tile, {h, position of G, position of -G, 0} (position = z | line
@@ -554,6 +581,9 @@ int vloc_plan_create(vloc_plan* out, int n1, int n2, int n3, const int32_t* g, i
         L.o_zd = append(zdense);
         L.zs = zs_ok;
         L.o_zs = append(zsh);
+        L.runs = runs_ok;
+        while (blob.size() & 3) blob.push_back(0);  // int4 alignment
+        L.o_rn = append(run_tab);
         while (blob.size() & 3) blob.push_back(0);  // int4 alignment
         L.o_gh = append(gamma_h);
         L.total = blob.size();
@@ -618,6 +648,7 @@ int vloc_plan_create(vloc_plan* out, int n1, int n2, int n3, const int32_t* g, i
     if ((e = dmalloc((void**)&p->d_err, sizeof(int)))) { free_plan(p); return cuda_fail(e, "cudaMalloc(error flag)"); }
 
     if ((e = cudaMemsetAsync(p->d_err, 0, sizeof(int), st))) { free_plan(p); return cuda_fail(e, "clear error flag"); }
+    p->dt.err = p->d_err;
     if (p->df) {
         for (int a = 0; a < 3; ++a) {
             if ((e = dmalloc((void**)&p->d_twdf[a], (size_t)ns[a] * 32))) { free_plan(p); return cuda_fail(e, "cudaMalloc(df twiddles)"); }
@@ -1393,7 +1424,7 @@ int vloc_get_info(vloc_plan p, vloc_info* info) {
     info->lines_per_tile = kLinesPerTile;
     info->path = (p->fast ? 1 : 0) | (p->gamma ? 4 : 0) | (p->df ? 8 : 0) | (p->k3tma_on ? 16 : 0) |
                  (p->lay.xq ? 32 : 0) | (p->lay.zq ? 64 : 0) | (p->gfused ? 128 : 0) |
-                 (p->lay.zs && p->fast ? 256 : 0);
+                 (p->lay.zs && p->fast ? 256 : 0) | (p->lay.runs && p->fast ? 512 : 0);
     info->chunk_bands = p->chunk;
     info->workspace_bytes = (int64_t)p->ws_bytes;
     for (int a = 0; a < 3; ++a) {
@@ -1433,6 +1464,9 @@ DevTables vloc::device_tables(const int* base, const HostTableLayout& L, int n1,
     t.zdense = base + L.o_zd;
     t.zs = L.zs;
     t.zsh = base + L.o_zs;
+    t.runs = L.runs;
+    t.run_tab = reinterpret_cast<const int4*>(base + L.o_rn);
+    t.err = nullptr;
     t.npw_half = L.nh;
     t.gamma_h_ptr = base + L.o_ghp;
     t.gamma_h = reinterpret_cast<const int4*>(base + L.o_gh);

@@ -38,6 +38,7 @@ VLOC_GAMMA = 0x1000
 VLOC_DOUBLE_FLOAT = 0x2000
 VLOC_X_TMA = 0x4000
 VLOC_Z_WARP = 0x20000
+VLOC_Z_BULK = 0x40000
 VLOC_POISON_WORKSPACE = 0x10000
 
 # every exported symbol declared in include/vloc.h
@@ -190,7 +191,8 @@ class VlocPlan:
 
     def __init__(self, grid, glist, dtype=None, *, partition: str = "greedy", chunk: int = 0,
                  graph: bool = False, host_only: bool = False, generic: bool = False, gamma: bool = False,
-                 double_float: bool = False, x_tma: bool = False, z_warp: bool = False, poison: bool = False, stream=None):
+                 double_float: bool = False, x_tma: bool = False, z_warp: bool = False, z_bulk: bool = False,
+                 poison: bool = False, stream=None):
         import torch
         dtype = dtype or torch.complex64
         if dtype not in (torch.complex64, torch.complex128):
@@ -220,6 +222,8 @@ class VlocPlan:
             flags |= VLOC_X_TMA
         if z_warp:
             flags |= VLOC_Z_WARP
+        if z_bulk:
+            flags |= VLOC_Z_BULK
         if poison:
             flags |= VLOC_POISON_WORKSPACE
         h = ctypes.c_void_p()
@@ -264,6 +268,7 @@ class VlocPlan:
             "z_quarter": bool(inf.path & 64),
             "gamma_fused": bool(inf.path & 128),
             "z_warp": bool(inf.path & 256),
+            "z_bulk": bool(inf.path & 512),
         }
 
     def set_schedule(self, axis: int, radices):

@@ -230,6 +230,28 @@ def test_warp_z_pass_selection(lib):
         assert not vloc.VlocPlan(n, g, torch.complex64, host_only=True, z_warp=True).info()["z_warp"]
 
 
+def test_bulk_staged_z_pass_selection(lib):
+    # VLOC_Z_BULK: the inverse z-pass stages each stick's coefficients by one
+    # bulk copy (info bit 9) when every |l| <= n3/4 and each stick's plane
+    # waves are consecutive in the caller's list with l ascending (the
+    # canonical order); otherwise, and without the flag, the direct loads run
+    import torch
+    n = (48, 40, 96)
+    g = synth.sphere_glist(*n, 24)
+    plan = lambda gl, dt=torch.complex64, **kw: vloc.VlocPlan(n, gl, dt, host_only=True, **kw).info()["z_bulk"]
+    assert plan(g, z_bulk=True)
+    assert not plan(g)
+    assert not plan(g, torch.complex128, z_bulk=True)
+    assert not plan(synth.sphere_glist(*n, 24, order="shuffled", seed=2), z_bulk=True)
+    # l descending within a stick, or a gap in l, breaks the runs
+    desc = g[np.lexsort((-g[:, 2], g[:, 1] % n[1], g[:, 0] % n[0]))]
+    assert not plan(desc, z_bulk=True)
+    gap = g[~((g[:, 0] == 0) & (g[:, 1] == 0) & (g[:, 2] == 3))]
+    assert not plan(gap, z_bulk=True)
+    # beyond the quarter band the tile scatter runs
+    assert not plan(synth.sphere_glist(*n, 25), z_bulk=True)
+
+
 @pytest.mark.parametrize("n,R", [((16, 18, 20), 4.5), ((96, 96, 96), 24), ((30, 45, 27), 7)])
 def test_gamma_partition_deals_mirror_pairs(lib, n, R):
     # Gamma-point plans deal a stick (h, k) and its mirror (-h, -k) to the
