@@ -109,8 +109,8 @@ template <class V> struct XRowsD {  // x rows at fixed y: the occupied planes
 // ------------------------------------------------------------------ K1
 // CTA (tile, band, half): lines [16 half, 16 half + 16) of the plan tile.
 template <class Pol, int N>
-__global__ void __launch_bounds__(kThreads) k1_w(DevTables t, const typename Pol::TW* __restrict__ tw3,
-                                                const double2* __restrict__ coeffs, typename Pol::V* __restrict__ cyl) {
+__device__ __forceinline__ void k1w_body(const DevTables& t, const typename Pol::TW* __restrict__ tw3,
+                                         const double2* __restrict__ coeffs, typename Pol::V* __restrict__ cyl) {
     using V = typename Pol::V;
     using TW = typename Pol::TW;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -141,6 +141,25 @@ __global__ void __launch_bounds__(kThreads) k1_w(DevTables t, const typename Pol
         V* row = cyl + (b * t.S + t.tile_sticks[s0 + l]) * (long long)N;
         for (int z = lane; z < N; z += 32) row[z] = w_store(w_at<V>(buf, z, l));
     }
+}
+
+// Block floors for the double-float z- and y-passes at length 96 (the
+// compiler's own choice leaves one resident CTA per SM fewer): measured ms per
+// 1024 bands at 96^3, own choice -> floor: K1 1.91 -> 1.76 (6 CTAs, 80
+// registers), inverse K2 3.74 -> 2.51 (6, 80), forward K2 3.09 -> 2.62 (7, 72),
+// K4 1.95 -> 1.79 (7, 72).  Floors make the compiler use registers up to the
+// cap, so the other lengths keep its own choice.
+template <class Pol, int N> constexpr bool df_floors() { return std::is_same<Pol, PolDF>::value && N == 96; }
+template <class Pol, int N>
+__global__ void __launch_bounds__(kThreads) k1_w(DevTables t, const typename Pol::TW* __restrict__ tw3,
+                                                const double2* __restrict__ coeffs, typename Pol::V* __restrict__ cyl) {
+    k1w_body<Pol, N>(t, tw3, coeffs, cyl);
+}
+template <class Pol, int N, int MINB>
+__global__ void __launch_bounds__(kThreads, MINB) k1_wb(DevTables t, const typename Pol::TW* __restrict__ tw3,
+                                                       const double2* __restrict__ coeffs,
+                                                       typename Pol::V* __restrict__ cyl) {
+    k1w_body<Pol, N>(t, tw3, coeffs, cyl);
 }
 
 // ------------------------------------------------------------------ K2
@@ -178,17 +197,9 @@ __global__ void __launch_bounds__(kThreads) k2_w(DevTables t, const typename Pol
                                                 typename Pol::V* cyl, typename Pol::V* slab) {
     k2w_body<Pol, S, N>(t, tw2, cyl, slab);
 }
-#ifndef VLOC_MINB_K2DF
-#define VLOC_MINB_K2DF 6
-#endif
-// The same with six resident CTAs per SM asked of the compiler (at most 80
-// registers a thread, no spills), for the double-float inverse y-pass up to
-// length 96: left to itself the compiler gives it 103 registers and four
-// CTAs per SM.  Measured at 96^3, ms per 1024 bands: 3.74 unbounded, 3.44
-// with a floor of 4 CTAs, 3.27 with 5, 2.51 with 6.
-template <class Pol, int S, int N>
-__global__ void __launch_bounds__(kThreads, VLOC_MINB_K2DF) k2_wb(DevTables t, const typename Pol::TW* __restrict__ tw2,
-                                                    typename Pol::V* cyl, typename Pol::V* slab) {
+template <class Pol, int S, int N, int MINB>
+__global__ void __launch_bounds__(kThreads, MINB) k2_wb(DevTables t, const typename Pol::TW* __restrict__ tw2,
+                                                       typename Pol::V* cyl, typename Pol::V* slab) {
     k2w_body<Pol, S, N>(t, tw2, cyl, slab);
 }
 
@@ -379,9 +390,9 @@ __global__ void __launch_bounds__(kThreads) k3q_w(DevTables t, const typename Po
 
 // ------------------------------------------------------------------ K4
 template <class Pol, int N>
-__global__ void __launch_bounds__(kThreads) k4_w(DevTables t, const typename Pol::TW* __restrict__ tw3,
-                                                const typename Pol::V* __restrict__ cyl, double2* out, double scale,
-                                                const double* __restrict__ diag, const double2* cin) {
+__device__ __forceinline__ void k4w_body(const DevTables& t, const typename Pol::TW* __restrict__ tw3,
+                                         const typename Pol::V* __restrict__ cyl, double2* out, double scale,
+                                         const double* __restrict__ diag, const double2* cin) {
     using V = typename Pol::V;
     using TW = typename Pol::TW;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -420,6 +431,20 @@ __global__ void __launch_bounds__(kThreads) k4_w(DevTables t, const typename Pol
     }
 }
 
+template <class Pol, int N>
+__global__ void __launch_bounds__(kThreads) k4_w(DevTables t, const typename Pol::TW* __restrict__ tw3,
+                                                const typename Pol::V* __restrict__ cyl, double2* out, double scale,
+                                                const double* __restrict__ diag, const double2* cin) {
+    k4w_body<Pol, N>(t, tw3, cyl, out, scale, diag, cin);
+}
+template <class Pol, int N, int MINB>
+__global__ void __launch_bounds__(kThreads, MINB) k4_wb(DevTables t, const typename Pol::TW* __restrict__ tw3,
+                                                       const typename Pol::V* __restrict__ cyl, double2* out,
+                                                       double scale, const double* __restrict__ diag,
+                                                       const double2* cin) {
+    k4w_body<Pol, N>(t, tw3, cyl, out, scale, diag, cin);
+}
+
 // ------------------------------------------------------------ launchers
 template <class Pol, int N> struct WSmem {
     static constexpr size_t sm = w_smem<Pol, N>();
@@ -433,10 +458,17 @@ template <int P, int N>
 int LaunchF64<P, N>::k1(const DevTables& t, const void* tw3, const void* coeffs, long long nb, void* cyl,
                         cudaStream_t st) {
     using Pol = PolOf<P>;
-    static const cudaError_t once = WSmem<Pol, N>::ensure(k1_w<Pol, N>);
-    if (once) return (int)once;
-    k1_w<Pol, N><<<dim3(t.T, (unsigned)nb, 2), kThreads, WSmem<Pol, N>::sm, st>>>(
-        t, (const typename Pol::TW*)tw3, (const double2*)coeffs, (typename Pol::V*)cyl);
+    if constexpr (df_floors<Pol, N>()) {
+        static const cudaError_t onceb = WSmem<Pol, N>::ensure(k1_wb<Pol, N, 6>);
+        if (onceb) return (int)onceb;
+        k1_wb<Pol, N, 6><<<dim3(t.T, (unsigned)nb, 2), kThreads, WSmem<Pol, N>::sm, st>>>(
+            t, (const typename Pol::TW*)tw3, (const double2*)coeffs, (typename Pol::V*)cyl);
+    } else {
+        static const cudaError_t once = WSmem<Pol, N>::ensure(k1_w<Pol, N>);
+        if (once) return (int)once;
+        k1_w<Pol, N><<<dim3(t.T, (unsigned)nb, 2), kThreads, WSmem<Pol, N>::sm, st>>>(
+            t, (const typename Pol::TW*)tw3, (const double2*)coeffs, (typename Pol::V*)cyl);
+    }
     return (int)cudaGetLastError();
 }
 template <int P, int N>
@@ -445,22 +477,30 @@ int LaunchF64<P, N>::k2(int sign, const DevTables& t, const void* tw2, long long
     using Pol = PolOf<P>;
     using V = typename Pol::V;
     const dim3 grid(t.NP, (t.n3 + kLinesDF - 1) / kLinesDF, (unsigned)nb);
-    if (sign > 0) {
-        if constexpr (std::is_same<Pol, PolDF>::value && N <= 96) {
-            static const cudaError_t onceb = WSmem<Pol, N>::ensure(k2_wb<Pol, +1, N>);
+    if constexpr (df_floors<Pol, N>()) {
+        if (sign > 0) {
+            static const cudaError_t onceb = WSmem<Pol, N>::ensure(k2_wb<Pol, +1, N, 6>);
             if (onceb) return (int)onceb;
-            k2_wb<Pol, +1, N><<<grid, kThreads, WSmem<Pol, N>::sm, st>>>(t, (const typename Pol::TW*)tw2, (V*)cyl,
-                                                                         (V*)slab);
+            k2_wb<Pol, +1, N, 6><<<grid, kThreads, WSmem<Pol, N>::sm, st>>>(t, (const typename Pol::TW*)tw2, (V*)cyl,
+                                                                            (V*)slab);
         } else {
+            static const cudaError_t onceb = WSmem<Pol, N>::ensure(k2_wb<Pol, -1, N, 7>);
+            if (onceb) return (int)onceb;
+            k2_wb<Pol, -1, N, 7><<<grid, kThreads, WSmem<Pol, N>::sm, st>>>(t, (const typename Pol::TW*)tw2, (V*)cyl,
+                                                                            (V*)slab);
+        }
+    } else {
+        if (sign > 0) {
             static const cudaError_t once = WSmem<Pol, N>::ensure(k2_w<Pol, +1, N>);
             if (once) return (int)once;
             k2_w<Pol, +1, N><<<grid, kThreads, WSmem<Pol, N>::sm, st>>>(t, (const typename Pol::TW*)tw2, (V*)cyl,
                                                                         (V*)slab);
+        } else {
+            static const cudaError_t once = WSmem<Pol, N>::ensure(k2_w<Pol, -1, N>);
+            if (once) return (int)once;
+            k2_w<Pol, -1, N><<<grid, kThreads, WSmem<Pol, N>::sm, st>>>(t, (const typename Pol::TW*)tw2, (V*)cyl,
+                                                                        (V*)slab);
         }
-    } else {
-        static const cudaError_t once = WSmem<Pol, N>::ensure(k2_w<Pol, -1, N>);
-        if (once) return (int)once;
-        k2_w<Pol, -1, N><<<grid, kThreads, WSmem<Pol, N>::sm, st>>>(t, (const typename Pol::TW*)tw2, (V*)cyl, (V*)slab);
     }
     return (int)cudaGetLastError();
 }
@@ -491,12 +531,20 @@ template <int P, int N>
 int LaunchF64<P, N>::k4(const DevTables& t, const void* tw3, const void* cyl, long long nb, void* out,
                         const void* diag, const void* cin, cudaStream_t st) {
     using Pol = PolOf<P>;
-    static const cudaError_t once = WSmem<Pol, N>::ensure(k4_w<Pol, N>);
-    if (once) return (int)once;
     const double scale = 1.0 / ((double)t.n1 * t.n2 * t.n3);
-    k4_w<Pol, N><<<dim3(t.T, (unsigned)nb, 2), kThreads, WSmem<Pol, N>::sm, st>>>(
-        t, (const typename Pol::TW*)tw3, (const typename Pol::V*)cyl, (double2*)out, scale, (const double*)diag,
-        (const double2*)cin);
+    if constexpr (df_floors<Pol, N>()) {
+        static const cudaError_t onceb = WSmem<Pol, N>::ensure(k4_wb<Pol, N, 7>);
+        if (onceb) return (int)onceb;
+        k4_wb<Pol, N, 7><<<dim3(t.T, (unsigned)nb, 2), kThreads, WSmem<Pol, N>::sm, st>>>(
+            t, (const typename Pol::TW*)tw3, (const typename Pol::V*)cyl, (double2*)out, scale, (const double*)diag,
+            (const double2*)cin);
+    } else {
+        static const cudaError_t once = WSmem<Pol, N>::ensure(k4_w<Pol, N>);
+        if (once) return (int)once;
+        k4_w<Pol, N><<<dim3(t.T, (unsigned)nb, 2), kThreads, WSmem<Pol, N>::sm, st>>>(
+            t, (const typename Pol::TW*)tw3, (const typename Pol::V*)cyl, (double2*)out, scale, (const double*)diag,
+            (const double2*)cin);
+    }
     return (int)cudaGetLastError();
 }
 
