@@ -793,11 +793,15 @@ __global__ void __launch_bounds__(32 * W, minb_k3q(N)) k3q_ct(DevTables t, const
     float2* twB = twA + N;
     const int n2 = t.n2, n3 = t.n3;
     const int slot = slot_of(), sub = sub_of(), warp = warp_of();
-    const int y = blockIdx.x;
-    const int z0 = blockIdx.y * kLines;
+    // tile = 16 consecutive line pairs (y, z pair) of the band in y-major
+    // order, so a tile may span two y rows and none is ragged (n3 / 2 line
+    // pairs per y row; 3 tiles a row at n3 = 96)
+    const int hz = n3 >> 1, npairs = n2 * hz;
     const long long b = blockIdx.z;
-    const int lines = min(kLines, n3 - z0);
-    const bool act = 2 * slot < lines;
+    auto pair_of = [&](int s) { return min((int)blockIdx.x * 16 + s, npairs - 1); };
+    const int f = pair_of(slot);
+    const bool act = (int)blockIdx.x * 16 + slot < npairs;
+    const int y = f / hz, zq = 2 * (f - y * hz);
     // twiddle rows (first read after the barrier that ends stage 0, which
     // needs none)
     for (int e = threadIdx.x; e < N; e += 32 * W) {
@@ -805,8 +809,8 @@ __global__ void __launch_bounds__(32 * W, minb_k3q(N)) k3q_ct(DevTables t, const
         twB[e] = tw1[(e / R0) * (e % R0)];
     }
     const int pstride = n2 * n3;
-    float2* sl = slab + b * t.NP * (long long)pstride + y * n3 + z0 + 2 * slot;  // plane 0, this lane's pair
-    const float* vrow = Vr + (long long)y * n3 + z0 + 2 * slot;
+    float2* sl = slab + b * t.NP * (long long)pstride + y * n3 + zq;  // plane 0, this lane's pair
+    const float* vrow = Vr + (long long)y * n3 + zq;
     SmemP sb{buf};
 
     // inverse x-FFT, first stage (radix R0, no twiddles): global rows -> buffer
@@ -867,10 +871,11 @@ __global__ void __launch_bounds__(32 * W, minb_k3q(N)) k3q_ct(DevTables t, const
         for (int k = 0; k < LT; ++k) {
             const int tk = threadIdx.x + k * 32 * W;  // line task: unit, slot, line
             const int i = FR * 2 * W + tk / 32, ls = (tk >> 1) & 15, ln = tk & 1;
-            if (tk < LU * 32 && 2 * ls < lines) {
+            if (tk < LU * 32 && (int)blockIdx.x * 16 + ls < npairs) {
+                const int fl = pair_of(ls), yl = fl / hz;
 #pragma unroll
                 for (int r = 0; r < R1; ++r) hl[k][r] = buf[(i + r * NB) * kLdP + 2 * ls + ln];
-                chain(hl[k], i, Vr + (long long)y * n3 + z0 + 2 * ls + ln,
+                chain(hl[k], i, Vr + (long long)yl * n3 + 2 * (fl - yl * hz) + ln,
                       [](float2& v, const float* q) { v = cscale(v, *q); });
             }
         }
@@ -890,7 +895,7 @@ __global__ void __launch_bounds__(32 * W, minb_k3q(N)) k3q_ct(DevTables t, const
         for (int k = 0; k < LT; ++k) {
             const int tk = threadIdx.x + k * 32 * W;
             const int i = FR * 2 * W + tk / 32, ls = (tk >> 1) & 15, ln = tk & 1;
-            if (tk < LU * 32 && 2 * ls < lines) {
+            if (tk < LU * 32 && (int)blockIdx.x * 16 + ls < npairs) {
 #pragma unroll
                 for (int r = 0; r < R1; ++r) buf[(i * R1 + r) * kLdP + 2 * ls + ln] = hl[k][r];
             }
@@ -1559,7 +1564,7 @@ int LaunchCT<T, N>::k3(const DevTables& t, const void* tw1, const void* V, long 
                 sm <= 48 * 1024 ? cudaSuccess
                                 : cudaFuncSetAttribute(k3q_ct<N, W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
             if (onceq) return (int)onceq;
-            const dim3 grid(t.n2, (t.n3 + kLines - 1) / kLines, (unsigned)nb);
+            const dim3 grid((unsigned)((t.n2 * (t.n3 / 2) + 15) / 16), 1, (unsigned)nb);  // 16 line pairs a tile
             k3q_ct<N, W><<<grid, 32 * W, sm, st>>>(t, (const float2*)tw1, (const float*)V, (float2*)slab);
             return (int)cudaGetLastError();
         }
