@@ -144,12 +144,25 @@ __device__ __forceinline__ void k1w_body(const DevTables& t, const typename Pol:
 }
 
 // Block floors for the double-float z- and y-passes at length 96 (the
-// compiler's own choice leaves one resident CTA per SM fewer): measured ms per
-// 1024 bands at 96^3, own choice -> floor: K1 1.91 -> 1.76 (6 CTAs, 80
-// registers), inverse K2 3.74 -> 2.51 (6, 80), forward K2 3.09 -> 2.62 (7, 72),
-// K4 1.95 -> 1.79 (7, 72).  Floors make the compiler use registers up to the
+// compiler's own choice leaves one or two resident CTAs per SM fewer):
+// measured ms per 1024 bands at 96^3, own choice -> floor: K1 1.91 -> 1.76 (6
+// CTAs, 80 registers) -> 1.66 (7, 72), inverse K2 3.74 -> 2.51 (6, 80) -> 2.46
+// (7, 72), forward K2 3.09 -> 2.62 (7, 72; 8 measured 2.66), K4 1.95 -> 1.79
+// (7, 72; 8 measured 1.82).  Floors make the compiler use registers up to the
 // cap, so the other lengths keep its own choice.
 template <class Pol, int N> constexpr bool df_floors() { return std::is_same<Pol, PolDF>::value && N == 96; }
+#ifndef VLOC_MINB_K1DF
+#define VLOC_MINB_K1DF 7
+#endif
+#ifndef VLOC_MINB_K2IDF
+#define VLOC_MINB_K2IDF 7
+#endif
+#ifndef VLOC_MINB_K2FDF
+#define VLOC_MINB_K2FDF 7
+#endif
+#ifndef VLOC_MINB_K4DF
+#define VLOC_MINB_K4DF 7
+#endif
 template <class Pol, int N>
 __global__ void __launch_bounds__(kThreads) k1_w(DevTables t, const typename Pol::TW* __restrict__ tw3,
                                                 const double2* __restrict__ coeffs, typename Pol::V* __restrict__ cyl) {
@@ -459,9 +472,9 @@ int LaunchF64<P, N>::k1(const DevTables& t, const void* tw3, const void* coeffs,
                         cudaStream_t st) {
     using Pol = PolOf<P>;
     if constexpr (df_floors<Pol, N>()) {
-        static const cudaError_t onceb = WSmem<Pol, N>::ensure(k1_wb<Pol, N, 6>);
+        static const cudaError_t onceb = WSmem<Pol, N>::ensure(k1_wb<Pol, N, VLOC_MINB_K1DF>);
         if (onceb) return (int)onceb;
-        k1_wb<Pol, N, 6><<<dim3(t.T, (unsigned)nb, 2), kThreads, WSmem<Pol, N>::sm, st>>>(
+        k1_wb<Pol, N, VLOC_MINB_K1DF><<<dim3(t.T, (unsigned)nb, 2), kThreads, WSmem<Pol, N>::sm, st>>>(
             t, (const typename Pol::TW*)tw3, (const double2*)coeffs, (typename Pol::V*)cyl);
     } else {
         static const cudaError_t once = WSmem<Pol, N>::ensure(k1_w<Pol, N>);
@@ -479,14 +492,14 @@ int LaunchF64<P, N>::k2(int sign, const DevTables& t, const void* tw2, long long
     const dim3 grid(t.NP, (t.n3 + kLinesDF - 1) / kLinesDF, (unsigned)nb);
     if constexpr (df_floors<Pol, N>()) {
         if (sign > 0) {
-            static const cudaError_t onceb = WSmem<Pol, N>::ensure(k2_wb<Pol, +1, N, 6>);
+            static const cudaError_t onceb = WSmem<Pol, N>::ensure(k2_wb<Pol, +1, N, VLOC_MINB_K2IDF>);
             if (onceb) return (int)onceb;
-            k2_wb<Pol, +1, N, 6><<<grid, kThreads, WSmem<Pol, N>::sm, st>>>(t, (const typename Pol::TW*)tw2, (V*)cyl,
+            k2_wb<Pol, +1, N, VLOC_MINB_K2IDF><<<grid, kThreads, WSmem<Pol, N>::sm, st>>>(t, (const typename Pol::TW*)tw2, (V*)cyl,
                                                                             (V*)slab);
         } else {
-            static const cudaError_t onceb = WSmem<Pol, N>::ensure(k2_wb<Pol, -1, N, 7>);
+            static const cudaError_t onceb = WSmem<Pol, N>::ensure(k2_wb<Pol, -1, N, VLOC_MINB_K2FDF>);
             if (onceb) return (int)onceb;
-            k2_wb<Pol, -1, N, 7><<<grid, kThreads, WSmem<Pol, N>::sm, st>>>(t, (const typename Pol::TW*)tw2, (V*)cyl,
+            k2_wb<Pol, -1, N, VLOC_MINB_K2FDF><<<grid, kThreads, WSmem<Pol, N>::sm, st>>>(t, (const typename Pol::TW*)tw2, (V*)cyl,
                                                                             (V*)slab);
         }
     } else {
@@ -533,9 +546,9 @@ int LaunchF64<P, N>::k4(const DevTables& t, const void* tw3, const void* cyl, lo
     using Pol = PolOf<P>;
     const double scale = 1.0 / ((double)t.n1 * t.n2 * t.n3);
     if constexpr (df_floors<Pol, N>()) {
-        static const cudaError_t onceb = WSmem<Pol, N>::ensure(k4_wb<Pol, N, 7>);
+        static const cudaError_t onceb = WSmem<Pol, N>::ensure(k4_wb<Pol, N, VLOC_MINB_K4DF>);
         if (onceb) return (int)onceb;
-        k4_wb<Pol, N, 7><<<dim3(t.T, (unsigned)nb, 2), kThreads, WSmem<Pol, N>::sm, st>>>(
+        k4_wb<Pol, N, VLOC_MINB_K4DF><<<dim3(t.T, (unsigned)nb, 2), kThreads, WSmem<Pol, N>::sm, st>>>(
             t, (const typename Pol::TW*)tw3, (const typename Pol::V*)cyl, (double2*)out, scale, (const double*)diag,
             (const double2*)cin);
     } else {
