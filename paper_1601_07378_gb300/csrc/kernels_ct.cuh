@@ -761,6 +761,9 @@ template <int N> __host__ __device__ constexpr size_t k3q_smem() {
 #define VLOC_K3Q_SPLIT 1
 #endif
 
+#ifndef VLOC_MINB_K3Q_96
+#define VLOC_MINB_K3Q_96 7  // 72 registers, no spills: 1.547 against 1.572 ms per 1024 bands with 6 (8: 1.69)
+#endif
 #ifndef VLOC_MINB_K3Q_100
 #define VLOC_MINB_K3Q_100 6
 #endif
@@ -774,7 +777,7 @@ template <int N> __host__ __device__ constexpr size_t k3q_smem() {
 #define VLOC_MINB_K3Q_144 4
 #endif
 constexpr int minb_k3q(int n) {
-    return n <= 96 ? VLOC_MINB_K3Q : n == 100 ? VLOC_MINB_K3Q_100 : n == 120 ? VLOC_MINB_K3Q_120
+    return n == 96 ? VLOC_MINB_K3Q_96 : n < 96 ? VLOC_MINB_K3Q : n == 100 ? VLOC_MINB_K3Q_100 : n == 120 ? VLOC_MINB_K3Q_120
            : n == 128 ? VLOC_MINB_K3Q_128 : n == 144 ? VLOC_MINB_K3Q_144 : 1;
 }
 template <int N, int W>
