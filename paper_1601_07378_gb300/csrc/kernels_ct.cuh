@@ -780,7 +780,10 @@ constexpr int minb_k3q(int n) {
     return n == 96 ? VLOC_MINB_K3Q_96 : n < 96 ? VLOC_MINB_K3Q : n == 100 ? VLOC_MINB_K3Q_100 : n == 120 ? VLOC_MINB_K3Q_120
            : n == 128 ? VLOC_MINB_K3Q_128 : n == 144 ? VLOC_MINB_K3Q_144 : 1;
 }
-template <int N, int W>
+// FLAT: tiles of 16 consecutive line pairs of the band (any even n3);
+// otherwise block (y, 32-z tile, band) for n3 a multiple of 32 (the same
+// tiles without the per-lane division that maps a flat index to (y, z pair)).
+template <int N, int W, bool FLAT = true>
 __global__ void __launch_bounds__(32 * W, minb_k3q(N)) k3q_ct(DevTables t, const float2* __restrict__ tw1,
                                                   const float* __restrict__ Vr, float2* slab) {
     using SC = Sched<N>;
@@ -801,10 +804,19 @@ __global__ void __launch_bounds__(32 * W, minb_k3q(N)) k3q_ct(DevTables t, const
     // pairs per y row; 3 tiles a row at n3 = 96)
     const int hz = n3 >> 1, npairs = n2 * hz;
     const long long b = blockIdx.z;
-    auto pair_of = [&](int s) { return min((int)blockIdx.x * 16 + s, npairs - 1); };
-    const int f = pair_of(slot);
-    const bool act = (int)blockIdx.x * 16 + slot < npairs;
-    const int y = f / hz, zq = 2 * (f - y * hz);
+    // flat line-pair index of slot s (its tile's first pair + s)
+    const int fbase = FLAT ? (int)blockIdx.x * 16 : (int)blockIdx.x * hz + (int)blockIdx.y * 16;
+    auto pair_of = [&](int s) { return min(fbase + s, npairs - 1); };
+    const bool act = fbase + slot < npairs;
+    int y, zq;
+    if constexpr (FLAT) {
+        const int f = pair_of(slot);
+        y = f / hz;
+        zq = 2 * (f - y * hz);
+    } else {
+        y = blockIdx.x;
+        zq = (int)blockIdx.y * kLines + 2 * slot;
+    }
     // twiddle rows (first read after the barrier that ends stage 0, which
     // needs none)
     for (int e = threadIdx.x; e < N; e += 32 * W) {
@@ -874,12 +886,19 @@ __global__ void __launch_bounds__(32 * W, minb_k3q(N)) k3q_ct(DevTables t, const
         for (int k = 0; k < LT; ++k) {
             const int tk = threadIdx.x + k * 32 * W;  // line task: unit, slot, line
             const int i = FR * 2 * W + tk / 32, ls = (tk >> 1) & 15, ln = tk & 1;
-            if (tk < LU * 32 && (int)blockIdx.x * 16 + ls < npairs) {
-                const int fl = pair_of(ls), yl = fl / hz;
+            if (tk < LU * 32 && fbase + ls < npairs) {
+                int yl, zl;
+                if constexpr (FLAT) {
+                    const int fl = pair_of(ls);
+                    yl = fl / hz;
+                    zl = 2 * (fl - yl * hz);
+                } else {
+                    yl = y;
+                    zl = (int)blockIdx.y * kLines + 2 * ls;
+                }
 #pragma unroll
                 for (int r = 0; r < R1; ++r) hl[k][r] = buf[(i + r * NB) * kLdP + 2 * ls + ln];
-                chain(hl[k], i, Vr + (long long)yl * n3 + 2 * (fl - yl * hz) + ln,
-                      [](float2& v, const float* q) { v = cscale(v, *q); });
+                chain(hl[k], i, Vr + (long long)yl * n3 + zl + ln, [](float2& v, const float* q) { v = cscale(v, *q); });
             }
         }
     }
@@ -898,7 +917,7 @@ __global__ void __launch_bounds__(32 * W, minb_k3q(N)) k3q_ct(DevTables t, const
         for (int k = 0; k < LT; ++k) {
             const int tk = threadIdx.x + k * 32 * W;
             const int i = FR * 2 * W + tk / 32, ls = (tk >> 1) & 15, ln = tk & 1;
-            if (tk < LU * 32 && (int)blockIdx.x * 16 + ls < npairs) {
+            if (tk < LU * 32 && fbase + ls < npairs) {
 #pragma unroll
                 for (int r = 0; r < R1; ++r) buf[(i * R1 + r) * kLdP + 2 * ls + ln] = hl[k][r];
             }
@@ -1569,12 +1588,14 @@ int LaunchCT<T, N>::k3(const DevTables& t, const void* tw1, const void* V, long 
             constexpr size_t sm = k3q_smem<N>();
             // (a preferred shared-memory carveout, 86 % or 100 %, measured
             // slower at every length than the driver's own choice)
-            static const cudaError_t onceq =
-                sm <= 48 * 1024 ? cudaSuccess
-                                : cudaFuncSetAttribute(k3q_ct<N, W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-            if (onceq) return (int)onceq;
-            const dim3 grid((unsigned)((t.n2 * (t.n3 / 2) + 15) / 16), 1, (unsigned)nb);  // 16 line pairs a tile
-            k3q_ct<N, W><<<grid, 32 * W, sm, st>>>(t, (const float2*)tw1, (const float*)V, (float2*)slab);
+            static_assert(sm <= 48 * 1024, "x-pass tile within the default shared-memory limit");
+            if (t.n3 % kLines == 0) {
+                const dim3 grid(t.n2, t.n3 / kLines, (unsigned)nb);
+                k3q_ct<N, W, false><<<grid, 32 * W, sm, st>>>(t, (const float2*)tw1, (const float*)V, (float2*)slab);
+            } else {
+                const dim3 grid((unsigned)((t.n2 * (t.n3 / 2) + 15) / 16), 1, (unsigned)nb);  // 16 line pairs a tile
+                k3q_ct<N, W, true><<<grid, 32 * W, sm, st>>>(t, (const float2*)tw1, (const float*)V, (float2*)slab);
+            }
             return (int)cudaGetLastError();
         }
     }
