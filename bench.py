@@ -532,10 +532,11 @@ def run_ours(args, rank, world, local_rank):
             "to_recip": leg(lambda: plan.to_recip(grid_d, out_d[:nh]), kh, nh,
                             Nn * 8 + 2 * slab_b + 2 * cyl_b + info["npw"] * 8),
             "density": leg(lambda: plan.density(c_d, rho=rho_d), kh, NBANDS,
-                           info["npw"] * 8 + 2 * cyl_b + slab_b),
+                           info["npw"] * 8 + 2 * cyl_b + 2 * slab_b),
             "what": "96^3, R = 24, FP32: psi = F+ S c to full grids (256 bands), r -> G of full grids "
-                    "(256 bands), rho = sum |psi_n|^2 (1024 bands); alg bytes per band: "
-                    "to_real/to_recip npw + 2 cyl + 2 slab + N, density npw + 2 cyl + slab (complex64)",
+                    "(256 bands), rho = sum |psi_n|^2 (1024 bands); alg bytes per band, every "
+                    "inter-kernel round trip counted as in B5: to_real/to_recip npw + 2 cyl + 2 slab + N, "
+                    "density npw + 2 cyl + 2 slab (complex64)",
         }
         del grid_d, rho_d
 
