@@ -48,9 +48,11 @@ struct DevTables {
     // z = C m + j, or -1 (the warp-register z-passes of kernels_zs.cuh)
     int zs;
     const int* zsh;
-    // stick runs of plain quarter-band plans whose every stick's plane waves
-    // are consecutive in the caller's list, l ascending (runs = 1): per tile
-    // line [T][32] {caller index of the first, its l, count, 0}
+    // stick runs of plain FP32 quarter-band plans whose every stick's plane
+    // waves are consecutive in the caller's list, l ascending: per tile line
+    // [T][32] {caller index of the first, its l, count, 0}; runs = 2: K1
+    // addresses its inputs from them, 1: K1 stages them by bulk copies
+    // (VLOC_Z_BULK), 0: no runs (K1 reads through the dense table)
     int runs;
     const int4* run_tab;
     int* err;  // the plan's device error flag (set by a bounded wait that ran out), or null

@@ -476,7 +476,10 @@ __global__ void __launch_bounds__(kThreads, minb_k1(N)) k1q_ct(DevTables t, cons
 #ifndef VLOC_K1_DIRECT
 #define VLOC_K1_DIRECT 1
 #endif
-template <int N>
+// RUNS: the caller's list in stick order (DevTables::runs); each line's
+// inputs are addressed from its run (first caller index, its l, count)
+// instead of the dense table.
+template <int N, bool RUNS>
 __global__ void __launch_bounds__(kThreads, minb_k1(N)) k1d_ct(DevTables t, const float2* __restrict__ tw3,
                                                   const float2* __restrict__ coeffs, float2* __restrict__ cyl) {
     using SC = Sched<N>;
@@ -498,18 +501,34 @@ __global__ void __launch_bounds__(kThreads, minb_k1(N)) k1d_ct(DevTables t, cons
     for (int u = 0; u < UA; ++u) {
         const int i = 2 * (warp + u * W) + sub;
         if (NA % (2 * W) == 0 || i < NA) {
-            int2 e[R0];
-            sfor<R0>([&](auto rc) {
-                constexpr int r = decltype(rc)::value;
-                if constexpr (QR::kind(r) != 0)
-                    e[r] = *reinterpret_cast<const int2*>(zd + (QR::group(r) * NA + i) * kLines);
-            });
             P2f h[R0];
-            sfor<R0>([&](auto rc) {
-                constexpr int r = decltype(rc)::value;
-                if constexpr (QR::kind(r) == 0) h[r] = czero<P2f>();
-                else h[r] = P2f{coef(e[r].x), coef(e[r].y)};
-            });
+            if constexpr (RUNS) {
+                const int lines = t.tile_ptr[tile + 1] - t.tile_ptr[tile];
+                const int4* rt = t.run_tab + (size_t)tile * kLines + 2 * slot;
+                const int4 ra = 2 * slot < lines ? rt[0] : make_int4(0, 0, 0, 0);
+                const int4 rb = 2 * slot + 1 < lines ? rt[1] : make_int4(0, 0, 0, 0);
+                auto at = [&](const int4& rr, int x) {
+                    const int p = (x <= N / 2 ? x : x - N) - rr.y;
+                    return (p >= 0 && p < rr.z) ? c[rr.x + p] : make_float2(0.f, 0.f);
+                };
+                sfor<R0>([&](auto rc) {
+                    constexpr int r = decltype(rc)::value;
+                    if constexpr (QR::kind(r) == 0) h[r] = czero<P2f>();
+                    else h[r] = P2f{at(ra, i + r * NA), at(rb, i + r * NA)};
+                });
+            } else {
+                int2 e[R0];
+                sfor<R0>([&](auto rc) {
+                    constexpr int r = decltype(rc)::value;
+                    if constexpr (QR::kind(r) != 0)
+                        e[r] = *reinterpret_cast<const int2*>(zd + (QR::group(r) * NA + i) * kLines);
+                });
+                sfor<R0>([&](auto rc) {
+                    constexpr int r = decltype(rc)::value;
+                    if constexpr (QR::kind(r) == 0) h[r] = czero<P2f>();
+                    else h[r] = P2f{coef(e[r].x), coef(e[r].y)};
+                });
+            }
             DftZ<R0, +1, QR::mask()>::run(h);
 #pragma unroll
             for (int r = 0; r < R0; ++r) sb(i * R0 + r, slot, h[r]);
@@ -1516,7 +1535,7 @@ int launch_k1_ct(const DevTables& t, const void* tw3, const void* coeffs, long l
         }
     }
     if constexpr (Sched<N>::nst == 2) {
-        if (!GM && VLOC_K1_BULK && t.runs && t.zd_rows == QRows<N>::groups() * QRows<N>::NA) {
+        if (!GM && VLOC_K1_BULK && t.runs == 1 && t.zd_rows == QRows<N>::groups() * QRows<N>::NA) {
             constexpr size_t sm = k1b_smem<N>();
             static const cudaError_t onceb =
                 sm <= 48 * 1024 ? cudaSuccess : cudaFuncSetAttribute(k1b_ct<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
@@ -1528,10 +1547,15 @@ int launch_k1_ct(const DevTables& t, const void* tw3, const void* coeffs, long l
         // the dense table exists for plain plans only (its entries are caller
         // indices of the complex band the kernel reads)
         if (!GM && VLOC_K1_DIRECT && t.zd_rows == QRows<N>::groups() * QRows<N>::NA) {
-            static const cudaError_t onced = CtSmem<N>::ensure(k1d_ct<N>);
+            if (t.runs == 2) {
+                k1d_ct<N, true><<<dim3(t.T, (unsigned)nb), kThreads, CtSmem<N>::sm, st>>>(t, (const float2*)tw3,
+                                                                                      (const float2*)coeffs, (float2*)cyl);
+                return (int)cudaGetLastError();
+            }
+            static const cudaError_t onced = CtSmem<N>::ensure(k1d_ct<N, false>);
             if (onced) return (int)onced;
-            k1d_ct<N><<<dim3(t.T, (unsigned)nb), kThreads, CtSmem<N>::sm, st>>>(t, (const float2*)tw3,
-                                                                                (const float2*)coeffs, (float2*)cyl);
+            k1d_ct<N, false><<<dim3(t.T, (unsigned)nb), kThreads, CtSmem<N>::sm, st>>>(t, (const float2*)tw3,
+                                                                                       (const float2*)coeffs, (float2*)cyl);
             return (int)cudaGetLastError();
         }
         if (t.zq) {

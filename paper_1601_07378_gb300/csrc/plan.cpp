@@ -505,13 +505,15 @@ int vloc_plan_create(vloc_plan* out, int n1, int n2, int n3, const int32_t* g, i
         zs_ok = 1;
     }
 
-    // ---- stick runs for the bulk-staged z-pass (VLOC_Z_BULK): plain
-    // quarter-band plans (the dense table exists) whose every stick holds
-    // consecutive caller indices in l order with no gap in l (the canonical
-    // order); per tile line {first caller index, its l, count, 0}
+    // ---- stick runs: plain FP32 quarter-band plans (the dense table exists)
+    // whose every stick holds consecutive caller indices in l order with no
+    // gap in l (the canonical order); per tile line {first caller index, its
+    // l, count, 0}.  K1 then addresses its inputs from the runs (runs = 2;
+    // 0.372 against 0.384 ms per 1024 bands at 96^3 through the dense table),
+    // or stages them by bulk copies with VLOC_Z_BULK (runs = 1).
     std::vector<int> run_tab;
     int runs_ok = 0;
-    if ((flags & VLOC_Z_BULK) && !(flags & VLOC_Z_WARP) && !dbl && zd_rows > 0) {
+    if (!(flags & VLOC_Z_WARP) && !dbl && zd_rows > 0) {
         bool ok = true;
         std::vector<int> first(S), lmin(S), cnt(S);
         for (int s = 0; ok && s < S; ++s) {
@@ -528,7 +530,7 @@ int vloc_plan_create(vloc_plan* out, int n1, int n2, int n3, const int32_t* g, i
                     int* e = &run_tab[((size_t)tt * kLinesPerTile + (i - tile_ptr[tt])) * 4];
                     e[0] = first[s]; e[1] = lmin[s]; e[2] = cnt[s];
                 }
-            runs_ok = 1;
+            runs_ok = (flags & VLOC_Z_BULK) ? 1 : 2;
         }
     }
 
@@ -1424,7 +1426,7 @@ int vloc_get_info(vloc_plan p, vloc_info* info) {
     info->lines_per_tile = kLinesPerTile;
     info->path = (p->fast ? 1 : 0) | (p->gamma ? 4 : 0) | (p->df ? 8 : 0) | (p->k3tma_on ? 16 : 0) |
                  (p->lay.xq ? 32 : 0) | (p->lay.zq ? 64 : 0) | (p->gfused ? 128 : 0) |
-                 (p->lay.zs && p->fast ? 256 : 0) | (p->lay.runs && p->fast ? 512 : 0);
+                 (p->lay.zs && p->fast ? 256 : 0) | (p->lay.runs == 1 && p->fast ? 512 : 0);
     info->chunk_bands = p->chunk;
     info->workspace_bytes = (int64_t)p->ws_bytes;
     for (int a = 0; a < 3; ++a) {
