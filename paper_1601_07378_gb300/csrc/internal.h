@@ -139,7 +139,7 @@ template <typename T, int N> struct LaunchCT {
                    double* partial, cudaStream_t st);
     static int k3g(int sign, const DevTables& t, const void* tw1, long long nb, void* slab, void* grid, cudaStream_t st);
     static int k3d(const DevTables& t, const void* tw1, const void* slab, long long nb, int bpg, const void* occ,
-                   long long b_base, int pair, long long nreal, double* partial, cudaStream_t st);
+                   long long b_base, int pair, long long nreal, float* partial, cudaStream_t st);
 };
 
 // Compile-time-length launchers for FP64 data (kernels_df.cuh), one value
@@ -185,12 +185,23 @@ int launch_k3_grid(int dbl, int fast, int sign, const DevTables& t, const Launch
 // Density x-pass: for slab bands b < nb (global index b_base + b) adds the
 // weighted |psi|^2 of groups of at most bpg bands into partial[group][N]
 // (occ: device weights or null; pair = 1 for Gamma-point pairs of nreal
-// real bands).  Returns the groups used via *used.
+// real bands).  Returns the groups used via *used.  The partials are FP32
+// (float[group][N] over the same bytes) where density_partials_f32 says so,
+// FP64 otherwise.
 int launch_k3d_density(int dbl, int fast, const DevTables& t, const LaunchAxes& ax, const void* tw1, const void* slab,
                        long long nb, int bpg, const void* occ, long long b_base, int pair, long long nreal,
                        double* partial, int* used, cudaStream_t st);
+// 1 when the density x-pass of this plan is a compile-time-length FP32
+// kernel, whose group sums are FP32 values and are stored as such.
+int density_partials_f32(int dbl, int fast, const DevTables& t);
 size_t density_smem_bytes(int dbl, int n);
 int launch_reduce_partials(const double* partial, int ngroups, long long N, double* acc, cudaStream_t st);
+// The same over FP32 partials: the groups are added in order in FP32 with
+// a compensation word, and the pair is added to acc in FP64 (acc taken as
+// zero when `first`); with `out` non-null the total goes there, rounded to
+// FP32, instead of to acc.
+int launch_reduce_partials_f32(const float* partial, int ngroups, long long N, double* acc, int first, float* out,
+                               cudaStream_t st);
 int launch_finish_grad_v(int dbl, const double* acc, void* gradV, long long N, cudaStream_t st);
 // Gamma-point real mode: pack bands (2p, 2p+1) of c [nb][nh] into complex
 // band p of C [np][nfull] over the full list (G, then -G at neg[q]), and

@@ -282,14 +282,25 @@ int launch_k3d_density(int dbl, int fast, const DevTables& t, const LaunchAxes& 
                        long long nb, int bpg, const void* occ, long long b_base, int pair, long long nreal,
                        double* partial, int* used, cudaStream_t st) {
     *used = (int)((nb + bpg - 1) / bpg);
-    if (!dbl && fast && (t.n3 & 1) == 0) switch (t.n1) {
-#define VLOC_CASE(N) case N: return LaunchCT<float, N>::k3d(t, tw1, slab, nb, bpg, occ, b_base, pair, nreal, partial, st);
+    if (density_partials_f32(dbl, fast, t)) switch (t.n1) {
+#define VLOC_CASE(N) \
+    case N: return LaunchCT<float, N>::k3d(t, tw1, slab, nb, bpg, occ, b_base, pair, nreal, (float*)partial, st);
         VLOC_CT_SIZES(VLOC_CASE)
 #undef VLOC_CASE
         default: break;
     }
     return dbl ? Launch<double>::k3d(t, ax, tw1, slab, nb, bpg, occ, b_base, pair, nreal, partial, st)
                : Launch<float>::k3d(t, ax, tw1, slab, nb, bpg, occ, b_base, pair, nreal, partial, st);
+}
+int density_partials_f32(int dbl, int fast, const DevTables& t) {
+    if (dbl || !fast || (t.n3 & 1)) return 0;
+    switch (t.n1) {
+#define VLOC_CASE(N) case N:
+        VLOC_CT_SIZES(VLOC_CASE)
+#undef VLOC_CASE
+        return 1;
+        default: return 0;
+    }
 }
 size_t density_smem_bytes(int dbl, int n) { return dbl ? Launch<double>::smem_dens(n) : Launch<float>::smem_dens(n); }
 
@@ -302,6 +313,33 @@ __global__ void k_reduce_partials(const double* __restrict__ partial, int ng, lo
 }
 int launch_reduce_partials(const double* partial, int ngroups, long long N, double* acc, cudaStream_t st) {
     k_reduce_partials<<<(unsigned)((N + 255) / 256), 256, 0, st>>>(partial, ngroups, N, acc);
+    return (int)cudaGetLastError();
+}
+// FP32 partials, added in group order by compensated summation in FP32
+// (Neumaier's form of Kahan summation, each step an error-free two-sum after
+// Knuth): s + c carries the running sum to about 2^-48 of the terms' sum,
+// so the groups cost FP32 adds rather than FP64 conversions and adds (a
+// slow pipe on this part); s + c then joins the FP64 accumulator.
+__global__ void k_reduce_partials_f32(const float* __restrict__ partial, int ng, long long N, double* __restrict__ acc,
+                                      int first, float* __restrict__ out) {
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    float s = 0.f, c = 0.f;
+#pragma unroll 8
+    for (int g = 0; g < ng; ++g) {
+        const float p = partial[(long long)g * N + i];
+        const float t = __fadd_rn(s, p);
+        const float bp = __fsub_rn(t, s);  // the part of p that t took
+        c = __fadd_rn(c, __fadd_rn(__fsub_rn(s, __fsub_rn(t, bp)), __fsub_rn(p, bp)));
+        s = t;
+    }
+    const double tot = (first ? 0.0 : acc[i]) + ((double)s + (double)c);
+    if (out) out[i] = (float)tot;
+    else acc[i] = tot;
+}
+int launch_reduce_partials_f32(const float* partial, int ngroups, long long N, double* acc, int first, float* out,
+                               cudaStream_t st) {
+    k_reduce_partials_f32<<<(unsigned)((N + 255) / 256), 256, 0, st>>>(partial, ngroups, N, acc, first, out);
     return (int)cudaGetLastError();
 }
 

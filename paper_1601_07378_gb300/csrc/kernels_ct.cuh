@@ -1322,12 +1322,13 @@ __global__ void __launch_bounds__(kThreads) k3g_ct(DevTables t, const float2* __
 
 // Density x-pass for one (y, z tile, band group): each band's inverse
 // x-pass ends in registers, where the weighted |psi|^2 is added in FP32 over
-// the group's bands (at most 16); the group's partial sum is written in FP64
-// and the groups are added later in a fixed order.
+// the group's bands (at most 16); the group's partial sum is stored as it is,
+// in FP32 (half the bytes of an FP64 copy, and nothing rounded), and the
+// groups are added later in FP64 in a fixed order.
 template <int N>
 __global__ void __launch_bounds__(kThreads, minb(N, 5)) k3d_ct(DevTables t, const float2* __restrict__ tw1, const float2* slab,
                                                   int nb, int bpg, const float* __restrict__ occ, long long b_base,
-                                                  int pair, long long nreal, double* __restrict__ partial) {
+                                                  int pair, long long nreal, float* __restrict__ partial) {
     using SC = Sched<N>;
     constexpr int nst = SC::nst;
     static_assert(nst >= 2, "compile-time x-pass needs at least two stages");
@@ -1390,17 +1391,14 @@ __global__ void __launch_bounds__(kThreads, minb(N, 5)) k3d_ct(DevTables t, cons
         __syncthreads();
     }
     if (act) {
-        double* part = partial + (long long)grp * N * pstride + y * n3 + z0 + 2 * slot;
+        // even offset (n3 even, z0 and 2 slot even): 8-byte aligned pairs
+        float* part = partial + (long long)grp * N * pstride + y * n3 + z0 + 2 * slot;
 #pragma unroll
         for (int u = 0; u < L::U; ++u) {
             const int i = 2 * (warp + u * kWarps) + sub;
             if (L::NI % (2 * kWarps) == 0 || i < L::NI) {
 #pragma unroll
-                for (int r = 0; r < R; ++r) {
-                    double* q = part + (i + r * L::NI) * pstride;
-                    q[0] = (double)acc[u][r].x;
-                    q[1] = (double)acc[u][r].y;
-                }
+                for (int r = 0; r < R; ++r) *reinterpret_cast<float2*>(part + (i + r * L::NI) * pstride) = acc[u][r];
             }
         }
     }
@@ -1417,7 +1415,7 @@ template <int N>
 __global__ void __launch_bounds__(kThreads, N <= 96 ? VLOC_MINB_K3DQ : 1) k3dq_ct(DevTables t, const float2* __restrict__ tw1,
                                                    const float2* slab, int nb, int bpg, const float* __restrict__ occ,
                                                    long long b_base, int pair, long long nreal,
-                                                   double* __restrict__ partial) {
+                                                   float* __restrict__ partial) {
     using SC = Sched<N>;
     static_assert(SC::nst == 2, "quarter-sphere x-pass: two-stage lengths");
     constexpr int W = kWarps;
@@ -1487,17 +1485,13 @@ __global__ void __launch_bounds__(kThreads, N <= 96 ? VLOC_MINB_K3DQ : 1) k3dq_c
         }
         __syncthreads();
     }
-    double* part0 = partial + (long long)grp * N * pstride + y * n3 + z0;
+    float* part0 = partial + (long long)grp * N * pstride + y * n3 + z0;  // the group sums in FP32, as in k3d_ct
     if (act) {
 #pragma unroll
         for (int u = 0; u < FR; ++u) {
             const int i = 2 * (warp + u * W) + sub;
 #pragma unroll
-            for (int r = 0; r < R; ++r) {
-                double* q = part0 + 2 * slot + (i + r * NB) * pstride;
-                q[0] = (double)acc[u][r].x;
-                q[1] = (double)acc[u][r].y;
-            }
+            for (int r = 0; r < R; ++r) *reinterpret_cast<float2*>(part0 + 2 * slot + (i + r * NB) * pstride) = acc[u][r];
         }
     }
     if constexpr (LU > 0) {
@@ -1507,7 +1501,7 @@ __global__ void __launch_bounds__(kThreads, N <= 96 ? VLOC_MINB_K3DQ : 1) k3dq_c
             const int i = FR * 2 * W + tk / 32, ls = (tk >> 1) & 15, ln = tk & 1;
             if (tk < LU * 32 && 2 * ls < lines) {
 #pragma unroll
-                for (int r = 0; r < R; ++r) part0[2 * ls + ln + (i + r * NB) * pstride] = (double)accl[k][r];
+                for (int r = 0; r < R; ++r) part0[2 * ls + ln + (i + r * NB) * pstride] = accl[k][r];
             }
         }
     }
@@ -1672,7 +1666,7 @@ int LaunchCT<T, N>::k3g(int sign, const DevTables& t, const void* tw1, long long
 }
 template <typename T, int N>
 int LaunchCT<T, N>::k3d(const DevTables& t, const void* tw1, const void* slab, long long nb, int bpg, const void* occ,
-                        long long b_base, int pair, long long nreal, double* partial, cudaStream_t st) {
+                        long long b_base, int pair, long long nreal, float* partial, cudaStream_t st) {
     const int ng = (int)((nb + bpg - 1) / bpg);
     const dim3 grid(t.n2, (t.n3 + kLines - 1) / kLines, ng);
     if constexpr (Sched<N>::nst == 2) {

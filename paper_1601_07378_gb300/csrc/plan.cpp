@@ -1137,13 +1137,21 @@ int vloc_density(vloc_plan p, const void* c, const void* occ, int64_t nb, void* 
     const DevTables& t = p->dt;
     const LaunchAxes& ax = p->ax;
     int rc;
-    if ((rc = launch(p, KK_AUX, st, [&] { return launch_zero_f64(p->d_acc, p->N, st); }))) return rc;
     const size_t slab_band = (size_t)p->NP * p->n2 * p->n3 * p->elem;
-    const long long per_pass = (long long)p->ngroups * kGradBandsPerGroup;  // bands per density x-pass
+    // bands per density x-pass: the partial buffer holds ngroups FP64 grids,
+    // or twice as many FP32 ones
+    const int pf32 = density_partials_f32(dbl, p->fast, t);
+    const long long per_pass = (long long)p->ngroups * (pf32 ? 2 : 1) * kGradBandsPerGroup;
     double* partial = p->d_acc + p->N;
+    // FP32 partials: the first reduction starts the FP64 accumulator and the
+    // last writes rho itself, so no zeroing and no finishing pass
+    const bool fused = pf32 && nb > 0;
+    bool first = true;
+    if (!fused && (rc = launch(p, KK_AUX, st, [&] { return launch_zero_f64(p->d_acc, p->N, st); }))) return rc;
     // K1 + K2 on `cb` complex bands at `src` (stride npw), then the density
-    // x-pass; `base` is the global index of the chunk's first (pair) band.
-    auto chunk_density = [&](const void* src, long long cb, long long base, int pair) -> int {
+    // x-pass; `base` is the global index of the chunk's first (pair) band,
+    // `last` says that no chunk follows.
+    auto chunk_density = [&](const void* src, long long cb, long long base, int pair, bool last) -> int {
         int r;
         if ((r = poison(p, st))) return r;
         if ((r = launch(p, KK_SCATTER_Z, st, [&] { return launch_k1_scatter_zpass(dbl, p->fast, t, ax, p->d_tw[2], src, cb, p->d_cyl, st); }))) return r;
@@ -1157,14 +1165,21 @@ int vloc_density(vloc_plan p, const void* c, const void* occ, int64_t nb, void* 
                                                base + j0, pair, nb, partial, &used, st);
                  })))
                 return r;
-            if ((r = launch(p, KK_AUX, st, [&] { return launch_reduce_partials(partial, used, p->N, p->d_acc, st); }))) return r;
+            const bool fin = last && j0 + m >= cb;
+            if ((r = launch(p, KK_AUX, st, [&] {
+                     return pf32 ? launch_reduce_partials_f32((const float*)partial, used, p->N, p->d_acc, first,
+                                                              fin ? (float*)rho : nullptr, st)
+                                 : launch_reduce_partials(partial, used, p->N, p->d_acc, st);
+                 })))
+                return r;
+            first = false;
         }
         return VLOC_OK;
     };
     if (!p->gamma) {
         for (int64_t b0 = 0; b0 < nb; b0 += p->chunk) {
             const long long cb = std::min<long long>(p->chunk, nb - b0);
-            if ((rc = chunk_density((const char*)c + b0 * ustride, cb, b0, 0))) return rc;
+            if ((rc = chunk_density((const char*)c + b0 * ustride, cb, b0, 0, b0 + cb >= nb))) return rc;
         }
     } else {
         // Gamma-point pairs: psi_2p + i psi_2p+1, both real, so |.|^2 splits
@@ -1178,9 +1193,10 @@ int vloc_density(vloc_plan p, const void* c, const void* occ, int64_t nb, void* 
                                               p->npw, p->d_gamma_buf, cp, st);
                  })))
                 return rc;
-            if ((rc = chunk_density(p->d_gamma_buf, cp, p0, 1))) return rc;
+            if ((rc = chunk_density(p->d_gamma_buf, cp, p0, 1, p0 + cp >= npairs))) return rc;
         }
     }
+    if (fused) return VLOC_OK;
     return launch(p, KK_AUX, st, [&] { return launch_finish_grad_v(dbl, p->d_acc, rho, p->N, st); });
 }
 

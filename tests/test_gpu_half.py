@@ -79,14 +79,17 @@ def test_density(prec, n, R, nb, order, generic):
     assert _rel(rho1.cpu().numpy(), O.density(n, g, c.astype(np.complex128))) < TOL[prec]
 
 
-def test_density_chunks_groups_and_determinism():
-    # chunks of 3 bands, more bands than one x-pass launch takes (groups of
-    # 16), bit-identical on repeat
+@pytest.mark.parametrize("generic", [False, True])
+def test_density_chunks_groups_and_determinism(generic):
+    # chunks of 3 and 64 bands and one of all 70, several groups of 16 bands;
+    # the compile-time FP32 kernels keep their group sums in FP32 (one x-pass
+    # launch takes a whole chunk), the runtime-radix ones in FP64 (a chunk
+    # of 64 or 70 bands takes two launches); bit-identical on repeat
     n, R, nb = (24, 20, 30), 5, 70
     g, c, _ = make_case(n, R, nb, seed=7, order="shuffled", prec="f32")
     ref = O.density(n, g, c.astype(np.complex128))
     for chunk in (3, 64, 0):
-        plan = vloc.VlocPlan(n, g, torch.complex64, chunk=chunk)
+        plan = vloc.VlocPlan(n, g, torch.complex64, chunk=chunk, generic=generic)
         ct = torch.from_numpy(c).cuda()
         a = plan.density(ct)
         b = plan.density(ct)
