@@ -1042,7 +1042,9 @@ __global__ void __launch_bounds__(kThreads, minb_k4q(N, GM)) k4q_ct(DevTables t,
 // k4q_ct without the gather pass: the last forward stage (radix R0, rows
 // x = i + r NA, the row structure of the dense z-band table) writes each
 // result straight to its caller position, times 1/N, plus diag times the
-// band for an H apply.  Plain plans with the dense table.
+// band for an H apply.  Plain plans with the dense table.  (Positions worked
+// out from each line's stick run, as k1d_ct reads its inputs, measured
+// slower here: 0.369 against 0.365 ms per 1024 bands at 96^3.)
 #ifndef VLOC_K4_DIRECT
 #define VLOC_K4_DIRECT 1
 #endif
@@ -1542,6 +1544,8 @@ int launch_k1_ct(const DevTables& t, const void* tw3, const void* coeffs, long l
         // indices of the complex band the kernel reads)
         if (!GM && VLOC_K1_DIRECT && t.zd_rows == QRows<N>::groups() * QRows<N>::NA) {
             if (t.runs == 2) {
+                static const cudaError_t oncer = CtSmem<N>::ensure(k1d_ct<N, true>);
+                if (oncer) return (int)oncer;
                 k1d_ct<N, true><<<dim3(t.T, (unsigned)nb), kThreads, CtSmem<N>::sm, st>>>(t, (const float2*)tw3,
                                                                                       (const float2*)coeffs, (float2*)cyl);
                 return (int)cudaGetLastError();

@@ -77,15 +77,24 @@ def test_bulk_staged_z_pass_chunks_poison_h_alias():
 def test_run_addressed_k1_matches_dense_table_bit_for_bit(n, R):
     # a caller list in stick order lets K1 address its inputs from each
     # stick's run; the same plane waves in a shuffled order go through the
-    # dense z-band table.  Each element of the transform sees the same values
-    # and the same arithmetic, so the results agree bit for bit.
-    g, c, V = make_case(n, R, 4, seed=103, prec="f32")
+    # dense z-band table.  Each element of the transform sees
+    # the same values and the same arithmetic, so the results agree bit for
+    # bit, for the action and for H = diag + V_loc written over its input.
+    g, c, V = make_case(n, R, 5, seed=103, prec="f32")
     perm = np.random.default_rng(104).permutation(len(g))
+    pt = torch.from_numpy(perm).cuda()
     p_run = vloc.VlocPlan(n, g, torch.complex64)
     p_tab = vloc.VlocPlan(n, np.ascontiguousarray(g[perm]), torch.complex64)
     Vt = torch.from_numpy(V).cuda()
-    out_run = p_run.apply(torch.from_numpy(c).cuda(), Vt)
-    out_tab = p_tab.apply(torch.from_numpy(np.ascontiguousarray(c[:, perm])).cuda(), Vt)
+    c_run, c_tab = torch.from_numpy(c).cuda(), torch.from_numpy(np.ascontiguousarray(c[:, perm])).cuda()
+    out_run, out_tab = p_run.apply(c_run, Vt), p_tab.apply(c_tab, Vt)
+    h = np.linspace(0.5, 2.0, len(g)).astype(np.float32)
+    h_run, h_tab = torch.from_numpy(h).cuda(), torch.from_numpy(np.ascontiguousarray(h[perm])).cuda()
+    p_run.apply_h(c_run, Vt, h_run, out=c_run)
+    p_tab.apply_h(c_tab, Vt, h_tab, out=c_tab)
     torch.cuda.synchronize()
-    assert torch.equal(out_tab, out_run[:, torch.from_numpy(perm).cuda()])
+    assert torch.equal(out_tab, out_run[:, pt])
+    assert torch.equal(c_tab, c_run[:, pt])
     assert rel_l2_per_band(out_run.cpu().numpy(), oracle_apply(n, g, c, V)).max() < TOL["f32"]
+    want = oracle_apply(n, g, c, V) + h.astype(np.float64)[None, :] * c.astype(np.complex128)
+    assert rel_l2_per_band(c_run.cpu().numpy(), want).max() < TOL["f32"]
