@@ -197,7 +197,8 @@ int density_partials_f32(int dbl, int fast, const DevTables& t);
 size_t density_smem_bytes(int dbl, int n);
 int launch_reduce_partials(const double* partial, int ngroups, long long N, double* acc, cudaStream_t st);
 // The same over FP32 partials: the groups are added in order in FP32 with
-// a compensation word, and the pair is added to acc in FP64 (acc taken as
+// a compensation word (a sum as accurate as one in twice FP32's precision),
+// and the pair is added to acc in FP64 (acc taken as
 // zero when `first`); with `out` non-null the total goes there, rounded to
 // FP32, instead of to acc.
 int launch_reduce_partials_f32(const float* partial, int ngroups, long long N, double* acc, int first, float* out,

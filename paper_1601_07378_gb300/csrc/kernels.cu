@@ -315,11 +315,14 @@ int launch_reduce_partials(const double* partial, int ngroups, long long N, doub
     k_reduce_partials<<<(unsigned)((N + 255) / 256), 256, 0, st>>>(partial, ngroups, N, acc);
     return (int)cudaGetLastError();
 }
-// FP32 partials, added in group order by compensated summation in FP32
-// (Neumaier's form of Kahan summation, each step an error-free two-sum after
-// Knuth): s + c carries the running sum to about 2^-48 of the terms' sum,
-// so the groups cost FP32 adds rather than FP64 conversions and adds (a
-// slow pipe on this part); s + c then joins the FP64 accumulator.
+// FP32 partials, added in group order by compensated summation in FP32: an
+// error-free two-sum (Knuth) per group, the rounding errors gathered in a
+// second word c (Ogita, Rump and Oishi's Sum2).  s + c is then as accurate as
+// a sum in twice FP32's precision: its error is at most ((ng - 1) u)^2 times
+// the sum of |partial|, u = 2^-24 (1.4e-11 for 64 groups), far below the
+// FP32 result's own rounding.  The groups so cost FP32 adds rather than FP64
+// conversions and adds (a slow pipe on this part); s + c then joins the FP64
+// accumulator.
 __global__ void k_reduce_partials_f32(const float* __restrict__ partial, int ng, long long N, double* __restrict__ acc,
                                       int first, float* __restrict__ out) {
     const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
