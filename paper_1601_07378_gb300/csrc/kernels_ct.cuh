@@ -811,7 +811,7 @@ __global__ void __launch_bounds__(32 * W, minb_k3q(N)) k3q_ct(DevTables t, const
     constexpr int R0 = SC::R(0), R1 = SC::R(1);
     constexpr int NA = N / R0;  // units of the first inverse and the last forward stage
     constexpr int NB = N / R1;  // units of the chained middle stage
-    constexpr int UA = (NA + 2 * W - 1) / (2 * W), UB = (NB + 2 * W - 1) / (2 * W);
+    constexpr int UA = (NA + 2 * W - 1) / (2 * W);
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float2* buf = reinterpret_cast<float2*>(smem_raw);
     float2* twA = buf + N * kLdP;
