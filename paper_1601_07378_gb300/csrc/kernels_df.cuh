@@ -163,6 +163,10 @@ template <class Pol, int N> constexpr bool df_floors() { return std::is_same<Pol
 #ifndef VLOC_MINB_K4DF
 #define VLOC_MINB_K4DF 7
 #endif
+// direct inverse z-pass (k1dw_body) where the dense z-band table exists
+#ifndef VLOC_DF_DIRECT_Z
+#define VLOC_DF_DIRECT_Z 1
+#endif
 template <class Pol, int N>
 __global__ void __launch_bounds__(kThreads) k1_w(DevTables t, const typename Pol::TW* __restrict__ tw3,
                                                 const double2* __restrict__ coeffs, typename Pol::V* __restrict__ cyl) {
@@ -173,6 +177,85 @@ __global__ void __launch_bounds__(kThreads, MINB) k1_wb(DevTables t, const typen
                                                        const double2* __restrict__ coeffs,
                                                        typename Pol::V* __restrict__ cyl) {
     k1w_body<Pol, N>(t, tw3, coeffs, cyl);
+}
+
+// ------------------------------------------------- K1, direct form
+// For plans whose plane waves all lie in the quarter band |l| <= n3/4 (the
+// dense z-band table exists): each thread loads its own first-stage inputs,
+// rows x = i + r NA of its line, through the table, and the rows outside the
+// band are neither loaded nor transformed.  No buffer clearing and no
+// scatter pass; the second stage and the row stores are those of k1w_body.
+// Measured per 1024 bands at 96^3: double-float 1.54 against 1.66-1.76 ms,
+// native 6.14 against 6.71 ms.  The mirror for K4 (the last forward stage
+// storing each result straight to its caller position) measured slower,
+// 2.01 against 1.78 ms (double-float) and 7.03 against 6.95 (native): its
+// 16-byte stores go to 16 different sticks per instruction, where the tile
+// form's gather writes the caller's band in order.
+template <class Pol, int N>
+__device__ __forceinline__ void k1dw_body(const DevTables& t, const typename Pol::TW* __restrict__ tw3,
+                                          const double2* __restrict__ coeffs, typename Pol::V* __restrict__ cyl) {
+    using V = typename Pol::V;
+    using TW = typename Pol::TW;
+    using QR = QRows<N>;
+    constexpr int R0 = QR::R0, NA = QR::NA, W = kWarps;
+    constexpr int UA = (NA + 2 * W - 1) / (2 * W);
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float2* buf = reinterpret_cast<float2*>(smem_raw);
+    TW* stw = reinterpret_cast<TW*>(buf + N * kLdP);
+    const int tile = blockIdx.x;
+    const long long b = blockIdx.y;
+    const int l0 = kLinesDF * (int)blockIdx.z;
+    const int s0 = t.tile_ptr[tile] + l0;
+    const int lines = min(kLinesDF, t.tile_ptr[tile + 1] - s0);
+    if (lines <= 0) return;  // uniform over the CTA
+    const int slot = slot_of_df(), sub = sub_of_df(), warp = warp_of_df();
+    const bool act = slot < lines;
+    // this slot's line of the plan tile (32 lines) in the table's rows
+    const int* zd = t.zdense + (size_t)tile * (QR::groups() * NA) * kLines + l0 + slot;
+    const double2* c = coeffs + b * t.npw;
+    SmemT<V> sb{buf};
+    if (act) {
+#pragma unroll
+        for (int u = 0; u < UA; ++u) {
+            const int i = 2 * (warp + u * W) + sub;
+            if (NA % (2 * W) == 0 || i < NA) {
+                int e[R0];
+                sfor<R0>([&](auto rc) {
+                    constexpr int r = decltype(rc)::value;
+                    if constexpr (QR::kind(r) != 0) e[r] = zd[(QR::group(r) * NA + i) * kLines];
+                });
+                V h[R0];
+                sfor<R0>([&](auto rc) {
+                    constexpr int r = decltype(rc)::value;
+                    if constexpr (QR::kind(r) == 0) h[r] = czero<V>();
+                    else h[r] = e[r] >= 0 ? Pol::from(c[e[r]]) : czero<V>();
+                });
+                DftZ<R0, +1, QR::mask()>::run(h);
+#pragma unroll
+                for (int r = 0; r < R0; ++r) sb(i * R0 + r, slot, h[r]);
+            }
+        }
+    }
+    load_tww(stw, tw3, N);
+    __syncthreads();
+    NatStage<N, +1, W, 1, V, TW>::template run<true>(stw, sb, sb, slot, sub, warp, act);
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    for (int l = threadIdx.x >> 5; l < lines; l += kWarps) {
+        V* row = cyl + (b * t.S + t.tile_sticks[s0 + l]) * (long long)N;
+        for (int z = lane; z < N; z += 32) row[z] = w_store(w_at<V>(buf, z, l));
+    }
+}
+template <class Pol, int N>
+__global__ void __launch_bounds__(kThreads) k1d_w(DevTables t, const typename Pol::TW* __restrict__ tw3,
+                                                 const double2* __restrict__ coeffs, typename Pol::V* __restrict__ cyl) {
+    k1dw_body<Pol, N>(t, tw3, coeffs, cyl);
+}
+template <class Pol, int N, int MINB>
+__global__ void __launch_bounds__(kThreads, MINB) k1d_wb(DevTables t, const typename Pol::TW* __restrict__ tw3,
+                                                        const double2* __restrict__ coeffs,
+                                                        typename Pol::V* __restrict__ cyl) {
+    k1dw_body<Pol, N>(t, tw3, coeffs, cyl);
 }
 
 // ------------------------------------------------------------------ K2
@@ -471,6 +554,22 @@ template <int P, int N>
 int LaunchF64<P, N>::k1(const DevTables& t, const void* tw3, const void* coeffs, long long nb, void* cyl,
                         cudaStream_t st) {
     using Pol = PolOf<P>;
+    if constexpr (Sched<N>::nst == 2) {
+        if (VLOC_DF_DIRECT_Z && t.zd_rows == QRows<N>::groups() * QRows<N>::NA) {
+            if constexpr (df_floors<Pol, N>()) {
+                static const cudaError_t onced = WSmem<Pol, N>::ensure(k1d_wb<Pol, N, VLOC_MINB_K1DF>);
+                if (onced) return (int)onced;
+                k1d_wb<Pol, N, VLOC_MINB_K1DF><<<dim3(t.T, (unsigned)nb, 2), kThreads, WSmem<Pol, N>::sm, st>>>(
+                    t, (const typename Pol::TW*)tw3, (const double2*)coeffs, (typename Pol::V*)cyl);
+            } else {
+                static const cudaError_t onced = WSmem<Pol, N>::ensure(k1d_w<Pol, N>);
+                if (onced) return (int)onced;
+                k1d_w<Pol, N><<<dim3(t.T, (unsigned)nb, 2), kThreads, WSmem<Pol, N>::sm, st>>>(
+                    t, (const typename Pol::TW*)tw3, (const double2*)coeffs, (typename Pol::V*)cyl);
+            }
+            return (int)cudaGetLastError();
+        }
+    }
     if constexpr (df_floors<Pol, N>()) {
         static const cudaError_t onceb = WSmem<Pol, N>::ensure(k1_wb<Pol, N, VLOC_MINB_K1DF>);
         if (onceb) return (int)onceb;

@@ -109,3 +109,23 @@ def test_double_float_batched_graph():
         torch.cuda.synchronize()
         assert rel_l2_per_band(outs[0].cpu().numpy(), oracle_apply(n1, g1, c1, V1)).max() < TOL["f64"]
         assert rel_l2_per_band(outs[1].cpu().numpy(), oracle_apply(n2, g2, c2, V2)).max() < TOL["f64"]
+
+
+@pytest.mark.parametrize("df", [True, False])
+@pytest.mark.parametrize("n,R", [((36, 40, 48), 12.0), ((36, 40, 48), 14.0), ((30, 24, 72), 18.0), ((40, 36, 96), 24.0)])
+def test_fp64_direct_z_pass_h_in_place(df, n, R):
+    # |l| <= n3/4 for every plane wave (R <= n3/4): the inverse z-pass loads
+    # the caller's band through the dense z-band table; R = 14 at n3 = 48
+    # leaves the band and takes the tile z-pass.  Both FP64 forms, H = diag +
+    # V_loc written over its input, chunks of 3 bands.
+    g, c, V = make_case(n, R, 7, seed=31, order="shuffled", prec="f64")
+    plan = vloc.VlocPlan(n, g, torch.complex128, double_float=df, chunk=3)
+    h = np.linspace(0.5, 2.0, len(g))
+    want = oracle_apply(n, g, c, V) + h[None, :] * c
+    ct = torch.from_numpy(np.ascontiguousarray(c)).cuda()
+    Vt, ht = torch.from_numpy(V).cuda(), torch.from_numpy(h).cuda()
+    out = plan.apply_h(ct, Vt, ht)
+    plan.apply_h(ct, Vt, ht, out=ct)
+    torch.cuda.synchronize()
+    assert rel_l2_per_band(out.cpu().numpy(), want).max() < TOL["f64"]
+    assert torch.equal(ct, out)
